@@ -1,0 +1,91 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the smoke check.
+
+This module holds no arithmetic of the method: only the random initial fields
+(splitmix64 counter stream) and the named workload settings.  Both the CUDA path
+and the CPU oracle receive the same host arrays from here.
+
+u0(x) = mean + amp * U(-1, 1), drawn independently per grid point, row-major
+over the grid (last axis fastest).  U is the top 53 bits of
+splitmix64(seed + (i + 1) * 0x9E3779B97F4A7C15), the published SplitMix64
+finaliser of Steele, Lea and Flood (2014).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed: int, count: int) -> np.ndarray:
+    """The first ``count`` outputs of a SplitMix64 stream started at ``seed``."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + (np.arange(1, count + 1, dtype=np.uint64) * _GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, count: int) -> np.ndarray:
+    """U[0, 1) doubles from the top 53 bits of the stream."""
+    return (splitmix64(seed, count) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def noisy_field(shape, mean: float, amp: float, seed: int) -> np.ndarray:
+    """mean + amp * U(-1, 1) per grid point, float64, C order."""
+    n = int(np.prod(shape))
+    u = 2.0 * uniform01(seed, n) - 1.0
+    return (mean + amp * u).reshape(shape)
+
+
+PAPER_ETA = tuple(math.sqrt(0.1 + 0.475 * j) for j in range(5))
+
+
+@dataclass
+class Workload:
+    """A named synthetic workload: model, grid, parameters, scheme and solver."""
+    name: str
+    model: str            # "pfc" or "fch"
+    n: tuple              # grid points per axis, last axis fastest
+    L: tuple              # domain lengths
+    eps: float
+    eta1: float = 0.0
+    eta2: float = 0.0
+    tau: float = 0.0
+    M: float = 1.0
+    scheme: str = "bdf2"  # bdf2 | mp | lbdf2 | lmp
+    precision: str = "fp64"  # fp64 | fp32_mixed
+    dt: float = 0.1
+    steps: int = 100
+    tol: float = 1e-10
+    mean: float = 0.0
+    amp: float = 0.05
+    seeds: tuple = (1, 2, 3, 4)
+    s: float = 0.9
+    eta: tuple = PAPER_ETA
+    max_iter: int = 1000
+
+    def u0(self, seed: int) -> np.ndarray:
+        return noisy_field(self.n, self.mean, self.amp, seed)
+
+
+FOURPI = 4.0 * math.pi
+
+# PFC 2D 64x64 on [0, 32 pi]^2, eps = 0.025, u0 = 0.07 + 0.05 U(-1,1), MP,
+# dt = 0.1, 100 steps, FP64, tol 1e-10.
+PFC64 = Workload("pfc2d_64_mp_fp64", "pfc", (64, 64), (32 * math.pi, 32 * math.pi), eps=0.025,
+                 scheme="mp", precision="fp64", dt=0.1, steps=100, tol=1e-10, mean=0.07, amp=0.05)
+
+# FCH 2D 256x256 on [0, 4 pi]^2, W = (u^2-1)^2/4 (tau = 0), eps = 0.1,
+# eta1 = eta2 = eps, u0 = -0.3 + 0.05 U(-1,1), BDF2 (fully implicit, FP32
+# iterations with FP64 norms) beside LBDF2, dt = 1e-3, 1000 steps, tol 1e-8.
+FCH256 = Workload("fch2d_256_bdf2_fp32mixed", "fch", (256, 256), (FOURPI, FOURPI), eps=0.1,
+                  eta1=0.1, eta2=0.1, tau=0.0, scheme="bdf2", precision="fp32_mixed", dt=1e-3,
+                  steps=1000, tol=1e-8, mean=-0.3, amp=0.05)
+
+WORKLOADS = {w.name: w for w in (PFC64, FCH256)}
