@@ -1,0 +1,142 @@
+/*
+ * pagd.h -- C ABI of the GB300 (sm_103a) PAGD time-step library.
+ *
+ * The library advances the phase field crystal (PFC) and functionalized
+ * Cahn-Hilliard (FCH) equations of Park, Salgado & Wise (arXiv 2204.07247,
+ * Sec. 2) on a periodic Fourier collocation grid (Sec. 3.2) with the fully
+ * implicit BDF2 / midpoint (MP) schemes (Sec. 3.1.1, Eqs. eqn:FCH-semidis-implicit,
+ * obj:BDF2, obj:MP), each step solved by the preconditioned Nesterov accelerated
+ * gradient descent with sweeping friction (Algorithm 2) and the averaged Newton
+ * preconditioner (Sec. 3.4.1), or with the linear IMEX schemes LBDF2 / LMP
+ * (Eq. eqn:FCH-semidis-simplicit, Sec. 3.3).
+ *
+ * Conventions (all entry points):
+ *  - Grid: n[0] x n[1] (dim 2) or n[0] x n[1] x n[2] (dim 3) points, row-major
+ *    with the last index fastest; powers of two from 8 to 512 per axis.  Domain
+ *    [0, L[d]) per axis, spacing h_d = L[d] / n[d].
+ *  - Fields are FP64, contiguous, caller-owned.  "_dev" pointers are device
+ *    memory of the current CUDA device; "_host" pointers are host memory.  The
+ *    library never frees caller memory and never calls cudaMalloc: its device
+ *    workspace is handed in by the caller (pagd_workspace_size /
+ *    pagd_set_workspace).
+ *  - Every call returns a pagd_status and never aborts.  On an error during a
+ *    step the solver state (u^n, u^{n-1}, step count) is left as it was before
+ *    the call and the output field is not written; pagd_last_error() then holds
+ *    a one-line description.
+ *  - Work is issued on the stream given at init (NULL = legacy default stream).
+ *    Calls that return numbers to the host synchronise that stream.
+ */
+#ifndef PAGD_H
+#define PAGD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pagd_solver pagd_solver; /* opaque, library-owned host object */
+
+typedef enum {
+    PAGD_OK = 0,
+    PAGD_EINVAL = 1,   /* bad argument (size, pointer, parameter) */
+    PAGD_ENOMEM = 2,   /* workspace missing or too small; host allocation failed */
+    PAGD_ECUDA = 3,    /* a CUDA runtime call failed */
+    PAGD_ENOCONV = 4,  /* PAGD hit max_iter before ||d||_inf <= tol (Algorithm 2) */
+    PAGD_EPRECOND = 5, /* averaged Newton symbol not positive on some wavenumber */
+    PAGD_ENAN = 6,     /* non-finite residual norm */
+    PAGD_ESTATE = 7,   /* call out of order (no workspace / no state set) */
+    PAGD_ETIMEOUT = 8  /* a device-wide barrier gave up waiting (no hang: error) */
+} pagd_status;
+
+enum { PAGD_PFC = 0, PAGD_FCH = 1 };
+/* schemes: BDF2 (backward Euler first step), MP, and the linear IMEX LBDF2, LMP */
+enum { PAGD_BDF2 = 0, PAGD_MP = 1, PAGD_LBDF2 = 2, PAGD_LMP = 3 };
+/* FP64: all arithmetic in FP64.  FP32_MIXED: FFTs and PAGD updates in FP32 on a
+ * correction to an FP64 base point; residual norms, energy, mass, the state and
+ * the acceptance check of every step stay FP64. */
+enum { PAGD_FP64 = 0, PAGD_FP32_MIXED = 1 };
+
+/* Solver settings (Table 1).  Defaults from pagd_default_opts: s = 0.9, the
+ * sweeping list eta = sqrt(0.1, 0.575, 1.05, 1.525, 2), max_iter = 1000,
+ * theta_mode = 0, accel = 1. */
+typedef struct {
+    double s;         /* step size of Algorithms 1/2, > 0 */
+    int n_eta;        /* 1..16 */
+    double eta[16];   /* sweeping friction values, > 0 */
+    int max_iter;     /* residual evaluations per step before PAGD_ENOCONV, >= 1 */
+    int theta_mode;   /* MP preconditioner: 0 = second variation of 2E((v+u^n)/2)
+                         (energy terms x 1/2), 1 = the printed form (x 1) */
+    int accel;        /* 1 = PAGD (Algorithm 2), 0 = PGD (Algorithm 1) */
+} pagd_opts;
+
+pagd_status pagd_default_opts(pagd_opts* opts);
+
+/* PFC model (Sec. 2.1, Eqs. obj:PFC-egy, eqn:PFCsystem): energy
+ * 1/4 u^4 + (1-eps)/2 u^2 - |grad u|^2 + 1/2 (Lap u)^2, mobility M > 0.
+ * stream: a cudaStream_t cast to void* (NULL for the default stream).
+ * On success *out receives a new solver; release it with pagd_destroy. */
+pagd_status pfc_init(pagd_solver** out, int dim, const int* n, const double* L, double eps,
+                     double M, int scheme, int precision, const pagd_opts* opts /* nullable */,
+                     void* stream);
+
+/* FCH model (Sec. 2.2, Eqs. obj:FCHegy, eqn:FCHPDE): energy
+ * 1/2 (eps^2 Lap u - F'(u))^2 - (eps^2 eta1/2 |grad u|^2 + eta2 F(u)),
+ * F(z) = 1/2 (z+1)^2 (1/2 (z-1)^2 + 2/3 tau (z-2)). */
+pagd_status fch_init(pagd_solver** out, int dim, const int* n, const double* L, double eps,
+                     double eta1, double eta2, double tau, double M, int scheme, int precision,
+                     const pagd_opts* opts /* nullable */, void* stream);
+
+/* Device workspace: query the size in bytes, allocate it (e.g. a torch uint8
+ * tensor on the device, 256-byte aligned) and hand it in.  It must stay valid
+ * until pagd_destroy or the next pagd_set_workspace. */
+pagd_status pagd_workspace_size(const pagd_solver* s, size_t* bytes);
+pagd_status pagd_set_workspace(pagd_solver* s, void* dev_ptr, size_t bytes);
+
+/* Set u^0 (and u^{-1} := u^0, Sec. 3.1.1) from a device field; resets the step
+ * counter.  Copies: the caller may reuse u0_dev afterwards. */
+pagd_status pagd_set_state(pagd_solver* s, const double* u0_dev);
+
+/* Advance one step of size dt (dt_{n+1}; the previous step size is remembered).
+ * Implicit schemes iterate PAGD until ||d_i||_inf <= tol (Algorithm 2; for
+ * FP32_MIXED the accepted step also passes that test in FP64).  Writes u^{n+1}
+ * to u_dev (device, n_pts doubles).  iters_out: residual evaluations taken
+ * (0 for IMEX); resid_out: the accepted ||d||_inf.  Both nullable.
+ * Synchronises the stream. */
+pagd_status pagd_step(pagd_solver* s, double* u_dev, double dt, double tol, int* iters_out,
+                      double* resid_out);
+
+/* Advance nsteps steps of size dt in one device launch per chunk of at most
+ * 4096 steps.  u_dev (nullable) receives the final field.  iters_out and
+ * resid_out (nullable, host arrays of nsteps) receive per-step values.
+ * On an error the steps before the failing one are kept. */
+pagd_status pagd_run(pagd_solver* s, double* u_dev, double dt, int nsteps, double tol,
+                     int* iters_out, double* resid_out);
+
+/* Same as pagd_run with host buffers: copies u0_host in (as pagd_set_state),
+ * runs, and copies the final field to u_host_out. */
+pagd_status pagd_run_host(pagd_solver* s, const double* u0_host, double* u_host_out, double dt,
+                          int nsteps, double tol, int* iters_out, double* resid_out);
+
+/* Discrete energy E_N (Fourier differentiation, trapezoidal rule, Sec. 3.2)
+ * and mass (u, 1)_N of a device field. */
+pagd_status pagd_energy(pagd_solver* s, const double* u_dev, double* E);
+pagd_status pagd_mass(pagd_solver* s, const double* u_dev, double* m);
+
+/* Unnormalised forward DFT of a real device field (Sec. 3.2): writes the half
+ * spectrum n[0] x ... x (n[dim-1]/2 + 1) complex (interleaved re, im doubles),
+ * row-major.  pagd_fft_c2r inverts it including the 1/n_pts factor. */
+pagd_status pagd_fft_r2c(pagd_solver* s, const double* u_dev, double* spec_dev);
+pagd_status pagd_fft_c2r(pagd_solver* s, const double* spec_dev, double* u_dev);
+
+/* Copy the current u^n / u^{n-1} to device buffers (either nullable), and the
+ * number of steps taken since pagd_set_state. */
+pagd_status pagd_get_state(pagd_solver* s, double* un_dev, double* unm1_dev, int* step);
+
+const char* pagd_last_error(const pagd_solver* s);
+void pagd_destroy(pagd_solver* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAGD_H */

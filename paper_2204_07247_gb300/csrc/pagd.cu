@@ -1,0 +1,620 @@
+// pagd.cu -- C ABI of the PAGD library (include/pagd.h): solver objects,
+// workspace layout, launch planning and the persistent cooperative kernel.
+//
+// Built by nvcc for sm_103a into libpagd.so.  The same file also compiles as
+// host C++ with -DPAGD_EMU into a test-only emulation library in which device
+// memory is host memory and a "launch" runs the kernel's phases block by block
+// on the calling thread.
+#include "solver.cuh"
+#include "../../include/pagd.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace pagd;
+
+#ifndef PAGD_EMU
+namespace pagd {
+
+constexpr unsigned long long kBarrierTimeoutNs = 5000000000ull;  // 5 s per wait
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Device-wide barrier for a cooperative launch (all CTAs co-resident).  The
+// wait is bounded: after kBarrierTimeoutNs, or once another CTA has flagged an
+// error, the CTA records the error and returns false instead of spinning on.
+__device__ bool grid_barrier(Scal* sc, unsigned& gen) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = gen;
+        __threadfence();
+        const unsigned prev = atomicAdd(&sc->bar_count, 1u);
+        if (prev == gridDim.x - 1) {
+            atomicExch(&sc->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&sc->bar_gen, 1u);
+        } else {
+            const unsigned long long t0 = gtimer();
+            volatile unsigned* vg = &sc->bar_gen;
+            volatile int* ve = &sc->bar_error;
+            while (*vg == g) {
+                if (*ve) { ok = 0; break; }
+                __nanosleep(32);
+                if (gtimer() - t0 > kBarrierTimeoutNs) {
+                    atomicOr(&sc->bar_error, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    gen++;
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) pagd_kernel(Params P) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ double red[32];
+    Ctl c = ctl_init(P);
+    unsigned gen = 0;
+    while (c.ph != PH_DONE) {
+        exec_phase<T>(P, c, smem, red);
+        if (!grid_barrier(P.sc, gen)) break;
+        ctl_advance<T>(P, c);
+    }
+}
+
+}  // namespace pagd
+#else
+thread_local EmuDim3 threadIdx{0, 0, 0}, blockIdx{0, 0, 0}, blockDim{1, 1, 1}, gridDim{1, 1, 1};
+#endif
+
+// ------------------------------------------------------------ solver object
+
+constexpr int kMaxChunk = 4096;
+
+struct pagd_solver {
+    int model, dim, n[3];
+    double L[3];
+    double eps, eta1, eta2, tau, M;
+    int scheme, precision;
+    pagd_opts opts;
+    void* stream;
+    // layout
+    long long npts;
+    int h1, nslots, tsize;
+    size_t off[32];
+    size_t ws_bytes;
+    char* ws;
+    // launch plan
+    int rb, cb, grid;
+    size_t smem;
+    // state
+    int have_state, step, cur;
+    double dt_prev;
+    std::string err;
+};
+
+enum {
+    O_SC, O_NORMS, O_SUMS, O_STATS, O_TW64, O_TW32, O_U0, O_U1, O_VB, O_G64, O_VBT, O_LBT, O_DD0,
+    O_DD1, O_SS0, O_SS1, O_C0, O_NB, O_DB, O_CL64, O_NB64, O_DB64, O_END
+};
+
+static pagd_status fail(pagd_solver* s, pagd_status st, const char* msg) {
+    if (s) s->err = msg;
+    return st;
+}
+
+static bool pow2_ok(int v) { return v >= 8 && v <= 512 && (v & (v - 1)) == 0; }
+
+static int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) l++;
+    return l;
+}
+
+static void plan_layout(pagd_solver* s) {
+    const long long N = s->npts;
+    const long long H = (long long)s->h1 * s->n[0];
+    const int T = s->tsize;
+    size_t sz[O_END];
+    sz[O_SC] = sizeof(Scal);
+    sz[O_NORMS] = sizeof(unsigned long long) * s->nslots;
+    sz[O_SUMS] = sizeof(double) * s->nslots;
+    sz[O_STATS] = sizeof(StepStat) * kMaxChunk;
+    sz[O_TW64] = sizeof(double2) * kNMax;
+    sz[O_TW32] = sizeof(float2) * kNMax;
+    sz[O_U0] = sz[O_U1] = sz[O_VB] = sz[O_G64] = sizeof(double) * N;
+    sz[O_VBT] = sz[O_LBT] = sz[O_DD0] = sz[O_DD1] = (size_t)T * N;
+    sz[O_SS0] = sz[O_SS1] = sz[O_C0] = (size_t)2 * T * H;
+    sz[O_NB] = sz[O_DB] = (size_t)2 * T * H * 2;
+    sz[O_CL64] = sizeof(double2) * H * 3;
+    sz[O_NB64] = sizeof(double2) * H * 3;
+    sz[O_DB64] = sizeof(double2) * H * 2;
+    size_t o = 0;
+    for (int i = 0; i < O_END; i++) {
+        s->off[i] = o;
+        o += (sz[i] + 255) & ~(size_t)255;
+    }
+    s->ws_bytes = o;
+}
+
+static Params base_params(const pagd_solver* s) {
+    Params P;
+    std::memset(&P, 0, sizeof(P));
+    P.model = s->model;
+    P.scheme = s->scheme;
+    P.precision = s->precision;
+    P.n0 = s->n[0];
+    P.n1 = s->n[1];
+    P.logn0 = ilog2(s->n[0]);
+    P.logn1 = ilog2(s->n[1]);
+    P.h1 = s->h1;
+    P.npts = s->npts;
+    P.rb = s->rb;
+    P.cb = s->cb;
+    const double twopi = 6.283185307179586476925286766559;
+    P.k0sq = (twopi / s->L[0]) * (twopi / s->L[0]);
+    P.k1sq = (twopi / s->L[1]) * (twopi / s->L[1]);
+    P.cellvol = (s->L[0] / s->n[0]) * (s->L[1] / s->n[1]);
+    P.eps = s->eps;
+    P.eta1 = s->eta1;
+    P.eta2 = s->eta2;
+    P.tau = s->tau;
+    P.M = s->M;
+    P.s = s->opts.s;
+    P.n_eta = s->opts.n_eta;
+    P.accel = s->opts.accel;
+    P.max_iter = s->opts.max_iter;
+    P.max_recheck = 16;
+    P.theta_mode = s->opts.theta_mode;
+    const double sq = std::sqrt(s->opts.s);
+    for (int j = 0; j < s->opts.n_eta; j++) P.lam[j] = (1.0 - s->opts.eta[j] * sq) / (1.0 + s->opts.eta[j] * sq);
+    P.nslots = s->nslots;
+    P.cur0 = s->cur;
+    P.step0 = s->step;
+    char* w = s->ws;
+    P.sc = (Scal*)(w + s->off[O_SC]);
+    P.norms = (unsigned long long*)(w + s->off[O_NORMS]);
+    P.sums = (double*)(w + s->off[O_SUMS]);
+    P.stats = (StepStat*)(w + s->off[O_STATS]);
+    P.tw64 = (const double2*)(w + s->off[O_TW64]);
+    P.tw32 = (const float2*)(w + s->off[O_TW32]);
+    P.U[0] = (double*)(w + s->off[O_U0]);
+    P.U[1] = (double*)(w + s->off[O_U1]);
+    P.VB = (double*)(w + s->off[O_VB]);
+    P.G64 = (double*)(w + s->off[O_G64]);
+    P.VBt = w + s->off[O_VBT];
+    P.LBt = w + s->off[O_LBT];
+    P.DD[0] = w + s->off[O_DD0];
+    P.DD[1] = w + s->off[O_DD1];
+    P.SS[0] = w + s->off[O_SS0];
+    P.SS[1] = w + s->off[O_SS1];
+    P.C0 = w + s->off[O_C0];
+    P.NB = w + s->off[O_NB];
+    P.DB = w + s->off[O_DB];
+    P.CL64 = (double2*)(w + s->off[O_CL64]);
+    P.NB64 = (double2*)(w + s->off[O_NB64]);
+    P.DB64 = (double2*)(w + s->off[O_DB64]);
+    return P;
+}
+
+// ------------------------------------------------------- device plumbing
+
+#ifdef PAGD_EMU
+static pagd_status dcopy(pagd_solver*, void* dst, const void* src, size_t n) {
+    std::memmove(dst, src, n);
+    return PAGD_OK;
+}
+static pagd_status dzero(pagd_solver*, void* dst, size_t n) {
+    std::memset(dst, 0, n);
+    return PAGD_OK;
+}
+static pagd_status dsync(pagd_solver*) { return PAGD_OK; }
+static int num_sms() {
+    const char* e = std::getenv("PAGD_EMU_SMS");  // tile plan of an n-SM device
+    const int v = e ? std::atoi(e) : 4;
+    return v > 0 ? v : 4;
+}
+template <class T> static pagd_status launch(pagd_solver* s, const Params& P) {
+    std::vector<char> sm(s->smem + 64);
+    char* base = (char*)(((uintptr_t)sm.data() + 15) & ~(uintptr_t)15);
+    double red[32];
+    gridDim.x = (unsigned)s->grid;
+    blockDim.x = 1;
+    threadIdx.x = 0;
+    Ctl c = ctl_init(P);
+    while (c.ph != PH_DONE) {
+        for (int b = 0; b < s->grid; b++) {
+            blockIdx.x = (unsigned)b;
+            exec_phase<T>(P, c, base, red);
+        }
+        ctl_advance<T>(P, c);
+    }
+    return PAGD_OK;
+}
+#else
+static pagd_status cuda_fail(pagd_solver* s, cudaError_t e, const char* what) {
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    return fail(s, PAGD_ECUDA, buf);
+}
+static pagd_status dcopy(pagd_solver* s, void* dst, const void* src, size_t n) {
+    cudaError_t e = cudaMemcpyAsync(dst, src, n, cudaMemcpyDefault, (cudaStream_t)s->stream);
+    return e == cudaSuccess ? PAGD_OK : cuda_fail(s, e, "cudaMemcpyAsync");
+}
+static pagd_status dzero(pagd_solver* s, void* dst, size_t n) {
+    cudaError_t e = cudaMemsetAsync(dst, 0, n, (cudaStream_t)s->stream);
+    return e == cudaSuccess ? PAGD_OK : cuda_fail(s, e, "cudaMemsetAsync");
+}
+static pagd_status dsync(pagd_solver* s) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)s->stream);
+    return e == cudaSuccess ? PAGD_OK : cuda_fail(s, e, "cudaStreamSynchronize");
+}
+static int num_sms() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return v > 0 ? v : 1;
+}
+template <class T> static pagd_status launch(pagd_solver* s, const Params& P) {
+    void (*kern)(Params) = pagd_kernel<T>;
+    cudaError_t e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)s->smem);
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaFuncSetAttribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, kThreads, s->smem);
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm < 1) return fail(s, PAGD_EINVAL, "kernel does not fit on an SM with this tile plan");
+    int grid = s->grid;
+    const int cap = per_sm * num_sms();
+    if (grid > cap) grid = cap;
+    Params Pc = P;
+    void* args[] = {(void*)&Pc};
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kThreads), args, s->smem,
+                                    (cudaStream_t)s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaLaunchCooperativeKernel");
+    return PAGD_OK;
+}
+#endif
+
+static pagd_status run_program(pagd_solver* s, Params& P) {
+    pagd_status st = dzero(s, P.sc, sizeof(Scal));
+    if (st != PAGD_OK) return st;
+    if (s->tsize == 8) st = launch<double>(s, P);
+    else st = launch<float>(s, P);
+    return st;
+}
+
+static void make_plan(pagd_solver* s) {
+    const int sms = num_sms();
+    const int n0 = s->n[0];
+    int rb = 2;
+    while (rb < n0 && n0 / rb > sms) rb *= 2;
+    int cb = 1;
+    while ((s->h1 + cb - 1) / cb > sms) cb *= 2;
+    s->rb = rb;
+    s->cb = cb;
+    const int rt = n0 / rb, ct = (s->h1 + cb - 1) / cb;
+    s->grid = rt > ct ? rt : ct;
+    if (s->grid < 1) s->grid = 1;
+    Params P = base_params(s);
+    s->smem = program_smem(P, 2 * s->tsize);
+}
+
+// ----------------------------------------------------------------- C ABI
+
+extern "C" {
+
+pagd_status pagd_default_opts(pagd_opts* o) {
+    if (!o) return PAGD_EINVAL;
+    std::memset(o, 0, sizeof(*o));
+    o->s = 0.9;
+    o->n_eta = 5;
+    for (int j = 0; j < 5; j++) o->eta[j] = std::sqrt(0.1 + 0.475 * j);
+    o->max_iter = 1000;
+    o->theta_mode = 0;
+    o->accel = 1;
+    return PAGD_OK;
+}
+
+static pagd_status init_common(pagd_solver** out, int model, int dim, const int* n, const double* L,
+                               double eps, double eta1, double eta2, double tau, double M, int scheme,
+                               int precision, const pagd_opts* opts, void* stream) {
+    if (!out) return PAGD_EINVAL;
+    *out = nullptr;
+    if (dim != 2 || !n || !L) return PAGD_EINVAL;
+    for (int d = 0; d < dim; d++) {
+        if (!pow2_ok(n[d]) || !(L[d] > 0.0) || !std::isfinite(L[d])) return PAGD_EINVAL;
+    }
+    if (!(M > 0.0) || !std::isfinite(eps)) return PAGD_EINVAL;
+    if (scheme < PAGD_BDF2 || scheme > PAGD_LMP) return PAGD_EINVAL;
+    if (precision != PAGD_FP64 && precision != PAGD_FP32_MIXED) return PAGD_EINVAL;
+    pagd_opts o;
+    if (opts) o = *opts;
+    else pagd_default_opts(&o);
+    if (!(o.s > 0.0) || o.n_eta < 1 || o.n_eta > 16 || o.max_iter < 1 || o.max_iter > 100000 ||
+        (o.theta_mode != 0 && o.theta_mode != 1) || (o.accel != 0 && o.accel != 1))
+        return PAGD_EINVAL;
+    for (int j = 0; j < o.n_eta; j++)
+        if (!(o.eta[j] > 0.0)) return PAGD_EINVAL;
+    pagd_solver* s = new (std::nothrow) pagd_solver();
+    if (!s) return PAGD_ENOMEM;
+    s->model = model;
+    s->dim = dim;
+    for (int d = 0; d < 3; d++) {
+        s->n[d] = d < dim ? n[d] : 1;
+        s->L[d] = d < dim ? L[d] : 1.0;
+    }
+    s->eps = eps;
+    s->eta1 = eta1;
+    s->eta2 = eta2;
+    s->tau = tau;
+    s->M = M;
+    s->scheme = scheme;
+    s->precision = precision;
+    s->opts = o;
+    s->stream = stream;
+    s->npts = (long long)s->n[0] * s->n[1];
+    s->h1 = s->n[1] / 2 + 1;
+    s->nslots = o.max_iter + 16 * 9 + 16;
+    s->tsize = precision == PAGD_FP64 ? 8 : 4;
+    s->ws = nullptr;
+    s->have_state = 0;
+    s->step = 0;
+    s->cur = 0;
+    s->dt_prev = 0.0;
+    plan_layout(s);
+    make_plan(s);
+    *out = s;
+    return PAGD_OK;
+}
+
+pagd_status pfc_init(pagd_solver** out, int dim, const int* n, const double* L, double eps, double M,
+                     int scheme, int precision, const pagd_opts* opts, void* stream) {
+    return init_common(out, PAGD_PFC, dim, n, L, eps, 0.0, 0.0, 0.0, M, scheme, precision, opts, stream);
+}
+
+pagd_status fch_init(pagd_solver** out, int dim, const int* n, const double* L, double eps, double eta1,
+                     double eta2, double tau, double M, int scheme, int precision, const pagd_opts* opts,
+                     void* stream) {
+    if (!std::isfinite(eta1) || !std::isfinite(eta2) || !std::isfinite(tau)) return PAGD_EINVAL;
+    return init_common(out, PAGD_FCH, dim, n, L, eps, eta1, eta2, tau, M, scheme, precision, opts, stream);
+}
+
+pagd_status pagd_workspace_size(const pagd_solver* s, size_t* bytes) {
+    if (!s || !bytes) return PAGD_EINVAL;
+    *bytes = s->ws_bytes;
+    return PAGD_OK;
+}
+
+pagd_status pagd_set_workspace(pagd_solver* s, void* dev_ptr, size_t bytes) {
+    if (!s) return PAGD_EINVAL;
+    if (!dev_ptr || ((uintptr_t)dev_ptr & 255)) return fail(s, PAGD_EINVAL, "workspace must be 256-byte aligned");
+    if (bytes < s->ws_bytes) return fail(s, PAGD_ENOMEM, "workspace smaller than pagd_workspace_size");
+    s->ws = (char*)dev_ptr;
+    s->have_state = 0;
+    // twiddles exp(-2 pi i m / kNMax) from the host libm in long double
+    std::vector<double2> t64(kNMax);
+    std::vector<float2> t32(kNMax);
+    for (int m = 0; m < kNMax; m++) {
+        const long double ang = -2.0L * 3.141592653589793238462643383279502884L * (long double)m / (long double)kNMax;
+        t64[m].x = (double)cosl(ang);
+        t64[m].y = (double)sinl(ang);
+        t32[m].x = (float)t64[m].x;
+        t32[m].y = (float)t64[m].y;
+    }
+    pagd_status st = dcopy(s, s->ws + s->off[O_TW64], t64.data(), sizeof(double2) * kNMax);
+    if (st == PAGD_OK) st = dcopy(s, s->ws + s->off[O_TW32], t32.data(), sizeof(float2) * kNMax);
+    if (st == PAGD_OK) st = dsync(s);
+    return st;
+}
+
+pagd_status pagd_set_state(pagd_solver* s, const double* u0_dev) {
+    if (!s || !u0_dev) return PAGD_EINVAL;
+    if (!s->ws) return fail(s, PAGD_ESTATE, "no workspace");
+    const size_t b = sizeof(double) * s->npts;
+    s->cur = 0;
+    pagd_status st = dcopy(s, s->ws + s->off[O_U0], u0_dev, b);
+    if (st == PAGD_OK) st = dcopy(s, s->ws + s->off[O_U1], u0_dev, b);
+    if (st == PAGD_OK) st = dsync(s);
+    if (st != PAGD_OK) return st;
+    s->have_state = 1;
+    s->step = 0;
+    s->dt_prev = 0.0;
+    return PAGD_OK;
+}
+
+static pagd_status status_from(int st) {
+    switch (st) {
+        case ST_OK: return PAGD_OK;
+        case ST_ENOCONV: return PAGD_ENOCONV;
+        case ST_EPRECOND: return PAGD_EPRECOND;
+        case ST_ENAN: return PAGD_ENAN;
+        default: return PAGD_ECUDA;
+    }
+}
+
+static pagd_status run_chunk(pagd_solver* s, double* u_out, double dt, int nsteps, double tol, int* iters,
+                             double* resid) {
+    Params P = base_params(s);
+    const bool imex = s->scheme == PAGD_LBDF2 || s->scheme == PAGD_LMP;
+    P.prog = imex ? PROG_IMEX : PROG_RUN;
+    P.tol = tol;
+    P.dt = dt;
+    P.dt_prev0 = (s->step == 0) ? dt : s->dt_prev;
+    P.nsteps = nsteps;
+    P.out_real = u_out;
+    pagd_status st = run_program(s, P);
+    if (st != PAGD_OK) return st;
+    Scal sc;
+    st = dcopy(s, &sc, P.sc, sizeof(Scal));
+    if (st == PAGD_OK) st = dsync(s);
+    if (st != PAGD_OK) return st;
+    std::vector<StepStat> stats(nsteps);
+    const int ndone = sc.steps_done;
+    const int nrec = (sc.status != ST_OK) ? ndone + 1 : ndone;
+    if (nrec > 0) {
+        st = dcopy(s, stats.data(), P.stats, sizeof(StepStat) * (size_t)(nrec < nsteps ? nrec : nsteps));
+        if (st == PAGD_OK) st = dsync(s);
+        if (st != PAGD_OK) return st;
+    }
+    for (int i = 0; i < nrec && i < nsteps; i++) {
+        if (iters) iters[i] = stats[i].iters;
+        if (resid) resid[i] = stats[i].resid;
+    }
+    if (ndone > 0) {
+        s->step += ndone;
+        s->cur ^= (ndone & 1);
+        s->dt_prev = dt;
+    }
+    if (sc.bar_error) return fail(s, PAGD_ETIMEOUT, "device barrier timed out");
+    if (sc.status != ST_OK) {
+        char buf[160];
+        std::snprintf(buf, sizeof(buf), "step %d (global %d) failed with status %d after %d evaluations",
+                      sc.fail_step, s->step, sc.status, nrec > 0 ? stats[nrec - 1].iters : 0);
+        return fail(s, status_from(sc.status), buf);
+    }
+    if (ndone != nsteps) return fail(s, PAGD_ECUDA, "kernel ended early");
+    return PAGD_OK;
+}
+
+pagd_status pagd_run(pagd_solver* s, double* u_dev, double dt, int nsteps, double tol, int* iters_out,
+                     double* resid_out) {
+    if (!s) return PAGD_EINVAL;
+    if (!s->ws || !s->have_state) return fail(s, PAGD_ESTATE, "workspace and state must be set first");
+    if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0 || !(tol >= 0.0))
+        return fail(s, PAGD_EINVAL, "bad dt / nsteps / tol");
+    int done = 0;
+    while (done < nsteps) {
+        const int c = (nsteps - done > kMaxChunk) ? kMaxChunk : nsteps - done;
+        const bool last = done + c == nsteps;
+        pagd_status st = run_chunk(s, last ? u_dev : nullptr, dt, c, tol, iters_out ? iters_out + done : nullptr,
+                                   resid_out ? resid_out + done : nullptr);
+        if (st != PAGD_OK) return st;
+        done += c;
+    }
+    return PAGD_OK;
+}
+
+pagd_status pagd_step(pagd_solver* s, double* u_dev, double dt, double tol, int* iters_out, double* resid_out) {
+    if (!u_dev) return fail(s, PAGD_EINVAL, "null output");
+    return pagd_run(s, u_dev, dt, 1, tol, iters_out, resid_out);
+}
+
+pagd_status pagd_run_host(pagd_solver* s, const double* u0_host, double* u_host_out, double dt, int nsteps,
+                          double tol, int* iters_out, double* resid_out) {
+    if (!s || !u0_host || !u_host_out) return PAGD_EINVAL;
+    if (!s->ws) return fail(s, PAGD_ESTATE, "no workspace");
+    const size_t b = sizeof(double) * s->npts;
+    s->cur = 0;
+    pagd_status st = dcopy(s, s->ws + s->off[O_U0], u0_host, b);
+    if (st == PAGD_OK) st = dcopy(s, s->ws + s->off[O_U1], u0_host, b);
+    if (st != PAGD_OK) return st;
+    s->have_state = 1;
+    s->step = 0;
+    s->dt_prev = 0.0;
+    st = pagd_run(s, nullptr, dt, nsteps, tol, iters_out, resid_out);
+    if (st != PAGD_OK) return st;
+    st = dcopy(s, u_host_out, s->ws + (s->cur ? s->off[O_U1] : s->off[O_U0]), b);
+    if (st == PAGD_OK) st = dsync(s);
+    return st;
+}
+
+pagd_status pagd_get_state(pagd_solver* s, double* un_dev, double* unm1_dev, int* step) {
+    if (!s) return PAGD_EINVAL;
+    if (!s->ws || !s->have_state) return fail(s, PAGD_ESTATE, "no state");
+    const size_t b = sizeof(double) * s->npts;
+    const size_t oc = s->cur ? s->off[O_U1] : s->off[O_U0];
+    const size_t op = s->cur ? s->off[O_U0] : s->off[O_U1];
+    pagd_status st = PAGD_OK;
+    if (un_dev) st = dcopy(s, un_dev, s->ws + oc, b);
+    if (st == PAGD_OK && unm1_dev) st = dcopy(s, unm1_dev, s->ws + op, b);
+    if (st == PAGD_OK) st = dsync(s);
+    if (step) *step = s->step;
+    return st;
+}
+
+static pagd_status reduce_program(pagd_solver* s, int prog, const double* u_dev, double* red2) {
+    Params P = base_params(s);
+    P.prog = prog;
+    P.in_real = u_dev;
+    pagd_status st = run_program(s, P);
+    if (st != PAGD_OK) return st;
+    Scal sc;
+    st = dcopy(s, &sc, P.sc, sizeof(Scal));
+    if (st == PAGD_OK) st = dsync(s);
+    if (st != PAGD_OK) return st;
+    if (sc.bar_error) return fail(s, PAGD_ETIMEOUT, "device barrier timed out");
+    red2[0] = sc.red[0];
+    red2[1] = sc.red[1];
+    return PAGD_OK;
+}
+
+pagd_status pagd_energy(pagd_solver* s, const double* u_dev, double* E) {
+    if (!s || !u_dev || !E) return PAGD_EINVAL;
+    if (!s->ws) return fail(s, PAGD_ESTATE, "no workspace");
+    double r[2];
+    pagd_status st = reduce_program(s, PROG_ENERGY, u_dev, r);
+    if (st != PAGD_OK) return st;
+    const double h = (s->L[0] / s->n[0]) * (s->L[1] / s->n[1]);
+    const double N = (double)s->npts;
+    if (s->model == PAGD_PFC) *E = h * (r[0] + r[1] / N);
+    else *E = h * r[0] - 0.5 * s->eps * s->eps * s->eta1 * h * r[1] / N;
+    return PAGD_OK;
+}
+
+pagd_status pagd_mass(pagd_solver* s, const double* u_dev, double* m) {
+    if (!s || !u_dev || !m) return PAGD_EINVAL;
+    if (!s->ws) return fail(s, PAGD_ESTATE, "no workspace");
+    double r[2];
+    pagd_status st = reduce_program(s, PROG_MASS, u_dev, r);
+    if (st != PAGD_OK) return st;
+    *m = r[0] * (s->L[0] / s->n[0]) * (s->L[1] / s->n[1]);
+    return PAGD_OK;
+}
+
+pagd_status pagd_fft_r2c(pagd_solver* s, const double* u_dev, double* spec_dev) {
+    if (!s || !u_dev || !spec_dev) return PAGD_EINVAL;
+    if (!s->ws) return fail(s, PAGD_ESTATE, "no workspace");
+    Params P = base_params(s);
+    P.prog = PROG_FFT_FWD;
+    P.in_real = u_dev;
+    P.out_spec = (double2*)spec_dev;
+    pagd_status st = run_program(s, P);
+    if (st == PAGD_OK) st = dsync(s);
+    return st;
+}
+
+pagd_status pagd_fft_c2r(pagd_solver* s, const double* spec_dev, double* u_dev) {
+    if (!s || !u_dev || !spec_dev) return PAGD_EINVAL;
+    if (!s->ws) return fail(s, PAGD_ESTATE, "no workspace");
+    Params P = base_params(s);
+    P.prog = PROG_FFT_INV;
+    P.in_spec = (const double2*)spec_dev;
+    P.out_real = u_dev;
+    pagd_status st = run_program(s, P);
+    if (st == PAGD_OK) st = dsync(s);
+    return st;
+}
+
+const char* pagd_last_error(const pagd_solver* s) { return s ? s->err.c_str() : "null solver"; }
+
+void pagd_destroy(pagd_solver* s) { delete s; }
+
+}  // extern "C"

@@ -1,0 +1,1057 @@
+// solver.cuh -- the PAGD time step as one persistent cooperative kernel.
+//
+// One launch runs a "program" (a run of time steps, a DFT, an energy or a mass
+// evaluation) as a sequence of phases separated by device-wide barriers.  Every
+// CTA evaluates the same control state machine after each barrier, so all CTAs
+// agree on the next phase without any host round trip.
+//
+// Phases are of three kinds:
+//   row pass    -- per tile of rows: optional inverse x-DFT of K_in fields from
+//                  the column-major half-spectrum buffer, a pointwise functor,
+//                  optional forward x-DFT of K_out fields back to such a buffer;
+//   column pass -- per tile of half-spectrum columns: optional forward y-DFT of
+//                  K_in fields, a per-wavenumber functor, optional inverse y-DFT
+//                  of K_out fields;
+//   pointwise   -- grid-stride over the grid points.
+//
+// The time step (Sec. 3.1.1, Sec. 3.4, Algorithm 2) is solved in a correction
+// form: v = VB + delta, where v is the scheme argument breve u (u for BDF2,
+// (u + u^n)/2 for MP, Eq. obj:MP), VB is the FP64 argument at the initial guess,
+// and the iteration runs on delta in precision T.  With theta_v = 1 (BDF2) or
+// 1/2 (MP) the PAGD recurrences in v are
+//     ybar_i = delta_i + lambda_i (delta_i - delta_{i-1}),
+//     delta_{i+1} = ybar_i + theta_v s d_i,
+// where d_i = Lcal^{-1} r_i, r_i = -G'_N(y_i) (Eq. obj:G'), which is Algorithm 2
+// rewritten with v = theta_v x + (1 - theta_v) u^n.  G'_N splits into an FP64
+// base part C0 = G'_N at VB (computed once per base) and a correction that is
+// linear in delta plus the nonlinear difference N(VB + delta) - N(VB), written
+// so that every term is proportional to delta (no cancellation in FP32).
+#pragma once
+#include "fft.cuh"
+
+namespace pagd {
+
+enum { M_PFC = 0, M_FCH = 1 };
+enum { S_BDF2 = 0, S_MP = 1, S_LBDF2 = 2, S_LMP = 3 };
+enum { P_FP64 = 0, P_MIXED = 1 };
+enum { PROG_RUN = 0, PROG_FFT_FWD = 1, PROG_FFT_INV = 2, PROG_ENERGY = 3, PROG_MASS = 4,
+       PROG_IMEX = 5 };
+enum { ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ECUDA = 3, ST_ENOCONV = 4, ST_EPRECOND = 5,
+       ST_ENAN = 6, ST_ESTATE = 7, ST_ETIMEOUT = 8 };
+enum { FLAG_PRECOND = 1 };
+
+enum Phase {
+    PH_A, PH_B, PH_C, PH_D, PH_E, PH_R1, PH_CI, PH_RI, PH_REBASE, PH_ACCEPT, PH_FAIL,
+    PH_FWD_R, PH_FWD_C, PH_INV_C, PH_INV_R, PH_EN_R, PH_EN_C, PH_EN_R2, PH_MASS,
+    PH_IM_A, PH_IM_R0, PH_IM_C0, PH_IM_R1, PH_IM_C1, PH_IM_R2, PH_IM_ACCEPT,
+    PH_DONE
+};
+
+// device-resident scalars; zeroed by the host before every launch
+struct Scal {
+    unsigned bar_count, bar_gen;
+    int bar_error, flags;
+    int status, steps_done, fail_step, pad;
+    double beta_sum[2];
+    double red[4];
+};
+
+struct StepStat {
+    int iters, status;
+    double resid;
+};
+
+constexpr int kMaxK = 3;        // fields per pass
+constexpr int kThreads = 256;   // CTA size of the persistent kernel
+
+struct Params {
+    int model, scheme, precision, prog;
+    int n0, n1, logn0, logn1, h1;
+    long long npts;
+    int rb, cb;          // rows per row tile, columns per column tile
+    double k0sq, k1sq;   // (2 pi / L0)^2, (2 pi / L1)^2
+    double cellvol;      // h0 h1
+    double eps, eta1, eta2, tau, M;
+    double s;
+    int n_eta, accel, max_iter, max_recheck, theta_mode, pad0;
+    double lam[16];      // (1 - eta_j sqrt s) / (1 + eta_j sqrt s)
+    double tol, dt, dt_prev0;
+    int step0, nsteps, cur0, nslots;
+    // workspace
+    double* U[2];
+    double* VB;
+    double* G64;
+    void* VBt;
+    void* LBt;
+    void* DD[2];
+    void* SS[2];
+    void* C0;
+    void* NB;
+    void* DB;
+    double2* CL64;
+    double2* NB64;
+    double2* DB64;
+    const double2* tw64;
+    const float2* tw32;
+    Scal* sc;
+    unsigned long long* norms;
+    double* sums;
+    StepStat* stats;
+    // program input / output
+    const double* in_real;
+    double* out_real;
+    const double2* in_spec;
+    double2* out_spec;
+};
+
+struct Ctl {
+    int ph, step, it, ev, lastev, cur, rech, fail, best_ev, pad;
+    double resid, base_nrm, best_nrm;
+};
+
+// FP32 iterations stop improving once ||d|| reaches about 1e-7 of the FP64
+// direction at the base point (the FP32 rounding of C0); the base is moved
+// before that floor is reached.
+constexpr double kRebaseRatio = 1.0e-6;
+constexpr int kStagnation = 12;
+
+template <class T> __device__ __forceinline__ const cx<T>* twiddles(const Params& P);
+template <> __device__ __forceinline__ const cx<double>* twiddles<double>(const Params& P) { return P.tw64; }
+template <> __device__ __forceinline__ const cx<float>* twiddles<float>(const Params& P) { return P.tw32; }
+
+// ---------------------------------------------------------------- helpers
+
+struct StepK {
+    double a, b, c, thv, ts, Ai, rho, gun, thpc;
+};
+
+// Scheme coefficients a_n, b_n, c_n (Eqs. obj:BDF2, obj:MP; backward Euler /
+// its IMEX version for the first BDF2 / LBDF2 step, Algorithm 3 caption), the
+// weight theta_v of the new iterate in breve u, and the extrapolation ratio rho.
+__device__ __forceinline__ StepK step_coeffs(const Params& P, int step) {
+    StepK k;
+    const int n = P.step0 + step;
+    const double dt = P.dt;
+    const double dtp = (step == 0) ? P.dt_prev0 : P.dt;
+    const bool bdf = (P.scheme == S_BDF2 || P.scheme == S_LBDF2);
+    if (!bdf || n == 0) {
+        k.a = 1.0 / dt; k.b = -1.0 / dt; k.c = 0.0;
+    } else {
+        k.a = 1.0 / dt + 1.0 / (dt + dtp);
+        k.b = -1.0 / dt - 1.0 / dtp;
+        k.c = 1.0 / dtp - 1.0 / (dt + dtp);
+    }
+    k.thv = (P.scheme == S_MP) ? 0.5 : 1.0;
+    k.ts = k.thv * P.s;
+    k.Ai = k.a / k.thv;
+    k.rho = (n == 0) ? 0.0 : dt / dtp;
+    k.gun = k.a * (1.0 - k.thv) / k.thv;
+    k.thpc = (P.scheme == S_MP && P.theta_mode == 0) ? 0.5 : 1.0;
+    return k;
+}
+
+struct Beta {
+    double m2, b0, b2, b4;
+};
+
+// Averaged Newton constants (Sec. 3.4.1) from the grid sums over the argument
+// of the initial guess.
+__device__ __forceinline__ Beta betas(const Params& P, const StepK& k) {
+    Beta B;
+    const double inv = 1.0 / (double)P.npts;
+    B.m2 = k.a / P.M;
+    const double s0 = ldcg(&P.sc->beta_sum[0]) * inv;
+    if (P.model == M_PFC) {
+        B.b0 = k.thpc * fabs(s0);
+        B.b2 = -2.0 * k.thpc;
+        B.b4 = k.thpc;
+    } else {
+        const double s2 = ldcg(&P.sc->beta_sum[1]) * inv;
+        const double e2 = P.eps * P.eps;
+        B.b0 = k.thpc * fabs(s0);
+        B.b2 = k.thpc * fabs(s2);
+        B.b4 = k.thpc * e2 * e2;
+    }
+    return B;
+}
+
+__device__ __forceinline__ double lam_at(const Params& P, int i) {
+    return P.accel ? P.lam[i % P.n_eta] : 0.0;
+}
+
+// kappa = |k|^2 at half-spectrum index (k1 column, k0 row)
+__device__ __forceinline__ double kappa_at(const Params& P, int k1, int k0) {
+    const int r0 = (k0 <= (P.n0 >> 1)) ? k0 : k0 - P.n0;
+    return P.k1sq * (double)k1 * (double)k1 + P.k0sq * (double)r0 * (double)r0;
+}
+
+// double well derivatives, expanded: F'(z) = (z^2 - 1)(z + tau),
+// F''(z) = 3 z^2 + 2 tau z - 1, F'''(z) = 6 z + 2 tau, and
+// F(z) = z^4/4 + tau z^3/3 - z^2/2 - tau z + (1/2 - 4 tau/3)/2.
+template <class T> __device__ __forceinline__ T dF1(T z, T tau) { return (z * z - (T)1) * (z + tau); }
+template <class T> __device__ __forceinline__ T dF2(T z, T tau) { return (T)3 * z * z + (T)2 * tau * z - (T)1; }
+template <class T> __device__ __forceinline__ T dF3(T z, T tau) { return (T)6 * z + (T)2 * tau; }
+__device__ __forceinline__ double Fwell(double z, double tau) {
+    return 0.25 * z * z * z * z + tau * z * z * z / 3.0 - 0.5 * z * z - tau * z +
+           0.5 * (0.5 - 4.0 * tau / 3.0);
+}
+
+__device__ __forceinline__ double nanmax(double a, double b) { return (b > a || b != b) ? b : a; }
+
+// block-wide reductions; the result is valid in thread 0
+__device__ __forceinline__ double block_max(double v, double* red) {
+#ifdef PAGD_EMU
+    (void)red;
+    return v;
+#else
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_max(v);
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (lane < nw) ? red[lane] : 0.0;
+        v = warp_max(v);
+    }
+    return v;
+#endif
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#ifdef PAGD_EMU
+    (void)red;
+    return v;
+#else
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (lane < nw) ? red[lane] : 0.0;
+        v = warp_sum(v);
+    }
+    return v;
+#endif
+}
+
+// ---------------------------------------------------------- pass templates
+
+__host__ __device__ __forceinline__ int pitch_of(int n) { return n + 2; }
+
+// shared memory bytes of a row pass / column pass
+__host__ __device__ __forceinline__ size_t row_smem(int n1, int rb, int kin, int szin, int kout,
+                                                    int szout) {
+    const size_t pitch = (size_t)pitch_of(n1);
+    return 2 * (size_t)(kin * rb / 2) * pitch * szin + 2 * (size_t)(kout * rb / 2) * pitch * szout;
+}
+__host__ __device__ __forceinline__ size_t col_smem(int n0, int cb, int kin, int szin, int kout,
+                                                    int szout) {
+    const size_t pitch = (size_t)pitch_of(n0);
+    return 2 * (size_t)(kin * cb) * pitch * szin + 2 * (size_t)(kout * cb) * pitch * szout;
+}
+
+// Row pass.  src/dst: column-major half spectra, field f, column k1, row r at
+// f*h1*n0 + k1*n0 + r.  Real line l = f*rb + rr of a tile; lines 2j and 2j+1 are
+// packed as the real and imaginary part of complex line j.
+// fn(p, row, x, const TI* in, TO* out) handles one grid point.
+template <class TI, class TO, class Fn>
+__device__ void row_pass(const Params& P, int kin, int kout, const cx<TI>* src, cx<TO>* dst,
+                         char* smem, Fn&& fn) {
+    using CI = cx<TI>;
+    using CO = cx<TO>;
+    const int n0 = P.n0, n1 = P.n1, h1 = P.h1, rb = P.rb, logn1 = P.logn1;
+    const int pitch = pitch_of(n1);
+    const int xl = kin * rb / 2, yl = kout * rb / 2;
+    CI* X0 = (CI*)smem;
+    CI* X1 = X0 + (size_t)xl * pitch;
+    CO* Y0 = (CO*)(X1 + (size_t)xl * pitch);
+    CO* Y1 = Y0 + (size_t)yl * pitch;
+    const TI iscale = (TI)(1.0 / ((double)n0 * (double)n1));
+    const int ntiles = n0 / rb;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int r0 = tile * rb;
+        CI* Xr = X0;
+        if (kin > 0) {
+            // stage the half spectra of every real line: X1[l * h1 + k]
+            const int tot = kin * h1 * rb;
+            for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+                const int rr = t % rb;
+                const int k = (t / rb) % h1;
+                const int f = t / (rb * h1);
+                X1[(size_t)(f * rb + rr) * h1 + k] = src[(size_t)f * h1 * n0 + (size_t)k * n0 + r0 + rr];
+            }
+            __syncthreads();
+            // Z_j = A + i B on the full circle, A/B the spectra of lines 2j, 2j+1
+            const int tz = xl * n1;
+            for (int t = threadIdx.x; t < tz; t += blockDim.x) {
+                const int j = t >> logn1;
+                const int x = t & (n1 - 1);
+                const CI* sa = X1 + (size_t)(2 * j) * h1;
+                const CI* sb = sa + h1;
+                CI z;
+                if (x <= (n1 >> 1)) {
+                    CI A = sa[x], B = sb[x];
+                    if (x == 0 || x == (n1 >> 1)) { A.y = 0; B.y = 0; }
+                    z = CI{A.x - B.y, A.y + B.x};
+                } else {
+                    const CI A = sa[n1 - x], B = sb[n1 - x];
+                    z = CI{A.x + B.y, B.x - A.y};
+                }
+                X0[(size_t)j * pitch + x] = z;
+            }
+            const int res = fft_lines<+1, TI>(X0, X1, logn1, xl, pitch, twiddles<TI>(P));
+            Xr = res ? X1 : X0;
+        }
+        // pointwise
+        const int tp = rb * n1;
+        for (int t = threadIdx.x; t < tp; t += blockDim.x) {
+            const int rr = t >> logn1;
+            const int x = t & (n1 - 1);
+            TI in[kMaxK];
+            TO out[kMaxK];
+            for (int f = 0; f < kin; f++) {
+                const int l = f * rb + rr;
+                const CI z = Xr[(size_t)(l >> 1) * pitch + x];
+                in[f] = ((l & 1) ? z.y : z.x) * iscale;
+            }
+            const long long p = (long long)(r0 + rr) * n1 + x;
+            fn(p, r0 + rr, x, in, out);
+            for (int g = 0; g < kout; g++) {
+                const int l = g * rb + rr;
+                CO* q = Y0 + (size_t)(l >> 1) * pitch + x;
+                if (l & 1) q->y = out[g];
+                else q->x = out[g];
+            }
+        }
+        if (kout > 0) {
+            const int res = fft_lines<-1, TO>(Y0, Y1, logn1, yl, pitch, twiddles<TO>(P));
+            const CO* Yr = res ? Y1 : Y0;
+            const TO half = (TO)0.5;
+            const int tot = kout * h1 * rb;
+            for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+                const int rr = t % rb;
+                const int k = (t / rb) % h1;
+                const int g = t / (rb * h1);
+                const int l = g * rb + rr;
+                const CO* zl = Yr + (size_t)(l >> 1) * pitch;
+                const CO zk = zl[k];
+                const CO zn = zl[(n1 - k) & (n1 - 1)];
+                CO v;
+                if ((l & 1) == 0) v = CO{half * (zk.x + zn.x), half * (zk.y - zn.y)};
+                else v = CO{half * (zk.y + zn.y), half * (zn.x - zk.x)};
+                dst[(size_t)g * h1 * n0 + (size_t)k * n0 + r0 + rr] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Column pass over half-spectrum columns k1 in [0, h1).  fn(k1, k0, in, out).
+template <class TI, class TO, class Fn>
+__device__ void col_pass(const Params& P, int kin, int kout, const cx<TI>* src, cx<TO>* dst,
+                         char* smem, Fn&& fn) {
+    using CI = cx<TI>;
+    using CO = cx<TO>;
+    const int n0 = P.n0, h1 = P.h1, cb = P.cb, logn0 = P.logn0;
+    const int pitch = pitch_of(n0);
+    CI* X0 = (CI*)smem;
+    CI* X1 = X0 + (size_t)(kin * cb) * pitch;
+    CO* Y0 = (CO*)(X1 + (size_t)(kin * cb) * pitch);
+    CO* Y1 = Y0 + (size_t)(kout * cb) * pitch;
+    const int ntiles = (h1 + cb - 1) / cb;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int k10 = tile * cb;
+        const int cc = (h1 - k10 < cb) ? (h1 - k10) : cb;
+        const CI* Xr = X0;
+        if (kin > 0) {
+            const int tot = kin * cc * n0;
+            for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+                const int k0 = t & (n0 - 1);
+                const int kk = (t >> logn0) % cc;
+                const int f = (t >> logn0) / cc;
+                X0[(size_t)(f * cc + kk) * pitch + k0] = src[(size_t)f * h1 * n0 + (size_t)(k10 + kk) * n0 + k0];
+            }
+            const int res = fft_lines<-1, TI>(X0, X1, logn0, kin * cc, pitch, twiddles<TI>(P));
+            Xr = res ? X1 : X0;
+        }
+        const int tp = cc * n0;
+        for (int t = threadIdx.x; t < tp; t += blockDim.x) {
+            const int kk = t >> logn0;
+            const int k0 = t & (n0 - 1);
+            CI in[kMaxK];
+            CO out[kMaxK];
+            for (int f = 0; f < kin; f++) in[f] = Xr[(size_t)(f * cc + kk) * pitch + k0];
+            fn(k10 + kk, k0, in, out);
+            for (int g = 0; g < kout; g++) Y0[(size_t)(g * cc + kk) * pitch + k0] = out[g];
+        }
+        if (kout > 0) {
+            const int res = fft_lines<+1, TO>(Y0, Y1, logn0, kout * cc, pitch, twiddles<TO>(P));
+            const CO* Yr = res ? Y1 : Y0;
+            const int tot = kout * cc * n0;
+            for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+                const int k0 = t & (n0 - 1);
+                const int kk = (t >> logn0) % cc;
+                const int g = (t >> logn0) / cc;
+                dst[(size_t)g * h1 * n0 + (size_t)(k10 + kk) * n0 + k0] = Yr[(size_t)(g * cc + kk) * pitch + k0];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ phase bodies
+
+// number of fields in the iteration passes: PFC transforms v^3 differences and
+// inverts d; FCH transforms (dF', dP) and inverts (d, Lap ybar)
+__host__ __device__ __forceinline__ int k_iter(int model) { return model == M_PFC ? 1 : 2; }
+__host__ __device__ __forceinline__ int k_base(int model) { return model == M_PFC ? 3 : 2; }
+
+// Phase A: initial guess (Sec. 3.4.2: extrapolation of the two previous
+// solutions), base argument VB, history term g, preconditioner sums.
+template <class T>
+__device__ void phase_A(const Params& P, const Ctl& c, double* red) {
+    const StepK k = step_coeffs(P, c.step);
+    const double* un = P.U[c.cur];
+    const double* um = P.U[c.cur ^ 1];
+    T* vbt = (T*)P.VBt;
+    T* d0 = (T*)P.DD[0];
+    T* d1 = (T*)P.DD[1];
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gs = (long long)gridDim.x * blockDim.x;
+    for (long long q = gt; q < P.nslots; q += gs) {
+        P.norms[q] = 0ull;
+        P.sums[q] = 0.0;
+    }
+    double s0 = 0.0, s2 = 0.0;
+    const double e2 = P.eps * P.eps;
+    for (long long p = gt; p < P.npts; p += gs) {
+        const double a = un[p], b = um[p];
+        const double x0 = a + k.rho * (a - b);
+        const double vb = k.thv * x0 + (1.0 - k.thv) * a;
+        P.VB[p] = vb;
+        P.G64[p] = k.b * a + k.c * b - k.gun * a;
+        vbt[p] = (T)vb;
+        d0[p] = (T)0;
+        d1[p] = (T)0;
+        if (P.model == M_PFC) {
+            s0 += 3.0 * vb * vb + 1.0 - P.eps;
+        } else {
+            const double f1 = dF1(vb, P.tau), f2 = dF2(vb, P.tau), f3 = dF3(vb, P.tau);
+            s0 += f2 * f2 - P.eta2 * f2 + f3 * f1;
+            s2 += e2 * (f2 - P.eta1);
+        }
+    }
+    s0 = block_sum(s0, red);
+    if (threadIdx.x == 0) atomicAdd(&P.sc->beta_sum[0], s0);
+    if (P.model == M_FCH) {
+        s2 = block_sum(s2, red);
+        if (threadIdx.x == 0) atomicAdd(&P.sc->beta_sum[1], s2);
+    }
+}
+
+// Phase B: forward x-DFT of the FP64 base fields (VB, g[, VB^3]).
+__device__ void phase_B(const Params& P, char* smem) {
+    const int kb = k_base(P.model);
+    const bool pfc = P.model == M_PFC;
+    row_pass<double, double>(P, 0, kb, (const double2*)nullptr, P.NB64, smem,
+                             [&](long long p, int, int, const double*, double* out) {
+                                 const double vb = P.VB[p];
+                                 out[0] = vb;
+                                 out[1] = P.G64[p];
+                                 if (pfc) out[2] = vb * vb * vb;
+                             });
+}
+
+// Spectral base gradient C0 = G'_N(VB) (Eqs. misc07 / obj:G'), its
+// preconditioned direction d0 and the first correction delta_1 = theta_v s d0.
+template <class T>
+__device__ __forceinline__ void base_direction(const Params& P, const StepK& k, const Beta& B,
+                                               int k1, int k0, double kap, double2 G, double2& d) {
+    const long long idx = (long long)k1 * P.n0 + k0;
+    cx<T>* C0 = (cx<T>*)P.C0;
+    cx<T>* S0 = (cx<T>*)P.SS[0];
+    cx<T>* S1 = (cx<T>*)P.SS[1];
+    if (kap == 0.0) {
+        G = double2{0.0, 0.0};
+        d = double2{0.0, 0.0};
+    } else {
+        const double Lk = B.m2 / kap + B.b0 + B.b2 * kap + B.b4 * kap * kap;
+        if (!(Lk > 0.0)) atomicOr(&P.sc->flags, FLAG_PRECOND);
+        d = double2{-G.x / Lk, -G.y / Lk};
+    }
+    C0[idx] = cx<T>{(T)G.x, (T)G.y};
+    S0[idx] = cx<T>{(T)0, (T)0};
+    S1[idx] = cx<T>{(T)(k.ts * d.x), (T)(k.ts * d.y)};
+}
+
+template <class T>
+__device__ void phase_C(const Params& P, const Ctl& c, char* smem) {
+    const StepK k = step_coeffs(P, c.step);
+    const Beta B = betas(P, k);
+    const int kb = k_base(P.model);
+    const double iM = 1.0 / P.M;
+    const double e4 = P.eps * P.eps * P.eps * P.eps;
+    if (P.model == M_PFC) {
+        col_pass<double, double>(P, kb, 1, P.NB64, P.DB64, smem,
+                                 [&](int k1, int k0, const double2* in, double2* out) {
+                                     const double kap = kappa_at(P, k1, k0);
+                                     const double2 v = in[0], g = in[1], nl = in[2];
+                                     double2 G{0.0, 0.0};
+                                     if (kap != 0.0) {
+                                         const double Lh = 1.0 - P.eps - 2.0 * kap + kap * kap;
+                                         const double ik = iM / kap;
+                                         G.x = (k.Ai * v.x + g.x) * ik + Lh * v.x + nl.x;
+                                         G.y = (k.Ai * v.y + g.y) * ik + Lh * v.y + nl.y;
+                                     }
+                                     double2 d;
+                                     base_direction<T>(P, k, B, k1, k0, kap, G, d);
+                                     out[0] = d;
+                                 });
+    } else {
+        col_pass<double, double>(P, kb, 1, P.NB64, P.DB64, smem,
+                                 [&](int k1, int k0, const double2* in, double2* out) {
+                                     const double kap = kappa_at(P, k1, k0);
+                                     const double2 v = in[0], g = in[1];
+                                     double2 G{0.0, 0.0};
+                                     if (kap != 0.0) {
+                                         const double ik = iM / kap;
+                                         G.x = (k.Ai * v.x + g.x) * ik + e4 * kap * kap * v.x;
+                                         G.y = (k.Ai * v.y + g.y) * ik + e4 * kap * kap * v.y;
+                                     }
+                                     P.CL64[(long long)k1 * P.n0 + k0] = G;
+                                     out[0] = double2{-kap * v.x, -kap * v.y};
+                                 });
+    }
+}
+
+// FCH: physical Lap VB, then forward x-DFT of (F'(VB), P(VB)) where
+// P = -eps^2 (F'' - eta1) Lap v + (F'' - eta2) F'  (the non-Laplacian part of mu).
+template <class T>
+__device__ void phase_D(const Params& P, char* smem) {
+    T* lbt = (T*)P.LBt;
+    const double e2 = P.eps * P.eps;
+    row_pass<double, double>(P, 1, 2, P.DB64, P.NB64, smem,
+                             [&](long long p, int, int, const double* in, double* out) {
+                                 const double lb = in[0];
+                                 lbt[p] = (T)lb;
+                                 const double vb = P.VB[p];
+                                 const double f1 = dF1(vb, P.tau), f2 = dF2(vb, P.tau);
+                                 out[0] = f1;
+                                 out[1] = -e2 * (f2 - P.eta1) * lb + (f2 - P.eta2) * f1;
+                             });
+}
+
+template <class T>
+__device__ void phase_E(const Params& P, const Ctl& c, char* smem) {
+    const StepK k = step_coeffs(P, c.step);
+    const Beta B = betas(P, k);
+    const double e2 = P.eps * P.eps;
+    const double l1 = lam_at(P, 1);
+    col_pass<double, double>(P, 2, 2, P.NB64, P.DB64, smem,
+                             [&](int k1, int k0, const double2* in, double2* out) {
+                                 const double kap = kappa_at(P, k1, k0);
+                                 const double2 lin = P.CL64[(long long)k1 * P.n0 + k0];
+                                 double2 G{0.0, 0.0};
+                                 if (kap != 0.0) {
+                                     G.x = lin.x + e2 * kap * in[0].x + in[1].x;
+                                     G.y = lin.y + e2 * kap * in[0].y + in[1].y;
+                                 }
+                                 double2 d;
+                                 base_direction<T>(P, k, B, k1, k0, kap, G, d);
+                                 out[0] = d;
+                                 const double f = -kap * (1.0 + l1) * k.ts;
+                                 out[1] = double2{f * d.x, f * d.y};
+                             });
+}
+
+// Iteration row pass (R1 reads the FP64 base direction, RI the T one):
+// delta_it = ybar_{it-1} + theta_v s d_{it-1}; ||d_{it-1}||_inf; then the
+// nonlinear differences at ybar_it and their forward x-DFT.
+template <class TI, class T>
+__device__ void phase_R(const Params& P, const Ctl& c, char* smem, double* red,
+                        const cx<TI>* src) {
+    const StepK k = step_coeffs(P, c.step);
+    const int it = c.it;
+    const T lp = (T)lam_at(P, it - 1), l = (T)lam_at(P, it), ts = (T)k.ts;
+    T* dcur = (T*)P.DD[it & 1];
+    const T* dprev = (const T*)P.DD[(it - 1) & 1];
+    const T* vbt = (const T*)P.VBt;
+    const T* lbt = (const T*)P.LBt;
+    const int K = k_iter(P.model);
+    const T tau = (T)P.tau, e2 = (T)(P.eps * P.eps), eta1 = (T)P.eta1, eta2 = (T)P.eta2;
+    double amax = 0.0, asum = 0.0;
+    const bool pfc = P.model == M_PFC;
+    row_pass<TI, T>(P, K, K, src, (cx<T>*)P.NB, smem,
+                    [&](long long p, int, int, const TI* in, T* out) {
+                        const TI dd = in[0];
+                        const T dp = dprev[p], dpp = dcur[p];
+                        const T de = dp + lp * (dp - dpp) + ts * (T)dd;
+                        dcur[p] = de;
+                        amax = nanmax(amax, fabs((double)dd));
+                        asum += (double)de;
+                        const T y = de + l * (de - dp);
+                        const T b = vbt[p];
+                        if (pfc) {
+                            out[0] = y * ((T)3 * b * b + (T)3 * b * y + y * y);
+                        } else {
+                            const T lb = lbt[p];
+                            const T ly = (T)in[1];
+                            const T f1b = dF1(b, tau), f2b = dF2(b, tau);
+                            const T df1 = y * ((T)3 * b * b + (T)3 * b * y + y * y + tau * ((T)2 * b + y) - (T)1);
+                            const T df2 = y * ((T)6 * b + (T)3 * y + (T)2 * tau);
+                            const T f1n = f1b + df1, f2n = f2b + df2;
+                            out[0] = df1;
+                            out[1] = -e2 * (df2 * lb + (f2n - eta1) * ly) + df2 * f1n + (f2b - eta2) * df1;
+                        }
+                    });
+    amax = block_max(amax, red);
+    if (threadIdx.x == 0) atomicMax(&P.norms[c.ev], dbl_bits(amax));
+    asum = block_sum(asum, red);
+    if (threadIdx.x == 0) atomicAdd(&P.sums[c.ev], asum);
+}
+
+// Iteration column pass: ybar_hat, spectral residual (Eq. obj:G' with the
+// zero mode removed), d_hat = r_hat / Lcal_hat (Algorithm 2), the spectral
+// state update, and the inverse y-DFT of d (and of Lap ybar_{it+1} for FCH).
+template <class T>
+__device__ void phase_CI(const Params& P, const Ctl& c, char* smem) {
+    using C = cx<T>;
+    const StepK k = step_coeffs(P, c.step);
+    const Beta B = betas(P, k);
+    const int it = c.it;
+    const T l = (T)lam_at(P, it), ln = (T)lam_at(P, it + 1), ts = (T)k.ts;
+    const C* scur = (const C*)P.SS[it & 1];
+    C* sprev = (C*)P.SS[(it - 1) & 1];
+    const C* C0 = (const C*)P.C0;
+    const int K = k_iter(P.model);
+    const bool pfc = P.model == M_PFC;
+    const double iM = 1.0 / P.M, e2 = P.eps * P.eps, e4 = e2 * e2;
+    col_pass<T, T>(P, K, K, (const C*)P.NB, (C*)P.DB, smem,
+                   [&](int k1, int k0, const C* in, C* out) {
+                       const long long idx = (long long)k1 * P.n0 + k0;
+                       const double kap = kappa_at(P, k1, k0);
+                       const C sc = scur[idx], sp = sprev[idx];
+                       const C yh = C{sc.x + l * (sc.x - sp.x), sc.y + l * (sc.y - sp.y)};
+                       C d{(T)0, (T)0};
+                       if (kap != 0.0) {
+                           const C g0 = C0[idx];
+                           const double Lk = B.m2 / kap + B.b0 + B.b2 * kap + B.b4 * kap * kap;
+                           const T il = (T)(-1.0 / Lk);
+                           if (pfc) {
+                               const T m = (T)(k.Ai * iM / kap + 1.0 - P.eps - 2.0 * kap + kap * kap);
+                               d.x = il * (g0.x + m * yh.x + in[0].x);
+                               d.y = il * (g0.y + m * yh.y + in[0].y);
+                           } else {
+                               const T m = (T)(k.Ai * iM / kap + e4 * kap * kap);
+                               const T e2k = (T)(e2 * kap);
+                               d.x = il * (g0.x + m * yh.x + e2k * in[0].x + in[1].x);
+                               d.y = il * (g0.y + m * yh.y + e2k * in[0].y + in[1].y);
+                           }
+                       }
+                       const C sn = C{yh.x + ts * d.x, yh.y + ts * d.y};
+                       sprev[idx] = sn;
+                       out[0] = d;
+                       if (!pfc) {
+                           const T f = (T)(-kap);
+                           out[1] = C{f * (sn.x + ln * (sn.x - sc.x)), f * (sn.y + ln * (sn.y - sc.y))};
+                       }
+                   });
+}
+
+// Mixed precision: move the base to the candidate (FP64), clear the correction.
+template <class T>
+__device__ void phase_rebase(const Params& P, const Ctl& c) {
+    T* dc = (T*)P.DD[c.it & 1];
+    T* d0 = (T*)P.DD[0];
+    T* d1 = (T*)P.DD[1];
+    T* vbt = (T*)P.VBt;
+    const double m = ldcg(&P.sums[c.lastev]) / (double)P.npts;
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gs = (long long)gridDim.x * blockDim.x;
+    for (long long p = gt; p < P.npts; p += gs) {
+        const double v = P.VB[p] + ((double)dc[p] - m);
+        P.VB[p] = v;
+        vbt[p] = (T)v;
+        d0[p] = (T)0;
+        d1[p] = (T)0;
+    }
+}
+
+// Accept: u^{n+1} = (VB + delta - (1 - theta_v) u^n) / theta_v, written over
+// u^{n-1}; the mean of delta (zero in exact arithmetic, Remark on discrete mass
+// conservation) is removed in FP64.
+template <class T>
+__device__ void phase_accept(const Params& P, const Ctl& c) {
+    const StepK k = step_coeffs(P, c.step);
+    const T* dc = (const T*)P.DD[c.it & 1];
+    const double* un = P.U[c.cur];
+    double* unew = P.U[c.cur ^ 1];
+    const double m = ldcg(&P.sums[c.lastev]) / (double)P.npts;
+    const bool last = (c.step + 1 == P.nsteps) && P.out_real;
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gs = (long long)gridDim.x * blockDim.x;
+    const double ith = 1.0 / k.thv, w = (1.0 - k.thv);
+    for (long long p = gt; p < P.npts; p += gs) {
+        const double v = P.VB[p] + ((double)dc[p] - m);
+        const double x = (v - w * un[p]) * ith;
+        unew[p] = x;
+        if (last) P.out_real[p] = x;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.stats[c.step].iters = c.ev;
+        P.stats[c.step].status = ST_OK;
+        P.stats[c.step].resid = c.resid;
+        P.sc->beta_sum[0] = 0.0;
+        P.sc->beta_sum[1] = 0.0;
+        P.sc->steps_done = c.step + 1;
+    }
+}
+
+__device__ void phase_fail(const Params& P, const Ctl& c) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.sc->status = c.fail;
+        P.sc->fail_step = c.step;
+        P.stats[c.step].iters = c.ev;
+        P.stats[c.step].status = c.fail;
+        P.stats[c.step].resid = c.resid;
+    }
+}
+
+// ------------------------------------------------ DFT / energy / mass programs
+
+__device__ void phase_fwd_r(const Params& P, char* smem) {
+    row_pass<double, double>(P, 0, 1, (const double2*)nullptr, P.NB64, smem,
+                             [&](long long p, int, int, const double*, double* out) {
+                                 out[0] = P.in_real[p];
+                             });
+}
+__device__ void phase_fwd_c(const Params& P, char* smem) {
+    col_pass<double, double>(P, 1, 0, P.NB64, (double2*)nullptr, smem,
+                             [&](int k1, int k0, const double2* in, double2*) {
+                                 P.out_spec[(long long)k0 * P.h1 + k1] = in[0];
+                             });
+}
+__device__ void phase_inv_c(const Params& P, char* smem) {
+    col_pass<double, double>(P, 0, 1, (const double2*)nullptr, P.DB64, smem,
+                             [&](int k1, int k0, const double2*, double2* out) {
+                                 out[0] = P.in_spec[(long long)k0 * P.h1 + k1];
+                             });
+}
+__device__ void phase_inv_r(const Params& P, char* smem) {
+    row_pass<double, double>(P, 1, 0, P.DB64, (double2*)nullptr, smem,
+                             [&](long long p, int, int, const double* in, double*) {
+                                 P.out_real[p] = in[0];
+                             });
+}
+
+// energy (Eqs. obj:PFC-egy / obj:FCHegy with Fourier differentiation and the
+// trapezoidal rule): red[0] pointwise part, red[1] spectral part
+__device__ void phase_en_r(const Params& P, char* smem, double* red) {
+    double acc = 0.0;
+    const bool pfc = P.model == M_PFC;
+    row_pass<double, double>(P, 0, 1, (const double2*)nullptr, P.NB64, smem,
+                             [&](long long p, int, int, const double*, double* out) {
+                                 const double u = P.in_real[p];
+                                 out[0] = u;
+                                 if (pfc) acc += 0.25 * u * u * u * u + 0.5 * (1.0 - P.eps) * u * u;
+                             });
+    if (pfc) {
+        acc = block_sum(acc, red);
+        if (threadIdx.x == 0) atomicAdd(&P.sc->red[0], acc);
+    }
+}
+__device__ void phase_en_c(const Params& P, char* smem, double* red) {
+    double acc = 0.0;
+    const bool pfc = P.model == M_PFC;
+    const int half = P.n1 >> 1;
+    col_pass<double, double>(P, 1, pfc ? 0 : 1, P.NB64, P.DB64, smem,
+                             [&](int k1, int k0, const double2* in, double2* out) {
+                                 const double kap = kappa_at(P, k1, k0);
+                                 const double w = (k1 == 0 || k1 == half) ? 1.0 : 2.0;
+                                 const double a2 = in[0].x * in[0].x + in[0].y * in[0].y;
+                                 if (pfc) {
+                                     acc += w * (-kap + 0.5 * kap * kap) * a2;
+                                 } else {
+                                     acc += w * kap * a2;
+                                     out[0] = double2{-kap * in[0].x, -kap * in[0].y};
+                                 }
+                             });
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) atomicAdd(&P.sc->red[1], acc);
+}
+__device__ void phase_en_r2(const Params& P, char* smem, double* red) {
+    double acc = 0.0;
+    const double e2 = P.eps * P.eps;
+    row_pass<double, double>(P, 1, 0, P.DB64, (double2*)nullptr, smem,
+                             [&](long long p, int, int, const double* in, double*) {
+                                 const double u = P.in_real[p];
+                                 const double w = e2 * in[0] - dF1(u, P.tau);
+                                 acc += 0.5 * w * w - P.eta2 * Fwell(u, P.tau);
+                             });
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) atomicAdd(&P.sc->red[0], acc);
+}
+__device__ void phase_mass(const Params& P, double* red) {
+    double acc = 0.0;
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gs = (long long)gridDim.x * blockDim.x;
+    for (long long p = gt; p < P.npts; p += gs) acc += P.in_real[p];
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) atomicAdd(&P.sc->red[0], acc);
+}
+
+// ------------------------------------------------------ linear IMEX step
+//
+// Eq. eqn:FCH-semidis-simplicit with the splits of Sec. 3.1.1, solved per
+// wavenumber (Sec. 3.3), in FP64:
+//   IM_A : ubreve (extrapolation) pointwise -> stored in VB
+//   IM_R0: forward x-DFT of (ubreve, u^n, u^{n-1})
+//   IM_C0: (PFC) solve directly; (FCH) keep spectra, inverse y-DFT of -kappa ubreve
+//   IM_R1: (FCH) Lap ubreve physical, forward x-DFT of (F'(ub), Q(ub))
+//   IM_C1: (FCH) solve
+//   IM_R2: inverse x-DFT of u^{n+1} -> written over u^{n-1}
+__device__ void phase_im_a(const Params& P, const Ctl& c) {
+    const StepK k = step_coeffs(P, c.step);
+    const double* un = P.U[c.cur];
+    const double* um = P.U[c.cur ^ 1];
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long gs = (long long)gridDim.x * blockDim.x;
+    const bool lmp = P.scheme == S_LMP;
+    for (long long p = gt; p < P.npts; p += gs) {
+        const double a = un[p], b = um[p];
+        P.VB[p] = lmp ? 0.5 * ((2.0 + k.rho) * a - k.rho * b) : a + k.rho * (a - b);
+    }
+}
+__device__ void phase_im_r0(const Params& P, const Ctl& c, char* smem) {
+    const double* un = P.U[c.cur];
+    const double* um = P.U[c.cur ^ 1];
+    const bool pfc = P.model == M_PFC;
+    row_pass<double, double>(P, 0, pfc ? 3 : 3, (const double2*)nullptr, P.NB64, smem,
+                             [&](long long p, int, int, const double*, double* out) {
+                                 const double ub = P.VB[p];
+                                 out[0] = pfc ? ub * ub * ub - P.eps * ub : ub;
+                                 out[1] = un[p];
+                                 out[2] = um[p];
+                             });
+}
+// per-wavenumber solve; nh = N_hat(ubreve) (FCH: assembled from its parts)
+__device__ __forceinline__ double2 imex_solve(const Params& P, const StepK& k, double kap,
+                                              double2 nh, double2 un, double2 um) {
+    const double M = P.M;
+    double Lh;
+    if (P.model == M_PFC) Lh = (1.0 - kap) * (1.0 - kap);
+    else {
+        const double e2 = P.eps * P.eps;
+        Lh = e2 * e2 * kap * kap + kap + (1.0 - 2.0 * P.tau * P.tau + P.eta2);
+    }
+    const double half = (P.scheme == S_LMP) ? 0.5 : 1.0;
+    double rx = -k.b * un.x - k.c * um.x - M * kap * nh.x;
+    double ry = -k.b * un.y - k.c * um.y - M * kap * nh.y;
+    if (P.scheme == S_LMP) {
+        rx -= M * kap * 0.5 * Lh * un.x;
+        ry -= M * kap * 0.5 * Lh * un.y;
+    }
+    const double den = k.a + M * kap * half * Lh;
+    return double2{rx / den, ry / den};
+}
+__device__ void phase_im_c0(const Params& P, const Ctl& c, char* smem) {
+    const StepK k = step_coeffs(P, c.step);
+    if (P.model == M_PFC) {
+        col_pass<double, double>(P, 3, 1, P.NB64, P.DB64, smem,
+                                 [&](int k1, int k0, const double2* in, double2* out) {
+                                     const double kap = kappa_at(P, k1, k0);
+                                     out[0] = imex_solve(P, k, kap, in[0], in[1], in[2]);
+                                 });
+    } else {
+        col_pass<double, double>(P, 3, 1, P.NB64, P.DB64, smem,
+                                 [&](int k1, int k0, const double2* in, double2* out) {
+                                     const double kap = kappa_at(P, k1, k0);
+                                     const long long idx = (long long)k1 * P.n0 + k0;
+                                     // keep (ub_hat, un_hat) / um_hat in the FP64 spectral scratch
+                                     P.CL64[idx] = in[1];
+                                     P.CL64[idx + (long long)P.h1 * P.n0] = in[2];
+                                     P.CL64[idx + 2ll * P.h1 * P.n0] = in[0];
+                                     out[0] = double2{-kap * in[0].x, -kap * in[0].y};
+                                 });
+    }
+}
+__device__ void phase_im_r1(const Params& P, char* smem) {
+    // N(u) = -kappa0 u - eps^2 Lap F'(u) - (eps^2 (F'' - eta1) - kappa2) Lap u + (F'' - eta2) F'
+    const double e2 = P.eps * P.eps, kap0 = 1.0 - 2.0 * P.tau * P.tau + P.eta2;
+    row_pass<double, double>(P, 1, 2, P.DB64, P.NB64, smem,
+                             [&](long long p, int, int, const double* in, double* out) {
+                                 const double ub = P.VB[p], lu = in[0];
+                                 const double f1 = dF1(ub, P.tau), f2 = dF2(ub, P.tau);
+                                 out[0] = f1;
+                                 out[1] = -kap0 * ub - (e2 * (f2 - P.eta1) - 1.0) * lu + (f2 - P.eta2) * f1;
+                             });
+}
+__device__ void phase_im_c1(const Params& P, const Ctl& c, char* smem) {
+    const StepK k = step_coeffs(P, c.step);
+    const double e2 = P.eps * P.eps;
+    col_pass<double, double>(P, 2, 1, P.NB64, P.DB64, smem,
+                             [&](int k1, int k0, const double2* in, double2* out) {
+                                 const double kap = kappa_at(P, k1, k0);
+                                 const long long idx = (long long)k1 * P.n0 + k0;
+                                 const double2 unh = P.CL64[idx];
+                                 const double2 umh = P.CL64[idx + (long long)P.h1 * P.n0];
+                                 // -eps^2 Lap F' -> + eps^2 kappa F'_hat
+                                 const double2 nh{e2 * kap * in[0].x + in[1].x, e2 * kap * in[0].y + in[1].y};
+                                 out[0] = imex_solve(P, k, kap, nh, unh, umh);
+                             });
+}
+__device__ void phase_im_r2(const Params& P, const Ctl& c, char* smem) {
+    double* unew = P.U[c.cur ^ 1];
+    const bool last = (c.step + 1 == P.nsteps) && P.out_real;
+    row_pass<double, double>(P, 1, 0, P.DB64, (double2*)nullptr, smem,
+                             [&](long long p, int, int, const double* in, double*) {
+                                 unew[p] = in[0];
+                                 if (last) P.out_real[p] = in[0];
+                             });
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.stats[c.step].iters = 0;
+        P.stats[c.step].status = ST_OK;
+        P.stats[c.step].resid = 0.0;
+        P.sc->steps_done = c.step + 1;
+    }
+}
+
+// ------------------------------------------------------------ control
+
+__host__ __device__ inline Ctl ctl_init(const Params& P) {
+    Ctl c;
+    c.step = 0; c.it = 0; c.ev = 0; c.lastev = 0; c.cur = P.cur0; c.rech = 0; c.fail = 0;
+    c.best_ev = 0; c.pad = 0;
+    c.resid = 0.0; c.base_nrm = 0.0; c.best_nrm = 0.0;
+    switch (P.prog) {
+        case PROG_RUN: c.ph = (P.nsteps > 0) ? PH_A : PH_DONE; break;
+        case PROG_IMEX: c.ph = (P.nsteps > 0) ? PH_IM_A : PH_DONE; break;
+        case PROG_FFT_FWD: c.ph = PH_FWD_R; break;
+        case PROG_FFT_INV: c.ph = PH_INV_C; break;
+        case PROG_ENERGY: c.ph = PH_EN_R; break;
+        default: c.ph = PH_MASS; break;
+    }
+    return c;
+}
+
+// Decide the next phase.  Runs identically in every thread of every CTA after a
+// grid barrier; only device-global values that were final before the barrier
+// are read.
+template <class T>
+__device__ void ctl_advance(const Params& P, Ctl& c) {
+    const bool t64 = sizeof(T) == 8;
+    switch (c.ph) {
+        case PH_A: c.ph = PH_B; c.ev = 0; c.rech = 0; break;
+        case PH_B: c.ph = PH_C; break;
+        case PH_C:
+            if (P.model == M_FCH) { c.ph = PH_D; break; }
+            [[fallthrough]];
+        case PH_E:
+            if (!(fabs(ldcg(&P.sc->beta_sum[0])) + fabs(ldcg(&P.sc->beta_sum[1])) <= 1.0e300)) {
+                c.fail = ST_ENAN;  // non-finite initial guess
+                c.ph = PH_FAIL;
+                break;
+            }
+            if (ldcg(&P.sc->flags) & FLAG_PRECOND) { c.fail = ST_EPRECOND; c.ph = PH_FAIL; break; }
+            c.ph = PH_R1;
+            c.it = 1;
+            break;
+        case PH_D: c.ph = PH_E; break;
+        case PH_R1:
+        case PH_RI: {
+            const double nrm = bits_dbl(ldcg(&P.norms[c.ev]));
+            c.lastev = c.ev;
+            c.ev++;
+            c.resid = nrm;
+            if (!(nrm <= 1.0e300)) { c.fail = ST_ENAN; c.ph = PH_FAIL; break; }
+            if (c.ph == PH_R1 || nrm < c.best_nrm) { c.best_nrm = nrm; c.best_ev = c.ev; }
+            if (c.ph == PH_R1) c.base_nrm = nrm;
+            const bool fp32_norm = P.precision == P_MIXED && !t64 && c.ph == PH_RI;
+            if (nrm <= P.tol && !fp32_norm) {
+                c.ph = PH_ACCEPT;
+            } else if (c.ev >= P.max_iter || c.ev + 1 >= P.nslots) {
+                c.fail = ST_ENOCONV;
+                c.ph = PH_FAIL;
+            } else if (fp32_norm && (nrm <= P.tol || nrm <= kRebaseRatio * c.base_nrm ||
+                                     c.ev - c.best_ev >= kStagnation)) {
+                if (c.rech >= P.max_recheck) { c.fail = ST_ENOCONV; c.ph = PH_FAIL; break; }
+                c.rech++;
+                c.ph = PH_REBASE;
+            } else {
+                c.ph = PH_CI;
+            }
+            break;
+        }
+        case PH_CI: c.ph = PH_RI; c.it++; break;
+        case PH_REBASE: c.ph = PH_B; break;
+        case PH_ACCEPT:
+        case PH_IM_R2:
+            c.step++;
+            c.cur ^= 1;
+            if (c.step >= P.nsteps) c.ph = PH_DONE;
+            else c.ph = (c.ph == PH_ACCEPT) ? PH_A : PH_IM_A;
+            break;
+        case PH_IM_A: c.ph = PH_IM_R0; break;
+        case PH_IM_R0: c.ph = PH_IM_C0; break;
+        case PH_IM_C0: c.ph = (P.model == M_PFC) ? PH_IM_R2 : PH_IM_R1; break;
+        case PH_IM_R1: c.ph = PH_IM_C1; break;
+        case PH_IM_C1: c.ph = PH_IM_R2; break;
+        case PH_FWD_R: c.ph = PH_FWD_C; break;
+        case PH_INV_C: c.ph = PH_INV_R; break;
+        case PH_EN_R: c.ph = PH_EN_C; break;
+        case PH_EN_C: c.ph = (P.model == M_PFC) ? PH_DONE : PH_EN_R2; break;
+        default: c.ph = PH_DONE; break;
+    }
+}
+
+template <class T>
+__device__ void exec_phase(const Params& P, const Ctl& c, char* smem, double* red) {
+    switch (c.ph) {
+        case PH_A: phase_A<T>(P, c, red); break;
+        case PH_B: phase_B(P, smem); break;
+        case PH_C: phase_C<T>(P, c, smem); break;
+        case PH_D: phase_D<T>(P, smem); break;
+        case PH_E: phase_E<T>(P, c, smem); break;
+        case PH_R1: phase_R<double, T>(P, c, smem, red, P.DB64); break;
+        case PH_RI: phase_R<T, T>(P, c, smem, red, (const cx<T>*)P.DB); break;
+        case PH_CI: phase_CI<T>(P, c, smem); break;
+        case PH_REBASE: phase_rebase<T>(P, c); break;
+        case PH_ACCEPT: phase_accept<T>(P, c); break;
+        case PH_FAIL: phase_fail(P, c); break;
+        case PH_FWD_R: phase_fwd_r(P, smem); break;
+        case PH_FWD_C: phase_fwd_c(P, smem); break;
+        case PH_INV_C: phase_inv_c(P, smem); break;
+        case PH_INV_R: phase_inv_r(P, smem); break;
+        case PH_EN_R: phase_en_r(P, smem, red); break;
+        case PH_EN_C: phase_en_c(P, smem, red); break;
+        case PH_EN_R2: phase_en_r2(P, smem, red); break;
+        case PH_MASS: phase_mass(P, red); break;
+        case PH_IM_A: phase_im_a(P, c); break;
+        case PH_IM_R0: phase_im_r0(P, c, smem); break;
+        case PH_IM_C0: phase_im_c0(P, c, smem); break;
+        case PH_IM_R1: phase_im_r1(P, smem); break;
+        case PH_IM_C1: phase_im_c1(P, c, smem); break;
+        case PH_IM_R2: phase_im_r2(P, c, smem); break;
+        default: break;
+    }
+}
+
+// shared memory needed by any phase of a program (bytes)
+inline size_t program_smem(const Params& P, int tsize) {
+    const int n0 = P.n0, n1 = P.n1, rb = P.rb, cb = P.cb;
+    size_t m = 0;
+    auto upd = [&](size_t v) { if (v > m) m = v; };
+    const int ki = k_iter(P.model), kb = k_base(P.model);
+    upd(row_smem(n1, rb, 0, 16, 3, 16));       // B / IMEX R0 / DFT / energy
+    upd(row_smem(n1, rb, 1, 16, 2, 16));       // D / IMEX R1 / energy R2
+    upd(row_smem(n1, rb, ki, 16, ki, tsize));  // R1
+    upd(row_smem(n1, rb, ki, tsize, ki, tsize));
+    upd(col_smem(n0, cb, kb, 16, 1, 16));      // C
+    upd(col_smem(n0, cb, 3, 16, 1, 16));       // IMEX C0
+    upd(col_smem(n0, cb, 2, 16, 2, 16));       // E
+    upd(col_smem(n0, cb, ki, tsize, ki, tsize));
+    return m;
+}
+
+}  // namespace pagd

@@ -1,0 +1,272 @@
+"""Thin Python binding of the C ABI in ``include/pagd.h`` (ctypes).
+
+Argument marshalling only: every step of the time step runs in the CUDA
+kernels of ``libpagd.so``.  PyTorch provides the device memory (the solver
+workspace is a torch uint8 tensor) and the stream.  If the CUDA library is
+missing or no GPU is present the calls raise; there is no CPU fallback.
+
+The same binding can drive the test-only emulation library
+(``load_emulation()``), in which "device" buffers are host numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PFC, FCH = 0, 1
+BDF2, MP, LBDF2, LMP = 0, 1, 2, 3
+FP64, FP32_MIXED = 0, 1
+STATUS = {0: "PAGD_OK", 1: "PAGD_EINVAL", 2: "PAGD_ENOMEM", 3: "PAGD_ECUDA", 4: "PAGD_ENOCONV",
+          5: "PAGD_EPRECOND", 6: "PAGD_ENAN", 7: "PAGD_ESTATE", 8: "PAGD_ETIMEOUT"}
+SCHEMES = {"bdf2": BDF2, "mp": MP, "lbdf2": LBDF2, "lmp": LMP}
+PRECISIONS = {"fp64": FP64, "fp32_mixed": FP32_MIXED}
+EXPORTS = ("pagd_default_opts", "pfc_init", "fch_init", "pagd_workspace_size", "pagd_set_workspace",
+           "pagd_set_state", "pagd_step", "pagd_run", "pagd_run_host", "pagd_energy", "pagd_mass",
+           "pagd_fft_r2c", "pagd_fft_c2r", "pagd_get_state", "pagd_last_error", "pagd_destroy")
+
+
+class PagdError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_double), ("n_eta", ctypes.c_int), ("eta", ctypes.c_double * 16),
+                ("max_iter", ctypes.c_int), ("theta_mode", ctypes.c_int), ("accel", ctypes.c_int)]
+
+
+def _declare(lib):
+    P = ctypes.c_void_p
+    D = ctypes.POINTER(ctypes.c_double)
+    IP = ctypes.POINTER(ctypes.c_int)
+    i, d = ctypes.c_int, ctypes.c_double
+    sig = {
+        "pagd_default_opts": [ctypes.POINTER(Opts)],
+        "pfc_init": [ctypes.POINTER(P), i, IP, D, d, d, i, i, ctypes.POINTER(Opts), P],
+        "fch_init": [ctypes.POINTER(P), i, IP, D, d, d, d, d, d, i, i, ctypes.POINTER(Opts), P],
+        "pagd_workspace_size": [P, ctypes.POINTER(ctypes.c_size_t)],
+        "pagd_set_workspace": [P, P, ctypes.c_size_t],
+        "pagd_set_state": [P, P],
+        "pagd_step": [P, P, d, d, IP, D],
+        "pagd_run": [P, P, d, i, d, IP, D],
+        "pagd_run_host": [P, P, P, d, i, d, IP, D],
+        "pagd_energy": [P, P, D],
+        "pagd_mass": [P, P, D],
+        "pagd_fft_r2c": [P, P, P],
+        "pagd_fft_c2r": [P, P, P],
+        "pagd_get_state": [P, P, P, IP],
+        "pagd_last_error": [P],
+        "pagd_destroy": [P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.pagd_last_error.restype = ctypes.c_char_p
+    lib.pagd_destroy.restype = None
+    return lib
+
+
+_LIBS = {}
+
+
+def load(path: str | None = None):
+    """Load libpagd.so (building it with nvcc if needed).  Raises if the CUDA
+    library cannot be built or loaded."""
+    key = path or "cuda"
+    if key not in _LIBS:
+        p = path or _build.build_library()
+        _LIBS[key] = _declare(ctypes.CDLL(p))
+    return _LIBS[key]
+
+
+def load_emulation():
+    """Test-only: the CPU emulation of the kernels (host memory as 'device')."""
+    if "emu" not in _LIBS:
+        _LIBS["emu"] = _declare(ctypes.CDLL(_build.build_emulation()))
+    return _LIBS["emu"]
+
+
+def default_opts(lib=None) -> Opts:
+    o = Opts()
+    (lib or load_emulation_or_cuda()).pagd_default_opts(ctypes.byref(o))
+    return o
+
+
+def load_emulation_or_cuda():
+    return _LIBS.get("cuda") or _LIBS.get("emu") or load()
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+class Solver:
+    """One PFC or FCH problem on a periodic grid, advanced by the C ABI.
+
+    On the CUDA library, fields are torch float64 tensors on the current CUDA
+    device; on the emulation library they are numpy float64 arrays.
+    """
+
+    def __init__(self, model, n, L, eps, eta1=0.0, eta2=0.0, tau=0.0, M=1.0, scheme="bdf2",
+                 precision="fp64", s=0.9, eta=None, max_iter=1000, theta_mode=0, accel=1,
+                 lib=None, stream=None):
+        self.lib = lib if lib is not None else load()
+        self.emu = self.lib is _LIBS.get("emu")
+        self.model = {"pfc": PFC, "fch": FCH}.get(model, model)
+        self.n = tuple(int(v) for v in n)
+        self.L = tuple(float(v) for v in L)
+        self.scheme = SCHEMES.get(scheme, scheme)
+        self.precision = PRECISIONS.get(precision, precision)
+        o = Opts()
+        self.lib.pagd_default_opts(ctypes.byref(o))
+        o.s = s
+        if eta is not None:
+            o.n_eta = len(eta)
+            for j, e in enumerate(eta):
+                o.eta[j] = e
+        o.max_iter, o.theta_mode, o.accel = max_iter, theta_mode, accel
+        self.opts = o
+        self._h = ctypes.c_void_p()
+        nn = (ctypes.c_int * 3)(*(list(self.n) + [1] * (3 - len(self.n))))
+        LL = (ctypes.c_double * 3)(*(list(self.L) + [1.0] * (3 - len(self.L))))
+        self.stream = stream
+        sp = None
+        if stream is not None:
+            sp = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        if self.model == PFC:
+            st = self.lib.pfc_init(ctypes.byref(self._h), len(self.n), nn, LL, eps, M, self.scheme,
+                                   self.precision, ctypes.byref(o), sp)
+        else:
+            st = self.lib.fch_init(ctypes.byref(self._h), len(self.n), nn, LL, eps, eta1, eta2, tau,
+                                   M, self.scheme, self.precision, ctypes.byref(o), sp)
+        if st != 0:
+            raise PagdError(st, "init")
+        nb = ctypes.c_size_t()
+        self._check(self.lib.pagd_workspace_size(self._h, ctypes.byref(nb)), "workspace_size")
+        self.ws_bytes = nb.value
+        if self.emu:
+            raw = np.zeros(self.ws_bytes + 256, dtype=np.uint8)
+            off = (-raw.ctypes.data) % 256
+            self._ws_keep = raw
+            self.ws = raw[off:off + self.ws_bytes]
+            ptr = self.ws.ctypes.data
+        else:
+            import torch
+            self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device="cuda")
+            base = self.ws.data_ptr()
+            ptr = base + ((-base) % 256)
+        self._check(self.lib.pagd_set_workspace(self._h, ctypes.c_void_p(ptr), self.ws_bytes),
+                    "set_workspace")
+
+    # -------------------------------------------------------------- helpers
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.lib.pagd_last_error(self._h) if self._h else b""
+            raise PagdError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def _ptr(self, x):
+        if x is None:
+            return None
+        if _is_torch(x):
+            if self.emu:
+                raise TypeError("emulation library takes numpy arrays")
+            assert x.is_cuda and x.is_contiguous(), "expected a contiguous CUDA tensor"
+            return ctypes.c_void_p(x.data_ptr())
+        if self.emu:
+            assert x.flags.c_contiguous
+            return ctypes.c_void_p(x.ctypes.data)
+        raise TypeError("the CUDA library takes torch CUDA tensors")
+
+    def empty_field(self):
+        if self.emu:
+            return np.zeros(self.n, dtype=np.float64)
+        import torch
+        return torch.zeros(self.n, dtype=torch.float64, device="cuda")
+
+    def empty_spectrum(self):
+        shp = self.n[:-1] + (self.n[-1] // 2 + 1, 2)
+        if self.emu:
+            return np.zeros(shp, dtype=np.float64)
+        import torch
+        return torch.zeros(shp, dtype=torch.float64, device="cuda")
+
+    # ------------------------------------------------------------ C ABI
+    def set_state(self, u0):
+        self._check(self.lib.pagd_set_state(self._h, self._ptr(u0)), "set_state")
+
+    def step(self, u_out, dt, tol):
+        it = ctypes.c_int()
+        r = ctypes.c_double()
+        self._check(self.lib.pagd_step(self._h, self._ptr(u_out), dt, tol, ctypes.byref(it),
+                                       ctypes.byref(r)), "step")
+        return it.value, r.value
+
+    def run(self, dt, nsteps, tol, u_out=None):
+        iters = (ctypes.c_int * max(nsteps, 1))()
+        res = (ctypes.c_double * max(nsteps, 1))()
+        self._check(self.lib.pagd_run(self._h, self._ptr(u_out), dt, nsteps, tol, iters, res), "run")
+        return np.array(iters[:nsteps]), np.array(res[:nsteps])
+
+    def run_host(self, u0, dt, nsteps, tol):
+        u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        out = np.empty_like(u0)
+        iters = (ctypes.c_int * max(nsteps, 1))()
+        res = (ctypes.c_double * max(nsteps, 1))()
+        self._check(self.lib.pagd_run_host(self._h, ctypes.c_void_p(u0.ctypes.data),
+                                           ctypes.c_void_p(out.ctypes.data), dt, nsteps, tol, iters,
+                                           res), "run_host")
+        return out, np.array(iters[:nsteps]), np.array(res[:nsteps])
+
+    def energy(self, u):
+        e = ctypes.c_double()
+        self._check(self.lib.pagd_energy(self._h, self._ptr(u), ctypes.byref(e)), "energy")
+        return e.value
+
+    def mass(self, u):
+        m = ctypes.c_double()
+        self._check(self.lib.pagd_mass(self._h, self._ptr(u), ctypes.byref(m)), "mass")
+        return m.value
+
+    def fft_r2c(self, u, spec=None):
+        spec = self.empty_spectrum() if spec is None else spec
+        self._check(self.lib.pagd_fft_r2c(self._h, self._ptr(u), self._ptr(spec)), "fft_r2c")
+        return spec
+
+    def fft_c2r(self, spec, u=None):
+        u = self.empty_field() if u is None else u
+        self._check(self.lib.pagd_fft_c2r(self._h, self._ptr(spec), self._ptr(u)), "fft_c2r")
+        return u
+
+    def get_state(self):
+        un, um = self.empty_field(), self.empty_field()
+        st = ctypes.c_int()
+        self._check(self.lib.pagd_get_state(self._h, self._ptr(un), self._ptr(um), ctypes.byref(st)),
+                    "get_state")
+        return un, um, st.value
+
+    def close(self):
+        if self._h:
+            self.lib.pagd_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solver_for(workload, lib=None, **over):
+    """A Solver for a named workload from ``inputs.WORKLOADS``."""
+    w = workload
+    kw = dict(model=w.model, n=w.n, L=w.L, eps=w.eps, eta1=w.eta1, eta2=w.eta2, tau=w.tau, M=w.M,
+              scheme=w.scheme, precision=w.precision, s=w.s, eta=w.eta, max_iter=w.max_iter, lib=lib)
+    kw.update(over)
+    return Solver(**kw)
