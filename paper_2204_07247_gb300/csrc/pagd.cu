@@ -308,6 +308,15 @@ static void make_plan(pagd_solver* s) {
     while (rb < n0 && n0 / rb > sms) rb *= 2;
     int cb = 1;
     while ((s->h1 + cb - 1) / cb > sms) cb *= 2;
+    // tuning overrides (rows per row tile, columns per column tile)
+    if (const char* e = std::getenv("PAGD_TILE_ROWS")) {
+        const int v = std::atoi(e);
+        if (v >= 2 && v <= n0 && (v & (v - 1)) == 0) rb = v;
+    }
+    if (const char* e = std::getenv("PAGD_TILE_COLS")) {
+        const int v = std::atoi(e);
+        if (v >= 1 && v <= s->h1) cb = v;
+    }
     s->rb = rb;
     s->cb = cb;
     const int rt = n0 / rb, ct = (s->h1 + cb - 1) / cb;
