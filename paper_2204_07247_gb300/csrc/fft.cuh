@@ -1,12 +1,13 @@
-// fft.cuh -- shared-memory Stockham FFTs on many lines at once, for sm_103a.
+// fft.cuh -- warp-owned shared-memory Stockham FFTs for sm_103a.
 //
-// A CTA holds a set of complex lines (rows of a real field packed in pairs, or
-// columns of a half spectrum) in shared memory and transforms all of them
-// together: each radix-R stage reads R points of a line at stride N/R, applies
-// the twiddles exp(sign 2 pi i (j mod Ns) r / (Ns R)), does a length-R DFT in
-// registers and writes the results at (j div Ns) Ns R + (j mod Ns) + r Ns
-// (the Stockham autosort recursion, so the output is in natural order and no
-// bit reversal is needed).  Stages ping-pong between two buffers.
+// One warp transforms one complex line of length N (a row of two real fields
+// packed as real and imaginary parts, or a column of a half spectrum) held in
+// its own slice of shared memory.  Each radix-R stage reads R points at stride
+// N/R, applies the twiddles exp(sign 2 pi i (j mod Ns) r / (Ns R)), does a
+// length-R DFT in registers and writes the results at
+// (j div Ns) Ns R + (j mod Ns) + r Ns (the Stockham autosort recursion: natural
+// order, no bit reversal).  Stages ping-pong between two buffers and are
+// separated by __syncwarp only: no CTA-wide barrier inside a transform.
 //
 // The transforms are the DFT of Sec. 3.2 (Fourier collocation): forward
 // unnormalised with sign -1, inverse with sign +1; the 1/n_pts factor of the
@@ -16,9 +17,11 @@
 
 namespace pagd {
 
-// largest line length supported; the twiddle table holds exp(-2 pi i m / kNMax)
+// largest line length supported; the global twiddle table holds
+// exp(-2 pi i m / kNMax), m < kNMax
 constexpr int kLogNMax = 10;
 constexpr int kNMax = 1 << kLogNMax;
+constexpr int kWarp = PAGD_WARP;
 
 template <class T> struct V2;
 template <> struct V2<float> { using type = float2; };
@@ -30,7 +33,6 @@ template <class C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - 
 template <class C> __device__ __forceinline__ C cmul(C a, C b) {
     return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
-template <class C, class T> __device__ __forceinline__ C cscale(C a, T s) { return C{a.x * s, a.y * s}; }
 // multiply by S*i (S = -1: by -i, S = +1: by +i)
 template <int S, class C> __device__ __forceinline__ C mul_si(C a) {
     return (S < 0) ? C{a.y, -a.x} : C{-a.y, a.x};
@@ -77,32 +79,31 @@ template <int R, int S, class C> __device__ __forceinline__ void dftR(C* v) {
     else dft8<S>(v);
 }
 
-// One radix-R Stockham stage on `nlines` lines of length N = 1 << logN with
-// line pitch `pitch` (complex elements).  Ns = 1 << logNs is the length of the
-// sub-transforms already combined.  tw: exp(-2 pi i m / kNMax), m < kNMax.
+__device__ __forceinline__ void warp_sync() {
+#ifndef PAGD_EMU
+    __syncwarp();
+#endif
+}
+
+// One radix-R Stockham stage of one line of length N = 1 << logN, done by the
+// lanes of one warp.  Ns = 1 << logNs.  tw: exp(-2 pi i m / (1 << logTw)).
 template <int R, int S, class T>
-__device__ __forceinline__ void stockham_stage(const cx<T>* __restrict__ src, cx<T>* __restrict__ dst,
-                                               int logN, int logNs, int nlines, int pitch,
-                                               const cx<T>* __restrict__ tw) {
+__device__ __forceinline__ void stockham_stage_w(const cx<T>* src, cx<T>* dst, int logN, int logNs,
+                                                 const cx<T>* tw, int logTw, int lane) {
     using C = cx<T>;
     constexpr int logR = (R == 2) ? 1 : (R == 4) ? 2 : 3;
-    const int logNb = logN - logR;  // butterflies per line = N / R
+    const int logNb = logN - logR;  // butterflies = N / R
     const int nb = 1 << logNb;
-    const int total = nb * nlines;
-    const int twshift = kLogNMax - (logNs + logR);  // index scale kNMax / (Ns R)
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int line = t >> logNb;
-        const int j = t & (nb - 1);
-        const C* s = src + line * pitch;
-        C* d = dst + line * pitch;
+    const int twshift = logTw - (logNs + logR);  // index scale (1 << logTw) / (Ns R)
+    for (int j = lane; j < nb; j += kWarp) {
         C v[R];
 #pragma unroll
-        for (int r = 0; r < R; r++) v[r] = s[j + (r << logNb)];
+        for (int r = 0; r < R; r++) v[r] = src[j + (r << logNb)];
         const int jm = j & ((1 << logNs) - 1);
         if (jm) {
 #pragma unroll
             for (int r = 1; r < R; r++) {
-                C w = ldg(&tw[(jm * r) << twshift]);
+                C w = tw[(jm * r) << twshift];
                 if (S > 0) w.y = -w.y;
                 v[r] = cmul(v[r], w);
             }
@@ -110,33 +111,32 @@ __device__ __forceinline__ void stockham_stage(const cx<T>* __restrict__ src, cx
         dftR<R, S>(v);
         const int idxD = ((j - jm) << logR) + jm;
 #pragma unroll
-        for (int r = 0; r < R; r++) d[idxD + (r << logNs)] = v[r];
+        for (int r = 0; r < R; r++) dst[idxD + (r << logNs)] = v[r];
     }
 }
 
-// Full transform of all lines: data starts in buf[0]; returns the index (0/1)
-// of the buffer holding the result.  Every thread of the CTA must call it.
+// Whole transform of one line by one warp: data in b0 (written by any lane
+// before the call); returns 0/1, the buffer holding the result.
 template <int S, class T>
-__device__ int fft_lines(cx<T>* buf0, cx<T>* buf1, int logN, int nlines, int pitch,
-                         const cx<T>* __restrict__ tw) {
-    cx<T>* b[2] = {buf0, buf1};
+__device__ int fft_line_w(cx<T>* b0, cx<T>* b1, int logN, const cx<T>* tw, int logTw, int lane) {
+    cx<T>* b[2] = {b0, b1};
     int cur = 0, logNs = 0;
     while (logNs < logN) {
         const int rem = logN - logNs;
-        __syncthreads();
+        warp_sync();
         if (rem >= 3 && rem != 4) {
-            stockham_stage<8, S, T>(b[cur], b[cur ^ 1], logN, logNs, nlines, pitch, tw);
+            stockham_stage_w<8, S, T>(b[cur], b[cur ^ 1], logN, logNs, tw, logTw, lane);
             logNs += 3;
         } else if (rem >= 2) {
-            stockham_stage<4, S, T>(b[cur], b[cur ^ 1], logN, logNs, nlines, pitch, tw);
+            stockham_stage_w<4, S, T>(b[cur], b[cur ^ 1], logN, logNs, tw, logTw, lane);
             logNs += 2;
         } else {
-            stockham_stage<2, S, T>(b[cur], b[cur ^ 1], logN, logNs, nlines, pitch, tw);
+            stockham_stage_w<2, S, T>(b[cur], b[cur ^ 1], logN, logNs, tw, logTw, lane);
             logNs += 1;
         }
         cur ^= 1;
     }
-    __syncthreads();
+    warp_sync();
     return cur;
 }
 

@@ -67,13 +67,25 @@ __device__ bool grid_barrier(Scal* sc, unsigned& gen) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) pagd_kernel(Params P) {
+__global__ void __launch_bounds__(kThreads, 1) pagd_kernel(Params P) {
     extern __shared__ __align__(16) char smem[];
     __shared__ double red[32];
+    // twiddles exp(-2 pi i m / 2^logtw) staged from the global table
+    const int ntw = 1 << P.logtw;
+    double2* t64 = (double2*)smem;
+    float2* t32 = (float2*)(smem + (size_t)ntw * sizeof(double2));
+    const int stride = kNMax >> P.logtw;
+    for (int m = threadIdx.x; m < ntw; m += blockDim.x) {
+        t64[m] = P.tw64[m * stride];
+        t32[m] = P.tw32[m * stride];
+    }
+    __syncthreads();
+    const Tw tw{t64, t32, P.logtw};
+    char* wsm = smem + tw_smem_bytes(P.logtw);
     Ctl c = ctl_init(P);
     unsigned gen = 0;
     while (c.ph != PH_DONE) {
-        exec_phase<T>(P, c, smem, red);
+        exec_phase<T>(P, c, tw, wsm, red);
         if (!grid_barrier(P.sc, gen)) break;
         ctl_advance<T>(P, c);
     }
@@ -102,8 +114,8 @@ struct pagd_solver {
     size_t ws_bytes;
     char* ws;
     // launch plan
-    int rb, cb, grid;
-    size_t smem;
+    int grid, logtw;
+    size_t smem, warp_bytes;
     // state
     int have_state, step, cur;
     double dt_prev;
@@ -134,8 +146,8 @@ static void plan_layout(pagd_solver* s) {
     const int T = s->tsize;
     size_t sz[O_END];
     sz[O_SC] = sizeof(Scal);
-    sz[O_NORMS] = sizeof(unsigned long long) * s->nslots;
-    sz[O_SUMS] = sizeof(double) * s->nslots;
+    sz[O_NORMS] = sizeof(unsigned long long) * 2 * s->nslots;
+    sz[O_SUMS] = sizeof(double) * 2 * s->nslots;
     sz[O_STATS] = sizeof(StepStat) * kMaxChunk;
     sz[O_TW64] = sizeof(double2) * kNMax;
     sz[O_TW32] = sizeof(float2) * kNMax;
@@ -165,9 +177,9 @@ static Params base_params(const pagd_solver* s) {
     P.logn0 = ilog2(s->n[0]);
     P.logn1 = ilog2(s->n[1]);
     P.h1 = s->h1;
+    P.logtw = s->logtw;
     P.npts = s->npts;
-    P.rb = s->rb;
-    P.cb = s->cb;
+    P.warp_bytes = (long long)s->warp_bytes;
     const double twopi = 6.283185307179586476925286766559;
     P.k0sq = (twopi / s->L[0]) * (twopi / s->L[0]);
     P.k1sq = (twopi / s->L[1]) * (twopi / s->L[1]);
@@ -238,11 +250,20 @@ template <class T> static pagd_status launch(pagd_solver* s, const Params& P) {
     gridDim.x = (unsigned)s->grid;
     blockDim.x = 1;
     threadIdx.x = 0;
+    const int ntw = 1 << P.logtw;
+    double2* t64 = (double2*)base;
+    float2* t32 = (float2*)(base + (size_t)ntw * sizeof(double2));
+    for (int m = 0; m < ntw; m++) {
+        t64[m] = P.tw64[m * (kNMax >> P.logtw)];
+        t32[m] = P.tw32[m * (kNMax >> P.logtw)];
+    }
+    const Tw tw{t64, t32, P.logtw};
+    char* wsm = base + tw_smem_bytes(P.logtw);
     Ctl c = ctl_init(P);
     while (c.ph != PH_DONE) {
         for (int b = 0; b < s->grid; b++) {
             blockIdx.x = (unsigned)b;
-            exec_phase<T>(P, c, base, red);
+            exec_phase<T>(P, c, tw, wsm, red);
         }
         ctl_advance<T>(P, c);
     }
@@ -301,29 +322,22 @@ static pagd_status run_program(pagd_solver* s, Params& P) {
     return st;
 }
 
+// One warp per row unit / column; kThreads / 32 warps per CTA (one in the
+// emulation).  The grid covers the larger of the row and column unit counts
+// and is capped at the co-resident CTA count when launched.
 static void make_plan(pagd_solver* s) {
-    const int sms = num_sms();
-    const int n0 = s->n[0];
-    int rb = 2;
-    while (rb < n0 && n0 / rb > sms) rb *= 2;
-    int cb = 1;
-    while ((s->h1 + cb - 1) / cb > sms) cb *= 2;
-    // tuning overrides (rows per row tile, columns per column tile)
-    if (const char* e = std::getenv("PAGD_TILE_ROWS")) {
-        const int v = std::atoi(e);
-        if (v >= 2 && v <= n0 && (v & (v - 1)) == 0) rb = v;
-    }
-    if (const char* e = std::getenv("PAGD_TILE_COLS")) {
-        const int v = std::atoi(e);
-        if (v >= 1 && v <= s->h1) cb = v;
-    }
-    s->rb = rb;
-    s->cb = cb;
-    const int rt = n0 / rb, ct = (s->h1 + cb - 1) / cb;
-    s->grid = rt > ct ? rt : ct;
+#ifdef PAGD_EMU
+    const int wpb = 1;
+#else
+    const int wpb = kThreads / 32;
+#endif
+    const int units = s->n[0] > s->h1 ? s->n[0] : s->h1;
+    s->grid = (units + wpb - 1) / wpb;
     if (s->grid < 1) s->grid = 1;
-    Params P = base_params(s);
-    s->smem = program_smem(P, 2 * s->tsize);
+    const int l0 = ilog2(s->n[0]), l1 = ilog2(s->n[1]);
+    s->logtw = l0 > l1 ? l0 : l1;
+    s->warp_bytes = warp_smem_bytes(s->n[0], s->n[1], s->model, s->tsize);
+    s->smem = tw_smem_bytes(s->logtw) + (size_t)wpb * s->warp_bytes;
 }
 
 // ----------------------------------------------------------------- C ABI

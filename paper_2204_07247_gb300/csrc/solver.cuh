@@ -5,14 +5,13 @@
 // CTA evaluates the same control state machine after each barrier, so all CTAs
 // agree on the next phase without any host round trip.
 //
-// Phases are of three kinds:
-//   row pass    -- per tile of rows: optional inverse x-DFT of K_in fields from
-//                  the column-major half-spectrum buffer, a pointwise functor,
-//                  optional forward x-DFT of K_out fields back to such a buffer;
-//   column pass -- per tile of half-spectrum columns: optional forward y-DFT of
-//                  K_in fields, a per-wavenumber functor, optional inverse y-DFT
-//                  of K_out fields;
-//   pointwise   -- grid-stride over the grid points.
+// Phases are of two kinds, both built from warp-owned lines (no CTA-wide
+// barrier inside a phase):
+//   row pass    -- per unit of one or two rows: inverse x-DFT of K_in fields
+//                  from the column-major half-spectrum buffer, a pointwise
+//                  functor, forward x-DFT of K_out fields back to such a buffer;
+//   column pass -- per half-spectrum column: forward y-DFT of K_in fields, a
+//                  per-wavenumber functor, inverse y-DFT of K_out fields.
 //
 // The time step (Sec. 3.1.1, Sec. 3.4, Algorithm 2) is solved in a correction
 // form: v = VB + delta, where v is the scheme argument breve u (u for BDF2,
@@ -41,9 +40,9 @@ enum { ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ECUDA = 3, ST_ENOCONV = 4, ST
 enum { FLAG_PRECOND = 1 };
 
 enum Phase {
-    PH_A, PH_B, PH_C, PH_D, PH_E, PH_R1, PH_CI, PH_RI, PH_REBASE, PH_ACCEPT, PH_FAIL,
+    PH_B, PH_C, PH_D, PH_E, PH_R1, PH_CI, PH_RI, PH_ACCEPT, PH_FAIL,
     PH_FWD_R, PH_FWD_C, PH_INV_C, PH_INV_R, PH_EN_R, PH_EN_C, PH_EN_R2, PH_MASS,
-    PH_IM_A, PH_IM_R0, PH_IM_C0, PH_IM_R1, PH_IM_C1, PH_IM_R2, PH_IM_ACCEPT,
+    PH_IM_R0, PH_IM_C0, PH_IM_R1, PH_IM_C1, PH_IM_R2,
     PH_DONE
 };
 
@@ -52,7 +51,7 @@ struct Scal {
     unsigned bar_count, bar_gen;
     int bar_error, flags;
     int status, steps_done, fail_step, pad;
-    double beta_sum[2];
+    double beta_sum[2][2];  // [step parity][field]
     double red[4];
 };
 
@@ -62,13 +61,12 @@ struct StepStat {
 };
 
 constexpr int kMaxK = 3;        // fields per pass
-constexpr int kThreads = 256;   // CTA size of the persistent kernel
+constexpr int kThreads = 128;   // CTA size of the persistent kernel (4 warps)
 
 struct Params {
     int model, scheme, precision, prog;
-    int n0, n1, logn0, logn1, h1;
+    int n0, n1, logn0, logn1, h1, logtw;
     long long npts;
-    int rb, cb;          // rows per row tile, columns per column tile
     double k0sq, k1sq;   // (2 pi / L0)^2, (2 pi / L1)^2
     double cellvol;      // h0 h1
     double eps, eta1, eta2, tau, M;
@@ -76,7 +74,8 @@ struct Params {
     int n_eta, accel, max_iter, max_recheck, theta_mode, pad0;
     double lam[16];      // (1 - eta_j sqrt s) / (1 + eta_j sqrt s)
     double tol, dt, dt_prev0;
-    int step0, nsteps, cur0, nslots;
+    int step0, nsteps, cur0, nslots;  // nslots: norm / sum slots per step parity
+    long long warp_bytes;             // shared memory per warp
     // workspace
     double* U[2];
     double* VB;
@@ -105,8 +104,9 @@ struct Params {
 };
 
 struct Ctl {
-    int ph, step, it, ev, lastev, cur, rech, fail, best_ev, pad;
-    double resid, base_nrm, best_nrm;
+    int ph, step, it, ev, lastev, cur, rech, fail, best_ev;
+    int acc, acc_cur, acc_it, acc_lastev, acc_ev, reb;
+    double resid, base_nrm, best_nrm, acc_resid;
 };
 
 // FP32 iterations stop improving once ||d|| reaches about 1e-7 of the FP64
@@ -115,9 +115,15 @@ struct Ctl {
 constexpr double kRebaseRatio = 1.0e-6;
 constexpr int kStagnation = 12;
 
-template <class T> __device__ __forceinline__ const cx<T>* twiddles(const Params& P);
-template <> __device__ __forceinline__ const cx<double>* twiddles<double>(const Params& P) { return P.tw64; }
-template <> __device__ __forceinline__ const cx<float>* twiddles<float>(const Params& P) { return P.tw32; }
+// twiddle tables exp(-2 pi i m / (1 << log)) staged in shared memory
+struct Tw {
+    const double2* t64;
+    const float2* t32;
+    int log;
+};
+template <class T> __device__ __forceinline__ const cx<T>* tw_of(const Tw& t);
+template <> __device__ __forceinline__ const cx<double>* tw_of<double>(const Tw& t) { return t.t64; }
+template <> __device__ __forceinline__ const cx<float>* tw_of<float>(const Tw& t) { return t.t32; }
 
 // ---------------------------------------------------------------- helpers
 
@@ -128,7 +134,7 @@ struct StepK {
 // Scheme coefficients a_n, b_n, c_n (Eqs. obj:BDF2, obj:MP; backward Euler /
 // its IMEX version for the first BDF2 / LBDF2 step, Algorithm 3 caption), the
 // weight theta_v of the new iterate in breve u, and the extrapolation ratio rho.
-__device__ __forceinline__ StepK step_coeffs(const Params& P, int step) {
+__host__ __device__ __forceinline__ StepK step_coeffs(const Params& P, int step) {
     StepK k;
     const int n = P.step0 + step;
     const double dt = P.dt;
@@ -155,18 +161,19 @@ struct Beta {
 };
 
 // Averaged Newton constants (Sec. 3.4.1) from the grid sums over the argument
-// of the initial guess.
-__device__ __forceinline__ Beta betas(const Params& P, const StepK& k) {
+// of the initial guess of this step.
+__device__ __forceinline__ Beta betas(const Params& P, const StepK& k, int step) {
     Beta B;
     const double inv = 1.0 / (double)P.npts;
+    const int bank = step & 1;
     B.m2 = k.a / P.M;
-    const double s0 = ldcg(&P.sc->beta_sum[0]) * inv;
+    const double s0 = ldcg(&P.sc->beta_sum[bank][0]) * inv;
     if (P.model == M_PFC) {
         B.b0 = k.thpc * fabs(s0);
         B.b2 = -2.0 * k.thpc;
         B.b4 = k.thpc;
     } else {
-        const double s2 = ldcg(&P.sc->beta_sum[1]) * inv;
+        const double s2 = ldcg(&P.sc->beta_sum[bank][1]) * inv;
         const double e2 = P.eps * P.eps;
         B.b0 = k.thpc * fabs(s0);
         B.b2 = k.thpc * fabs(s2);
@@ -198,7 +205,7 @@ __device__ __forceinline__ double Fwell(double z, double tau) {
 
 __device__ __forceinline__ double nanmax(double a, double b) { return (b > a || b != b) ? b : a; }
 
-// block-wide reductions; the result is valid in thread 0
+// block-wide reductions; the result is valid in thread 0.  All threads call.
 __device__ __forceinline__ double block_max(double v, double* red) {
 #ifdef PAGD_EMU
     (void)red;
@@ -238,165 +245,144 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // ---------------------------------------------------------- pass templates
 
 __host__ __device__ __forceinline__ int pitch_of(int n) { return n + 2; }
+__host__ __device__ __forceinline__ int row_unit(int kin, int kout) { return ((kin | kout) & 1) ? 2 : 1; }
 
-// shared memory bytes of a row pass / column pass
-__host__ __device__ __forceinline__ size_t row_smem(int n1, int rb, int kin, int szin, int kout,
-                                                    int szout) {
-    const size_t pitch = (size_t)pitch_of(n1);
-    return 2 * (size_t)(kin * rb / 2) * pitch * szin + 2 * (size_t)(kout * rb / 2) * pitch * szout;
+// shared memory of one warp in a row pass / column pass (bytes)
+__host__ __device__ __forceinline__ size_t row_warp_smem(int n1, int kin, int szin, int kout, int szout) {
+    const int ru = row_unit(kin, kout);
+    const int szc = 2 * (szin > szout ? szin : szout);
+    return (size_t)kin * ru * n1 * szin + (size_t)kout * ru * n1 * szout + 2 * (size_t)pitch_of(n1) * szc;
 }
-__host__ __device__ __forceinline__ size_t col_smem(int n0, int cb, int kin, int szin, int kout,
-                                                    int szout) {
-    const size_t pitch = (size_t)pitch_of(n0);
-    return 2 * (size_t)(kin * cb) * pitch * szin + 2 * (size_t)(kout * cb) * pitch * szout;
+__host__ __device__ __forceinline__ size_t col_warp_smem(int n0, int k, int sz) {
+    return (size_t)(k + 1) * pitch_of(n0) * 2 * sz;
 }
 
-// Row pass.  src/dst: column-major half spectra, field f, column k1, row r at
-// f*h1*n0 + k1*n0 + r.  Real line l = f*rb + rr of a tile; lines 2j and 2j+1 are
-// packed as the real and imaginary part of complex line j.
-// fn(p, row, x, const TI* in, TO* out) handles one grid point.
+struct WarpCtx {
+    int lane, gw, nw;
+    char* mem;
+};
+
+__device__ __forceinline__ WarpCtx warp_ctx(const Params& P, char* smem) {
+    WarpCtx w;
+    w.lane = threadIdx.x % kWarp;
+    const int wib = threadIdx.x / kWarp, wpb = blockDim.x / kWarp;
+    w.gw = blockIdx.x * wpb + wib;
+    w.nw = gridDim.x * wpb;
+    w.mem = smem + (size_t)wib * P.warp_bytes;
+    return w;
+}
+
+// Row pass.  src/dst: column-major half spectra, field f, column k, row r at
+// f*h1*n0 + k*n0 + r.  A unit is ru rows (2 when a field count is odd);
+// real line l = f*ru + rr; lines 2j and 2j+1 are packed as the real and
+// imaginary parts of complex line j.  fn(p, row, x, const TI* in, TO* out).
 template <class TI, class TO, class Fn>
-__device__ void row_pass(const Params& P, int kin, int kout, const cx<TI>* src, cx<TO>* dst,
-                         char* smem, Fn&& fn) {
+__device__ void row_pass(const Params& P, const Tw& tw, int kin, int kout, const cx<TI>* src,
+                         cx<TO>* dst, char* smem, Fn&& fn) {
     using CI = cx<TI>;
     using CO = cx<TO>;
-    const int n0 = P.n0, n1 = P.n1, h1 = P.h1, rb = P.rb, logn1 = P.logn1;
+    const int n0 = P.n0, n1 = P.n1, h1 = P.h1, logn1 = P.logn1, half = n1 >> 1;
     const int pitch = pitch_of(n1);
-    const int xl = kin * rb / 2, yl = kout * rb / 2;
-    CI* X0 = (CI*)smem;
-    CI* X1 = X0 + (size_t)xl * pitch;
-    CO* Y0 = (CO*)(X1 + (size_t)xl * pitch);
-    CO* Y1 = Y0 + (size_t)yl * pitch;
+    const int ru = row_unit(kin, kout);
+    const WarpCtx w = warp_ctx(P, smem);
+    TI* Rin = (TI*)w.mem;
+    TO* Rout = (TO*)(w.mem + (size_t)kin * ru * n1 * sizeof(TI));
+    char* zb = w.mem + (size_t)kin * ru * n1 * sizeof(TI) + (size_t)kout * ru * n1 * sizeof(TO);
     const TI iscale = (TI)(1.0 / ((double)n0 * (double)n1));
-    const int ntiles = n0 / rb;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int r0 = tile * rb;
-        CI* Xr = X0;
-        if (kin > 0) {
-            // stage the half spectra of every real line: X1[l * h1 + k]
-            const int tot = kin * h1 * rb;
-            for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-                const int rr = t % rb;
-                const int k = (t / rb) % h1;
-                const int f = t / (rb * h1);
-                X1[(size_t)(f * rb + rr) * h1 + k] = src[(size_t)f * h1 * n0 + (size_t)k * n0 + r0 + rr];
+    const int nunits = n0 / ru;
+    for (int u = w.gw; u < nunits; u += w.nw) {
+        const int r0 = u * ru;
+        for (int j = 0; 2 * j < kin * ru; j++) {
+            CI* Z0 = (CI*)zb;
+            CI* Z1 = Z0 + pitch;
+            const int la = 2 * j, lb = 2 * j + 1;
+            const CI* sa = src + (size_t)(la / ru) * h1 * n0 + r0 + (la % ru);
+            const CI* sb = src + (size_t)(lb / ru) * h1 * n0 + r0 + (lb % ru);
+            for (int x = w.lane; x < n1; x += kWarp) {
+                const int k = (x <= half) ? x : n1 - x;
+                CI A = sa[(size_t)k * n0], B = sb[(size_t)k * n0];
+                if (x == 0 || x == half) { A.y = 0; B.y = 0; }
+                Z0[x] = (x <= half) ? CI{A.x - B.y, A.y + B.x} : CI{A.x + B.y, B.x - A.y};
             }
-            __syncthreads();
-            // Z_j = A + i B on the full circle, A/B the spectra of lines 2j, 2j+1
-            const int tz = xl * n1;
-            for (int t = threadIdx.x; t < tz; t += blockDim.x) {
-                const int j = t >> logn1;
-                const int x = t & (n1 - 1);
-                const CI* sa = X1 + (size_t)(2 * j) * h1;
-                const CI* sb = sa + h1;
-                CI z;
-                if (x <= (n1 >> 1)) {
-                    CI A = sa[x], B = sb[x];
-                    if (x == 0 || x == (n1 >> 1)) { A.y = 0; B.y = 0; }
-                    z = CI{A.x - B.y, A.y + B.x};
-                } else {
-                    const CI A = sa[n1 - x], B = sb[n1 - x];
-                    z = CI{A.x + B.y, B.x - A.y};
-                }
-                X0[(size_t)j * pitch + x] = z;
+            const int res = fft_line_w<+1, TI>(Z0, Z1, logn1, tw_of<TI>(tw), tw.log, w.lane);
+            const CI* Zr = res ? Z1 : Z0;
+            for (int x = w.lane; x < n1; x += kWarp) {
+                const CI z = Zr[x];
+                Rin[(size_t)la * n1 + x] = z.x * iscale;
+                Rin[(size_t)lb * n1 + x] = z.y * iscale;
             }
-            const int res = fft_lines<+1, TI>(X0, X1, logn1, xl, pitch, twiddles<TI>(P));
-            Xr = res ? X1 : X0;
+            warp_sync();
         }
-        // pointwise
-        const int tp = rb * n1;
-        for (int t = threadIdx.x; t < tp; t += blockDim.x) {
-            const int rr = t >> logn1;
-            const int x = t & (n1 - 1);
-            TI in[kMaxK];
-            TO out[kMaxK];
-            for (int f = 0; f < kin; f++) {
-                const int l = f * rb + rr;
-                const CI z = Xr[(size_t)(l >> 1) * pitch + x];
-                in[f] = ((l & 1) ? z.y : z.x) * iscale;
-            }
-            const long long p = (long long)(r0 + rr) * n1 + x;
-            fn(p, r0 + rr, x, in, out);
-            for (int g = 0; g < kout; g++) {
-                const int l = g * rb + rr;
-                CO* q = Y0 + (size_t)(l >> 1) * pitch + x;
-                if (l & 1) q->y = out[g];
-                else q->x = out[g];
+        for (int x = w.lane; x < n1; x += kWarp) {
+            for (int rr = 0; rr < ru; rr++) {
+                TI in[kMaxK];
+                TO out[kMaxK];
+                for (int f = 0; f < kin; f++) in[f] = Rin[(size_t)(f * ru + rr) * n1 + x];
+                fn((long long)(r0 + rr) * n1 + x, r0 + rr, x, in, out);
+                for (int g = 0; g < kout; g++) Rout[(size_t)(g * ru + rr) * n1 + x] = out[g];
             }
         }
-        if (kout > 0) {
-            const int res = fft_lines<-1, TO>(Y0, Y1, logn1, yl, pitch, twiddles<TO>(P));
-            const CO* Yr = res ? Y1 : Y0;
-            const TO half = (TO)0.5;
-            const int tot = kout * h1 * rb;
-            for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-                const int rr = t % rb;
-                const int k = (t / rb) % h1;
-                const int g = t / (rb * h1);
-                const int l = g * rb + rr;
-                const CO* zl = Yr + (size_t)(l >> 1) * pitch;
-                const CO zk = zl[k];
-                const CO zn = zl[(n1 - k) & (n1 - 1)];
-                CO v;
-                if ((l & 1) == 0) v = CO{half * (zk.x + zn.x), half * (zk.y - zn.y)};
-                else v = CO{half * (zk.y + zn.y), half * (zn.x - zk.x)};
-                dst[(size_t)g * h1 * n0 + (size_t)k * n0 + r0 + rr] = v;
+        for (int j = 0; 2 * j < kout * ru; j++) {
+            CO* Z0 = (CO*)zb;
+            CO* Z1 = Z0 + pitch;
+            const int la = 2 * j, lb = 2 * j + 1;
+            warp_sync();
+            for (int x = w.lane; x < n1; x += kWarp)
+                Z0[x] = CO{Rout[(size_t)la * n1 + x], Rout[(size_t)lb * n1 + x]};
+            const int res = fft_line_w<-1, TO>(Z0, Z1, logn1, tw_of<TO>(tw), tw.log, w.lane);
+            const CO* Zr = res ? Z1 : Z0;
+            CO* da = dst + (size_t)(la / ru) * h1 * n0 + r0 + (la % ru);
+            CO* db = dst + (size_t)(lb / ru) * h1 * n0 + r0 + (lb % ru);
+            const TO hf = (TO)0.5;
+            for (int k = w.lane; k <= half; k += kWarp) {
+                const CO zk = Zr[k];
+                const CO zn = Zr[(n1 - k) & (n1 - 1)];
+                da[(size_t)k * n0] = CO{hf * (zk.x + zn.x), hf * (zk.y - zn.y)};
+                db[(size_t)k * n0] = CO{hf * (zk.y + zn.y), hf * (zn.x - zk.x)};
             }
         }
-        __syncthreads();
+        warp_sync();
     }
 }
 
-// Column pass over half-spectrum columns k1 in [0, h1).  fn(k1, k0, in, out).
-template <class TI, class TO, class Fn>
-__device__ void col_pass(const Params& P, int kin, int kout, const cx<TI>* src, cx<TO>* dst,
+// Column pass over half-spectrum columns k1 in [0, h1): one warp per column.
+// fn(k1, k0, in, out); outputs may overwrite inputs of the same point.
+template <class T, class Fn>
+__device__ void col_pass(const Params& P, const Tw& tw, int kin, int kout, const cx<T>* src, cx<T>* dst,
                          char* smem, Fn&& fn) {
-    using CI = cx<TI>;
-    using CO = cx<TO>;
-    const int n0 = P.n0, h1 = P.h1, cb = P.cb, logn0 = P.logn0;
+    using C = cx<T>;
+    const int n0 = P.n0, h1 = P.h1, logn0 = P.logn0;
     const int pitch = pitch_of(n0);
-    CI* X0 = (CI*)smem;
-    CI* X1 = X0 + (size_t)(kin * cb) * pitch;
-    CO* Y0 = (CO*)(X1 + (size_t)(kin * cb) * pitch);
-    CO* Y1 = Y0 + (size_t)(kout * cb) * pitch;
-    const int ntiles = (h1 + cb - 1) / cb;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int k10 = tile * cb;
-        const int cc = (h1 - k10 < cb) ? (h1 - k10) : cb;
-        const CI* Xr = X0;
-        if (kin > 0) {
-            const int tot = kin * cc * n0;
-            for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-                const int k0 = t & (n0 - 1);
-                const int kk = (t >> logn0) % cc;
-                const int f = (t >> logn0) / cc;
-                X0[(size_t)(f * cc + kk) * pitch + k0] = src[(size_t)f * h1 * n0 + (size_t)(k10 + kk) * n0 + k0];
-            }
-            const int res = fft_lines<-1, TI>(X0, X1, logn0, kin * cc, pitch, twiddles<TI>(P));
-            Xr = res ? X1 : X0;
-        }
-        const int tp = cc * n0;
-        for (int t = threadIdx.x; t < tp; t += blockDim.x) {
-            const int kk = t >> logn0;
-            const int k0 = t & (n0 - 1);
-            CI in[kMaxK];
-            CO out[kMaxK];
-            for (int f = 0; f < kin; f++) in[f] = Xr[(size_t)(f * cc + kk) * pitch + k0];
-            fn(k10 + kk, k0, in, out);
-            for (int g = 0; g < kout; g++) Y0[(size_t)(g * cc + kk) * pitch + k0] = out[g];
-        }
-        if (kout > 0) {
-            const int res = fft_lines<+1, TO>(Y0, Y1, logn0, kout * cc, pitch, twiddles<TO>(P));
-            const CO* Yr = res ? Y1 : Y0;
-            const int tot = kout * cc * n0;
-            for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-                const int k0 = t & (n0 - 1);
-                const int kk = (t >> logn0) % cc;
-                const int g = (t >> logn0) / cc;
-                dst[(size_t)g * h1 * n0 + (size_t)(k10 + kk) * n0 + k0] = Yr[(size_t)(g * cc + kk) * pitch + k0];
+    const int nb = (kin > kout ? kin : kout) + 1;
+    const WarpCtx w = warp_ctx(P, smem);
+    for (int k1 = w.gw; k1 < h1; k1 += w.nw) {
+        C* buf[kMaxK + 1];
+        for (int i = 0; i < nb; i++) buf[i] = (C*)w.mem + (size_t)i * pitch;
+        for (int f = 0; f < kin; f++) {
+            const C* s = src + (size_t)f * h1 * n0 + (size_t)k1 * n0;
+            for (int k0 = w.lane; k0 < n0; k0 += kWarp) buf[f][k0] = s[k0];
+            const int res = fft_line_w<-1, T>(buf[f], buf[nb - 1], logn0, tw_of<T>(tw), tw.log, w.lane);
+            if (res) {
+                C* t = buf[f];
+                buf[f] = buf[nb - 1];
+                buf[nb - 1] = t;
             }
         }
-        __syncthreads();
+        for (int k0 = w.lane; k0 < n0; k0 += kWarp) {
+            C in[kMaxK];
+            C out[kMaxK];
+            for (int f = 0; f < kin; f++) in[f] = buf[f][k0];
+            fn(k1, k0, in, out);
+            for (int g = 0; g < kout; g++) buf[g][k0] = out[g];
+        }
+        for (int g = 0; g < kout; g++) {
+            const int res = fft_line_w<+1, T>(buf[g], buf[nb - 1], logn0, tw_of<T>(tw), tw.log, w.lane);
+            const C* r = res ? buf[nb - 1] : buf[g];
+            C* d = dst + (size_t)g * h1 * n0 + (size_t)k1 * n0;
+            for (int k0 = w.lane; k0 < n0; k0 += kWarp) d[k0] = r[k0];
+            warp_sync();
+        }
+        warp_sync();
     }
 }
 
@@ -407,60 +393,88 @@ __device__ void col_pass(const Params& P, int kin, int kout, const cx<TI>* src, 
 __host__ __device__ __forceinline__ int k_iter(int model) { return model == M_PFC ? 1 : 2; }
 __host__ __device__ __forceinline__ int k_base(int model) { return model == M_PFC ? 3 : 2; }
 
-// Phase A: initial guess (Sec. 3.4.2: extrapolation of the two previous
-// solutions), base argument VB, history term g, preconditioner sums.
+// Phase B: (1) the pending acceptance of the previous step, (2) either the new
+// step's initial guess (Sec. 3.4.2: extrapolation of the two previous solutions),
+// base argument VB, history term g and preconditioner sums, or a move of the
+// base to the current candidate (mixed precision), (3) the forward x-DFT of the
+// FP64 base fields (VB, g[, VB^3]).
 template <class T>
-__device__ void phase_A(const Params& P, const Ctl& c, double* red) {
+__device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red) {
     const StepK k = step_coeffs(P, c.step);
-    const double* un = P.U[c.cur];
-    const double* um = P.U[c.cur ^ 1];
+    const int bank = c.step & 1;
     T* vbt = (T*)P.VBt;
     T* d0 = (T*)P.DD[0];
     T* d1 = (T*)P.DD[1];
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gs = (long long)gridDim.x * blockDim.x;
-    for (long long q = gt; q < P.nslots; q += gs) {
-        P.norms[q] = 0ull;
-        P.sums[q] = 0.0;
+    // acceptance of step c.step - 1 (same scheme, so the same theta_v)
+    const T* dacc = (const T*)P.DD[c.acc_it & 1];
+    const double macc =
+        c.acc ? ldcg(&P.sums[(size_t)(bank ^ 1) * P.nslots + c.acc_lastev]) / (double)P.npts : 0.0;
+    // rebase: the candidate of this step
+    const T* dreb = (const T*)P.DD[c.it & 1];
+    const double mreb = c.reb ? ldcg(&P.sums[(size_t)bank * P.nslots + c.lastev]) / (double)P.npts : 0.0;
+    if (!c.reb) {
+        for (long long q = gt; q < P.nslots; q += gs) {
+            P.norms[(size_t)bank * P.nslots + q] = 0ull;
+            P.sums[(size_t)bank * P.nslots + q] = 0.0;
+        }
+        if (gt == 0) {
+            P.sc->beta_sum[bank ^ 1][0] = 0.0;
+            P.sc->beta_sum[bank ^ 1][1] = 0.0;
+        }
+    }
+    if (c.acc && blockIdx.x == 0 && threadIdx.x == 0) {
+        P.stats[c.step - 1].iters = c.acc_ev;
+        P.stats[c.step - 1].status = ST_OK;
+        P.stats[c.step - 1].resid = c.acc_resid;
+        P.sc->steps_done = c.step;
     }
     double s0 = 0.0, s2 = 0.0;
     const double e2 = P.eps * P.eps;
-    for (long long p = gt; p < P.npts; p += gs) {
-        const double a = un[p], b = um[p];
-        const double x0 = a + k.rho * (a - b);
-        const double vb = k.thv * x0 + (1.0 - k.thv) * a;
-        P.VB[p] = vb;
-        P.G64[p] = k.b * a + k.c * b - k.gun * a;
-        vbt[p] = (T)vb;
-        d0[p] = (T)0;
-        d1[p] = (T)0;
-        if (P.model == M_PFC) {
-            s0 += 3.0 * vb * vb + 1.0 - P.eps;
-        } else {
-            const double f1 = dF1(vb, P.tau), f2 = dF2(vb, P.tau), f3 = dF3(vb, P.tau);
-            s0 += f2 * f2 - P.eta2 * f2 + f3 * f1;
-            s2 += e2 * (f2 - P.eta1);
-        }
-    }
-    s0 = block_sum(s0, red);
-    if (threadIdx.x == 0) atomicAdd(&P.sc->beta_sum[0], s0);
-    if (P.model == M_FCH) {
-        s2 = block_sum(s2, red);
-        if (threadIdx.x == 0) atomicAdd(&P.sc->beta_sum[1], s2);
-    }
-}
-
-// Phase B: forward x-DFT of the FP64 base fields (VB, g[, VB^3]).
-__device__ void phase_B(const Params& P, char* smem) {
     const int kb = k_base(P.model);
     const bool pfc = P.model == M_PFC;
-    row_pass<double, double>(P, 0, kb, (const double2*)nullptr, P.NB64, smem,
+    const double ith = 1.0 / k.thv, wth = 1.0 - k.thv;
+    row_pass<double, double>(P, tw, 0, kb, (const double2*)nullptr, P.NB64, smem,
                              [&](long long p, int, int, const double*, double* out) {
-                                 const double vb = P.VB[p];
+                                 double vb, g;
+                                 if (c.reb) {
+                                     vb = P.VB[p] + ((double)dreb[p] - mreb);
+                                     g = P.G64[p];
+                                 } else {
+                                     if (c.acc) {
+                                         const double va = P.VB[p] + ((double)dacc[p] - macc);
+                                         P.U[c.acc_cur ^ 1][p] = (va - wth * P.U[c.acc_cur][p]) * ith;
+                                     }
+                                     const double a = P.U[c.cur][p], b = P.U[c.cur ^ 1][p];
+                                     const double x0 = a + k.rho * (a - b);
+                                     vb = k.thv * x0 + (1.0 - k.thv) * a;
+                                     g = k.b * a + k.c * b - k.gun * a;
+                                     P.G64[p] = g;
+                                     if (pfc) {
+                                         s0 += 3.0 * vb * vb + 1.0 - P.eps;
+                                     } else {
+                                         const double f1 = dF1(vb, P.tau), f2 = dF2(vb, P.tau), f3 = dF3(vb, P.tau);
+                                         s0 += f2 * f2 - P.eta2 * f2 + f3 * f1;
+                                         s2 += e2 * (f2 - P.eta1);
+                                     }
+                                 }
+                                 P.VB[p] = vb;
+                                 vbt[p] = (T)vb;
+                                 d0[p] = (T)0;
+                                 d1[p] = (T)0;
                                  out[0] = vb;
-                                 out[1] = P.G64[p];
+                                 out[1] = g;
                                  if (pfc) out[2] = vb * vb * vb;
                              });
+    if (!c.reb) {
+        s0 = block_sum(s0, red);
+        if (threadIdx.x == 0) atomicAdd(&P.sc->beta_sum[bank][0], s0);
+        if (!pfc) {
+            s2 = block_sum(s2, red);
+            if (threadIdx.x == 0) atomicAdd(&P.sc->beta_sum[bank][1], s2);
+        }
+    }
 }
 
 // Spectral base gradient C0 = G'_N(VB) (Eqs. misc07 / obj:G'), its
@@ -486,52 +500,52 @@ __device__ __forceinline__ void base_direction(const Params& P, const StepK& k, 
 }
 
 template <class T>
-__device__ void phase_C(const Params& P, const Ctl& c, char* smem) {
+__device__ void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     const StepK k = step_coeffs(P, c.step);
-    const Beta B = betas(P, k);
+    const Beta B = betas(P, k, c.step);
     const int kb = k_base(P.model);
     const double iM = 1.0 / P.M;
     const double e4 = P.eps * P.eps * P.eps * P.eps;
     if (P.model == M_PFC) {
-        col_pass<double, double>(P, kb, 1, P.NB64, P.DB64, smem,
-                                 [&](int k1, int k0, const double2* in, double2* out) {
-                                     const double kap = kappa_at(P, k1, k0);
-                                     const double2 v = in[0], g = in[1], nl = in[2];
-                                     double2 G{0.0, 0.0};
-                                     if (kap != 0.0) {
-                                         const double Lh = 1.0 - P.eps - 2.0 * kap + kap * kap;
-                                         const double ik = iM / kap;
-                                         G.x = (k.Ai * v.x + g.x) * ik + Lh * v.x + nl.x;
-                                         G.y = (k.Ai * v.y + g.y) * ik + Lh * v.y + nl.y;
-                                     }
-                                     double2 d;
-                                     base_direction<T>(P, k, B, k1, k0, kap, G, d);
-                                     out[0] = d;
-                                 });
+        col_pass<double>(P, tw, kb, 1, P.NB64, P.DB64, smem,
+                         [&](int k1, int k0, const double2* in, double2* out) {
+                             const double kap = kappa_at(P, k1, k0);
+                             const double2 v = in[0], g = in[1], nl = in[2];
+                             double2 G{0.0, 0.0};
+                             if (kap != 0.0) {
+                                 const double Lh = 1.0 - P.eps - 2.0 * kap + kap * kap;
+                                 const double ik = iM / kap;
+                                 G.x = (k.Ai * v.x + g.x) * ik + Lh * v.x + nl.x;
+                                 G.y = (k.Ai * v.y + g.y) * ik + Lh * v.y + nl.y;
+                             }
+                             double2 d;
+                             base_direction<T>(P, k, B, k1, k0, kap, G, d);
+                             out[0] = d;
+                         });
     } else {
-        col_pass<double, double>(P, kb, 1, P.NB64, P.DB64, smem,
-                                 [&](int k1, int k0, const double2* in, double2* out) {
-                                     const double kap = kappa_at(P, k1, k0);
-                                     const double2 v = in[0], g = in[1];
-                                     double2 G{0.0, 0.0};
-                                     if (kap != 0.0) {
-                                         const double ik = iM / kap;
-                                         G.x = (k.Ai * v.x + g.x) * ik + e4 * kap * kap * v.x;
-                                         G.y = (k.Ai * v.y + g.y) * ik + e4 * kap * kap * v.y;
-                                     }
-                                     P.CL64[(long long)k1 * P.n0 + k0] = G;
-                                     out[0] = double2{-kap * v.x, -kap * v.y};
-                                 });
+        col_pass<double>(P, tw, kb, 1, P.NB64, P.DB64, smem,
+                         [&](int k1, int k0, const double2* in, double2* out) {
+                             const double kap = kappa_at(P, k1, k0);
+                             const double2 v = in[0], g = in[1];
+                             double2 G{0.0, 0.0};
+                             if (kap != 0.0) {
+                                 const double ik = iM / kap;
+                                 G.x = (k.Ai * v.x + g.x) * ik + e4 * kap * kap * v.x;
+                                 G.y = (k.Ai * v.y + g.y) * ik + e4 * kap * kap * v.y;
+                             }
+                             P.CL64[(long long)k1 * P.n0 + k0] = G;
+                             out[0] = double2{-kap * v.x, -kap * v.y};
+                         });
     }
 }
 
 // FCH: physical Lap VB, then forward x-DFT of (F'(VB), P(VB)) where
 // P = -eps^2 (F'' - eta1) Lap v + (F'' - eta2) F'  (the non-Laplacian part of mu).
 template <class T>
-__device__ void phase_D(const Params& P, char* smem) {
+__device__ void phase_D(const Params& P, const Tw& tw, char* smem) {
     T* lbt = (T*)P.LBt;
     const double e2 = P.eps * P.eps;
-    row_pass<double, double>(P, 1, 2, P.DB64, P.NB64, smem,
+    row_pass<double, double>(P, tw, 1, 2, P.DB64, P.NB64, smem,
                              [&](long long p, int, int, const double* in, double* out) {
                                  const double lb = in[0];
                                  lbt[p] = (T)lb;
@@ -543,36 +557,37 @@ __device__ void phase_D(const Params& P, char* smem) {
 }
 
 template <class T>
-__device__ void phase_E(const Params& P, const Ctl& c, char* smem) {
+__device__ void phase_E(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     const StepK k = step_coeffs(P, c.step);
-    const Beta B = betas(P, k);
+    const Beta B = betas(P, k, c.step);
     const double e2 = P.eps * P.eps;
     const double l1 = lam_at(P, 1);
-    col_pass<double, double>(P, 2, 2, P.NB64, P.DB64, smem,
-                             [&](int k1, int k0, const double2* in, double2* out) {
-                                 const double kap = kappa_at(P, k1, k0);
-                                 const double2 lin = P.CL64[(long long)k1 * P.n0 + k0];
-                                 double2 G{0.0, 0.0};
-                                 if (kap != 0.0) {
-                                     G.x = lin.x + e2 * kap * in[0].x + in[1].x;
-                                     G.y = lin.y + e2 * kap * in[0].y + in[1].y;
-                                 }
-                                 double2 d;
-                                 base_direction<T>(P, k, B, k1, k0, kap, G, d);
-                                 out[0] = d;
-                                 const double f = -kap * (1.0 + l1) * k.ts;
-                                 out[1] = double2{f * d.x, f * d.y};
-                             });
+    col_pass<double>(P, tw, 2, 2, P.NB64, P.DB64, smem,
+                     [&](int k1, int k0, const double2* in, double2* out) {
+                         const double kap = kappa_at(P, k1, k0);
+                         const double2 lin = P.CL64[(long long)k1 * P.n0 + k0];
+                         double2 G{0.0, 0.0};
+                         if (kap != 0.0) {
+                             G.x = lin.x + e2 * kap * in[0].x + in[1].x;
+                             G.y = lin.y + e2 * kap * in[0].y + in[1].y;
+                         }
+                         double2 d;
+                         base_direction<T>(P, k, B, k1, k0, kap, G, d);
+                         out[0] = d;
+                         const double f = -kap * (1.0 + l1) * k.ts;
+                         out[1] = double2{f * d.x, f * d.y};
+                     });
 }
 
 // Iteration row pass (R1 reads the FP64 base direction, RI the T one):
 // delta_it = ybar_{it-1} + theta_v s d_{it-1}; ||d_{it-1}||_inf; then the
 // nonlinear differences at ybar_it and their forward x-DFT.
 template <class TI, class T>
-__device__ void phase_R(const Params& P, const Ctl& c, char* smem, double* red,
+__device__ void phase_R(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red,
                         const cx<TI>* src) {
     const StepK k = step_coeffs(P, c.step);
     const int it = c.it;
+    const int bank = c.step & 1;
     const T lp = (T)lam_at(P, it - 1), l = (T)lam_at(P, it), ts = (T)k.ts;
     T* dcur = (T*)P.DD[it & 1];
     const T* dprev = (const T*)P.DD[(it - 1) & 1];
@@ -582,7 +597,7 @@ __device__ void phase_R(const Params& P, const Ctl& c, char* smem, double* red,
     const T tau = (T)P.tau, e2 = (T)(P.eps * P.eps), eta1 = (T)P.eta1, eta2 = (T)P.eta2;
     double amax = 0.0, asum = 0.0;
     const bool pfc = P.model == M_PFC;
-    row_pass<TI, T>(P, K, K, src, (cx<T>*)P.NB, smem,
+    row_pass<TI, T>(P, tw, K, K, src, (cx<T>*)P.NB, smem,
                     [&](long long p, int, int, const TI* in, T* out) {
                         const TI dd = in[0];
                         const T dp = dprev[p], dpp = dcur[p];
@@ -606,19 +621,19 @@ __device__ void phase_R(const Params& P, const Ctl& c, char* smem, double* red,
                         }
                     });
     amax = block_max(amax, red);
-    if (threadIdx.x == 0) atomicMax(&P.norms[c.ev], dbl_bits(amax));
+    if (threadIdx.x == 0) atomicMax(&P.norms[(size_t)bank * P.nslots + c.ev], dbl_bits(amax));
     asum = block_sum(asum, red);
-    if (threadIdx.x == 0) atomicAdd(&P.sums[c.ev], asum);
+    if (threadIdx.x == 0) atomicAdd(&P.sums[(size_t)bank * P.nslots + c.ev], asum);
 }
 
 // Iteration column pass: ybar_hat, spectral residual (Eq. obj:G' with the
 // zero mode removed), d_hat = r_hat / Lcal_hat (Algorithm 2), the spectral
 // state update, and the inverse y-DFT of d (and of Lap ybar_{it+1} for FCH).
 template <class T>
-__device__ void phase_CI(const Params& P, const Ctl& c, char* smem) {
+__device__ void phase_CI(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     using C = cx<T>;
     const StepK k = step_coeffs(P, c.step);
-    const Beta B = betas(P, k);
+    const Beta B = betas(P, k, c.step);
     const int it = c.it;
     const T l = (T)lam_at(P, it), ln = (T)lam_at(P, it + 1), ts = (T)k.ts;
     const C* scur = (const C*)P.SS[it & 1];
@@ -627,68 +642,50 @@ __device__ void phase_CI(const Params& P, const Ctl& c, char* smem) {
     const int K = k_iter(P.model);
     const bool pfc = P.model == M_PFC;
     const double iM = 1.0 / P.M, e2 = P.eps * P.eps, e4 = e2 * e2;
-    col_pass<T, T>(P, K, K, (const C*)P.NB, (C*)P.DB, smem,
-                   [&](int k1, int k0, const C* in, C* out) {
-                       const long long idx = (long long)k1 * P.n0 + k0;
-                       const double kap = kappa_at(P, k1, k0);
-                       const C sc = scur[idx], sp = sprev[idx];
-                       const C yh = C{sc.x + l * (sc.x - sp.x), sc.y + l * (sc.y - sp.y)};
-                       C d{(T)0, (T)0};
-                       if (kap != 0.0) {
-                           const C g0 = C0[idx];
-                           const double Lk = B.m2 / kap + B.b0 + B.b2 * kap + B.b4 * kap * kap;
-                           const T il = (T)(-1.0 / Lk);
-                           if (pfc) {
-                               const T m = (T)(k.Ai * iM / kap + 1.0 - P.eps - 2.0 * kap + kap * kap);
-                               d.x = il * (g0.x + m * yh.x + in[0].x);
-                               d.y = il * (g0.y + m * yh.y + in[0].y);
-                           } else {
-                               const T m = (T)(k.Ai * iM / kap + e4 * kap * kap);
-                               const T e2k = (T)(e2 * kap);
-                               d.x = il * (g0.x + m * yh.x + e2k * in[0].x + in[1].x);
-                               d.y = il * (g0.y + m * yh.y + e2k * in[0].y + in[1].y);
-                           }
-                       }
-                       const C sn = C{yh.x + ts * d.x, yh.y + ts * d.y};
-                       sprev[idx] = sn;
-                       out[0] = d;
-                       if (!pfc) {
-                           const T f = (T)(-kap);
-                           out[1] = C{f * (sn.x + ln * (sn.x - sc.x)), f * (sn.y + ln * (sn.y - sc.y))};
-                       }
-                   });
+    col_pass<T>(P, tw, K, K, (const C*)P.NB, (C*)P.DB, smem,
+                [&](int k1, int k0, const C* in, C* out) {
+                    const long long idx = (long long)k1 * P.n0 + k0;
+                    const double kap = kappa_at(P, k1, k0);
+                    const C sc = scur[idx], sp = sprev[idx];
+                    const C yh = C{sc.x + l * (sc.x - sp.x), sc.y + l * (sc.y - sp.y)};
+                    C d{(T)0, (T)0};
+                    if (kap != 0.0) {
+                        const C g0 = C0[idx];
+                        const double Lk = B.m2 / kap + B.b0 + B.b2 * kap + B.b4 * kap * kap;
+                        const T il = (T)(-1.0 / Lk);
+                        if (pfc) {
+                            const T m = (T)(k.Ai * iM / kap + 1.0 - P.eps - 2.0 * kap + kap * kap);
+                            d.x = il * (g0.x + m * yh.x + in[0].x);
+                            d.y = il * (g0.y + m * yh.y + in[0].y);
+                        } else {
+                            const T m = (T)(k.Ai * iM / kap + e4 * kap * kap);
+                            const T e2k = (T)(e2 * kap);
+                            d.x = il * (g0.x + m * yh.x + e2k * in[0].x + in[1].x);
+                            d.y = il * (g0.y + m * yh.y + e2k * in[0].y + in[1].y);
+                        }
+                    }
+                    const C sn = C{yh.x + ts * d.x, yh.y + ts * d.y};
+                    sprev[idx] = sn;
+                    out[0] = d;
+                    if (!pfc) {
+                        const T f = (T)(-kap);
+                        out[1] = C{f * (sn.x + ln * (sn.x - sc.x)), f * (sn.y + ln * (sn.y - sc.y))};
+                    }
+                });
 }
 
-// Mixed precision: move the base to the candidate (FP64), clear the correction.
-template <class T>
-__device__ void phase_rebase(const Params& P, const Ctl& c) {
-    T* dc = (T*)P.DD[c.it & 1];
-    T* d0 = (T*)P.DD[0];
-    T* d1 = (T*)P.DD[1];
-    T* vbt = (T*)P.VBt;
-    const double m = ldcg(&P.sums[c.lastev]) / (double)P.npts;
-    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long gs = (long long)gridDim.x * blockDim.x;
-    for (long long p = gt; p < P.npts; p += gs) {
-        const double v = P.VB[p] + ((double)dc[p] - m);
-        P.VB[p] = v;
-        vbt[p] = (T)v;
-        d0[p] = (T)0;
-        d1[p] = (T)0;
-    }
-}
-
-// Accept: u^{n+1} = (VB + delta - (1 - theta_v) u^n) / theta_v, written over
-// u^{n-1}; the mean of delta (zero in exact arithmetic, Remark on discrete mass
-// conservation) is removed in FP64.
+// Accept of the last step of a launch: u^{n+1} = (VB + delta - mean(delta)
+// - (1 - theta_v) u^n) / theta_v, written over u^{n-1}.  (Earlier steps are
+// accepted inside the next step's phase B.)  The mean of delta is zero in exact
+// arithmetic (Remark on discrete mass conservation) and is removed in FP64.
 template <class T>
 __device__ void phase_accept(const Params& P, const Ctl& c) {
     const StepK k = step_coeffs(P, c.step);
+    const int bank = c.step & 1;
     const T* dc = (const T*)P.DD[c.it & 1];
     const double* un = P.U[c.cur];
     double* unew = P.U[c.cur ^ 1];
-    const double m = ldcg(&P.sums[c.lastev]) / (double)P.npts;
-    const bool last = (c.step + 1 == P.nsteps) && P.out_real;
+    const double m = ldcg(&P.sums[(size_t)bank * P.nslots + c.lastev]) / (double)P.npts;
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gs = (long long)gridDim.x * blockDim.x;
     const double ith = 1.0 / k.thv, w = (1.0 - k.thv);
@@ -696,14 +693,12 @@ __device__ void phase_accept(const Params& P, const Ctl& c) {
         const double v = P.VB[p] + ((double)dc[p] - m);
         const double x = (v - w * un[p]) * ith;
         unew[p] = x;
-        if (last) P.out_real[p] = x;
+        if (P.out_real) P.out_real[p] = x;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.stats[c.step].iters = c.ev;
         P.stats[c.step].status = ST_OK;
         P.stats[c.step].resid = c.resid;
-        P.sc->beta_sum[0] = 0.0;
-        P.sc->beta_sum[1] = 0.0;
         P.sc->steps_done = c.step + 1;
     }
 }
@@ -720,26 +715,26 @@ __device__ void phase_fail(const Params& P, const Ctl& c) {
 
 // ------------------------------------------------ DFT / energy / mass programs
 
-__device__ void phase_fwd_r(const Params& P, char* smem) {
-    row_pass<double, double>(P, 0, 1, (const double2*)nullptr, P.NB64, smem,
+__device__ void phase_fwd_r(const Params& P, const Tw& tw, char* smem) {
+    row_pass<double, double>(P, tw, 0, 1, (const double2*)nullptr, P.NB64, smem,
                              [&](long long p, int, int, const double*, double* out) {
                                  out[0] = P.in_real[p];
                              });
 }
-__device__ void phase_fwd_c(const Params& P, char* smem) {
-    col_pass<double, double>(P, 1, 0, P.NB64, (double2*)nullptr, smem,
-                             [&](int k1, int k0, const double2* in, double2*) {
-                                 P.out_spec[(long long)k0 * P.h1 + k1] = in[0];
-                             });
+__device__ void phase_fwd_c(const Params& P, const Tw& tw, char* smem) {
+    col_pass<double>(P, tw, 1, 0, P.NB64, (double2*)nullptr, smem,
+                     [&](int k1, int k0, const double2* in, double2*) {
+                         P.out_spec[(long long)k0 * P.h1 + k1] = in[0];
+                     });
 }
-__device__ void phase_inv_c(const Params& P, char* smem) {
-    col_pass<double, double>(P, 0, 1, (const double2*)nullptr, P.DB64, smem,
-                             [&](int k1, int k0, const double2*, double2* out) {
-                                 out[0] = P.in_spec[(long long)k0 * P.h1 + k1];
-                             });
+__device__ void phase_inv_c(const Params& P, const Tw& tw, char* smem) {
+    col_pass<double>(P, tw, 0, 1, (const double2*)nullptr, P.DB64, smem,
+                     [&](int k1, int k0, const double2*, double2* out) {
+                         out[0] = P.in_spec[(long long)k0 * P.h1 + k1];
+                     });
 }
-__device__ void phase_inv_r(const Params& P, char* smem) {
-    row_pass<double, double>(P, 1, 0, P.DB64, (double2*)nullptr, smem,
+__device__ void phase_inv_r(const Params& P, const Tw& tw, char* smem) {
+    row_pass<double, double>(P, tw, 1, 0, P.DB64, (double2*)nullptr, smem,
                              [&](long long p, int, int, const double* in, double*) {
                                  P.out_real[p] = in[0];
                              });
@@ -747,10 +742,10 @@ __device__ void phase_inv_r(const Params& P, char* smem) {
 
 // energy (Eqs. obj:PFC-egy / obj:FCHegy with Fourier differentiation and the
 // trapezoidal rule): red[0] pointwise part, red[1] spectral part
-__device__ void phase_en_r(const Params& P, char* smem, double* red) {
+__device__ void phase_en_r(const Params& P, const Tw& tw, char* smem, double* red) {
     double acc = 0.0;
     const bool pfc = P.model == M_PFC;
-    row_pass<double, double>(P, 0, 1, (const double2*)nullptr, P.NB64, smem,
+    row_pass<double, double>(P, tw, 0, 1, (const double2*)nullptr, P.NB64, smem,
                              [&](long long p, int, int, const double*, double* out) {
                                  const double u = P.in_real[p];
                                  out[0] = u;
@@ -761,29 +756,29 @@ __device__ void phase_en_r(const Params& P, char* smem, double* red) {
         if (threadIdx.x == 0) atomicAdd(&P.sc->red[0], acc);
     }
 }
-__device__ void phase_en_c(const Params& P, char* smem, double* red) {
+__device__ void phase_en_c(const Params& P, const Tw& tw, char* smem, double* red) {
     double acc = 0.0;
     const bool pfc = P.model == M_PFC;
     const int half = P.n1 >> 1;
-    col_pass<double, double>(P, 1, pfc ? 0 : 1, P.NB64, P.DB64, smem,
-                             [&](int k1, int k0, const double2* in, double2* out) {
-                                 const double kap = kappa_at(P, k1, k0);
-                                 const double w = (k1 == 0 || k1 == half) ? 1.0 : 2.0;
-                                 const double a2 = in[0].x * in[0].x + in[0].y * in[0].y;
-                                 if (pfc) {
-                                     acc += w * (-kap + 0.5 * kap * kap) * a2;
-                                 } else {
-                                     acc += w * kap * a2;
-                                     out[0] = double2{-kap * in[0].x, -kap * in[0].y};
-                                 }
-                             });
+    col_pass<double>(P, tw, 1, pfc ? 0 : 1, P.NB64, P.DB64, smem,
+                     [&](int k1, int k0, const double2* in, double2* out) {
+                         const double kap = kappa_at(P, k1, k0);
+                         const double w = (k1 == 0 || k1 == half) ? 1.0 : 2.0;
+                         const double a2 = in[0].x * in[0].x + in[0].y * in[0].y;
+                         if (pfc) {
+                             acc += w * (-kap + 0.5 * kap * kap) * a2;
+                         } else {
+                             acc += w * kap * a2;
+                             out[0] = double2{-kap * in[0].x, -kap * in[0].y};
+                         }
+                     });
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) atomicAdd(&P.sc->red[1], acc);
 }
-__device__ void phase_en_r2(const Params& P, char* smem, double* red) {
+__device__ void phase_en_r2(const Params& P, const Tw& tw, char* smem, double* red) {
     double acc = 0.0;
     const double e2 = P.eps * P.eps;
-    row_pass<double, double>(P, 1, 0, P.DB64, (double2*)nullptr, smem,
+    row_pass<double, double>(P, tw, 1, 0, P.DB64, (double2*)nullptr, smem,
                              [&](long long p, int, int, const double* in, double*) {
                                  const double u = P.in_real[p];
                                  const double w = e2 * in[0] - dF1(u, P.tau);
@@ -805,37 +800,30 @@ __device__ void phase_mass(const Params& P, double* red) {
 //
 // Eq. eqn:FCH-semidis-simplicit with the splits of Sec. 3.1.1, solved per
 // wavenumber (Sec. 3.3), in FP64:
-//   IM_A : ubreve (extrapolation) pointwise -> stored in VB
-//   IM_R0: forward x-DFT of (ubreve, u^n, u^{n-1})
-//   IM_C0: (PFC) solve directly; (FCH) keep spectra, inverse y-DFT of -kappa ubreve
+//   IM_R0: ubreve (extrapolation) and the forward x-DFT of
+//          (N(ubreve) or ubreve, u^n, u^{n-1})
+//   IM_C0: (PFC) solve; (FCH) keep u^n, u^{n-1} spectra, inverse y-DFT of -kappa ubreve
 //   IM_R1: (FCH) Lap ubreve physical, forward x-DFT of (F'(ub), Q(ub))
 //   IM_C1: (FCH) solve
 //   IM_R2: inverse x-DFT of u^{n+1} -> written over u^{n-1}
-__device__ void phase_im_a(const Params& P, const Ctl& c) {
+__device__ void phase_im_r0(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     const StepK k = step_coeffs(P, c.step);
     const double* un = P.U[c.cur];
     const double* um = P.U[c.cur ^ 1];
-    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long gs = (long long)gridDim.x * blockDim.x;
-    const bool lmp = P.scheme == S_LMP;
-    for (long long p = gt; p < P.npts; p += gs) {
-        const double a = un[p], b = um[p];
-        P.VB[p] = lmp ? 0.5 * ((2.0 + k.rho) * a - k.rho * b) : a + k.rho * (a - b);
-    }
-}
-__device__ void phase_im_r0(const Params& P, const Ctl& c, char* smem) {
-    const double* un = P.U[c.cur];
-    const double* um = P.U[c.cur ^ 1];
     const bool pfc = P.model == M_PFC;
-    row_pass<double, double>(P, 0, pfc ? 3 : 3, (const double2*)nullptr, P.NB64, smem,
+    const bool lmp = P.scheme == S_LMP;
+    row_pass<double, double>(P, tw, 0, 3, (const double2*)nullptr, P.NB64, smem,
                              [&](long long p, int, int, const double*, double* out) {
-                                 const double ub = P.VB[p];
+                                 const double a = un[p], b = um[p];
+                                 const double ub = lmp ? 0.5 * ((2.0 + k.rho) * a - k.rho * b)
+                                                       : a + k.rho * (a - b);
+                                 P.VB[p] = ub;
                                  out[0] = pfc ? ub * ub * ub - P.eps * ub : ub;
-                                 out[1] = un[p];
-                                 out[2] = um[p];
+                                 out[1] = a;
+                                 out[2] = b;
                              });
 }
-// per-wavenumber solve; nh = N_hat(ubreve) (FCH: assembled from its parts)
+// per-wavenumber solve; nh = N_hat(ubreve)
 __device__ __forceinline__ double2 imex_solve(const Params& P, const StepK& k, double kap,
                                               double2 nh, double2 un, double2 um) {
     const double M = P.M;
@@ -855,31 +843,29 @@ __device__ __forceinline__ double2 imex_solve(const Params& P, const StepK& k, d
     const double den = k.a + M * kap * half * Lh;
     return double2{rx / den, ry / den};
 }
-__device__ void phase_im_c0(const Params& P, const Ctl& c, char* smem) {
+__device__ void phase_im_c0(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     const StepK k = step_coeffs(P, c.step);
     if (P.model == M_PFC) {
-        col_pass<double, double>(P, 3, 1, P.NB64, P.DB64, smem,
-                                 [&](int k1, int k0, const double2* in, double2* out) {
-                                     const double kap = kappa_at(P, k1, k0);
-                                     out[0] = imex_solve(P, k, kap, in[0], in[1], in[2]);
-                                 });
+        col_pass<double>(P, tw, 3, 1, P.NB64, P.DB64, smem,
+                         [&](int k1, int k0, const double2* in, double2* out) {
+                             const double kap = kappa_at(P, k1, k0);
+                             out[0] = imex_solve(P, k, kap, in[0], in[1], in[2]);
+                         });
     } else {
-        col_pass<double, double>(P, 3, 1, P.NB64, P.DB64, smem,
-                                 [&](int k1, int k0, const double2* in, double2* out) {
-                                     const double kap = kappa_at(P, k1, k0);
-                                     const long long idx = (long long)k1 * P.n0 + k0;
-                                     // keep (ub_hat, un_hat) / um_hat in the FP64 spectral scratch
-                                     P.CL64[idx] = in[1];
-                                     P.CL64[idx + (long long)P.h1 * P.n0] = in[2];
-                                     P.CL64[idx + 2ll * P.h1 * P.n0] = in[0];
-                                     out[0] = double2{-kap * in[0].x, -kap * in[0].y};
-                                 });
+        col_pass<double>(P, tw, 3, 1, P.NB64, P.DB64, smem,
+                         [&](int k1, int k0, const double2* in, double2* out) {
+                             const double kap = kappa_at(P, k1, k0);
+                             const long long idx = (long long)k1 * P.n0 + k0;
+                             P.CL64[idx] = in[1];
+                             P.CL64[idx + (long long)P.h1 * P.n0] = in[2];
+                             out[0] = double2{-kap * in[0].x, -kap * in[0].y};
+                         });
     }
 }
-__device__ void phase_im_r1(const Params& P, char* smem) {
+__device__ void phase_im_r1(const Params& P, const Tw& tw, char* smem) {
     // N(u) = -kappa0 u - eps^2 Lap F'(u) - (eps^2 (F'' - eta1) - kappa2) Lap u + (F'' - eta2) F'
     const double e2 = P.eps * P.eps, kap0 = 1.0 - 2.0 * P.tau * P.tau + P.eta2;
-    row_pass<double, double>(P, 1, 2, P.DB64, P.NB64, smem,
+    row_pass<double, double>(P, tw, 1, 2, P.DB64, P.NB64, smem,
                              [&](long long p, int, int, const double* in, double* out) {
                                  const double ub = P.VB[p], lu = in[0];
                                  const double f1 = dF1(ub, P.tau), f2 = dF2(ub, P.tau);
@@ -887,24 +873,24 @@ __device__ void phase_im_r1(const Params& P, char* smem) {
                                  out[1] = -kap0 * ub - (e2 * (f2 - P.eta1) - 1.0) * lu + (f2 - P.eta2) * f1;
                              });
 }
-__device__ void phase_im_c1(const Params& P, const Ctl& c, char* smem) {
+__device__ void phase_im_c1(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     const StepK k = step_coeffs(P, c.step);
     const double e2 = P.eps * P.eps;
-    col_pass<double, double>(P, 2, 1, P.NB64, P.DB64, smem,
-                             [&](int k1, int k0, const double2* in, double2* out) {
-                                 const double kap = kappa_at(P, k1, k0);
-                                 const long long idx = (long long)k1 * P.n0 + k0;
-                                 const double2 unh = P.CL64[idx];
-                                 const double2 umh = P.CL64[idx + (long long)P.h1 * P.n0];
-                                 // -eps^2 Lap F' -> + eps^2 kappa F'_hat
-                                 const double2 nh{e2 * kap * in[0].x + in[1].x, e2 * kap * in[0].y + in[1].y};
-                                 out[0] = imex_solve(P, k, kap, nh, unh, umh);
-                             });
+    col_pass<double>(P, tw, 2, 1, P.NB64, P.DB64, smem,
+                     [&](int k1, int k0, const double2* in, double2* out) {
+                         const double kap = kappa_at(P, k1, k0);
+                         const long long idx = (long long)k1 * P.n0 + k0;
+                         const double2 unh = P.CL64[idx];
+                         const double2 umh = P.CL64[idx + (long long)P.h1 * P.n0];
+                         // -eps^2 Lap F' -> + eps^2 kappa F'_hat
+                         const double2 nh{e2 * kap * in[0].x + in[1].x, e2 * kap * in[0].y + in[1].y};
+                         out[0] = imex_solve(P, k, kap, nh, unh, umh);
+                     });
 }
-__device__ void phase_im_r2(const Params& P, const Ctl& c, char* smem) {
+__device__ void phase_im_r2(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     double* unew = P.U[c.cur ^ 1];
     const bool last = (c.step + 1 == P.nsteps) && P.out_real;
-    row_pass<double, double>(P, 1, 0, P.DB64, (double2*)nullptr, smem,
+    row_pass<double, double>(P, tw, 1, 0, P.DB64, (double2*)nullptr, smem,
                              [&](long long p, int, int, const double* in, double*) {
                                  unew[p] = in[0];
                                  if (last) P.out_real[p] = in[0];
@@ -922,11 +908,11 @@ __device__ void phase_im_r2(const Params& P, const Ctl& c, char* smem) {
 __host__ __device__ inline Ctl ctl_init(const Params& P) {
     Ctl c;
     c.step = 0; c.it = 0; c.ev = 0; c.lastev = 0; c.cur = P.cur0; c.rech = 0; c.fail = 0;
-    c.best_ev = 0; c.pad = 0;
-    c.resid = 0.0; c.base_nrm = 0.0; c.best_nrm = 0.0;
+    c.best_ev = 0; c.acc = 0; c.acc_cur = 0; c.acc_it = 0; c.acc_lastev = 0; c.acc_ev = 0; c.reb = 0;
+    c.resid = 0.0; c.base_nrm = 0.0; c.best_nrm = 0.0; c.acc_resid = 0.0;
     switch (P.prog) {
-        case PROG_RUN: c.ph = (P.nsteps > 0) ? PH_A : PH_DONE; break;
-        case PROG_IMEX: c.ph = (P.nsteps > 0) ? PH_IM_A : PH_DONE; break;
+        case PROG_RUN: c.ph = (P.nsteps > 0) ? PH_B : PH_DONE; break;
+        case PROG_IMEX: c.ph = (P.nsteps > 0) ? PH_IM_R0 : PH_DONE; break;
         case PROG_FFT_FWD: c.ph = PH_FWD_R; break;
         case PROG_FFT_INV: c.ph = PH_INV_C; break;
         case PROG_ENERGY: c.ph = PH_EN_R; break;
@@ -941,14 +927,19 @@ __host__ __device__ inline Ctl ctl_init(const Params& P) {
 template <class T>
 __device__ void ctl_advance(const Params& P, Ctl& c) {
     const bool t64 = sizeof(T) == 8;
+    const int bank = c.step & 1;
     switch (c.ph) {
-        case PH_A: c.ph = PH_B; c.ev = 0; c.rech = 0; break;
-        case PH_B: c.ph = PH_C; break;
+        case PH_B:
+            if (!c.reb) { c.ev = 0; c.rech = 0; }
+            c.acc = 0;
+            c.reb = 0;
+            c.ph = PH_C;
+            break;
         case PH_C:
             if (P.model == M_FCH) { c.ph = PH_D; break; }
             [[fallthrough]];
         case PH_E:
-            if (!(fabs(ldcg(&P.sc->beta_sum[0])) + fabs(ldcg(&P.sc->beta_sum[1])) <= 1.0e300)) {
+            if (!(fabs(ldcg(&P.sc->beta_sum[bank][0])) + fabs(ldcg(&P.sc->beta_sum[bank][1])) <= 1.0e300)) {
                 c.fail = ST_ENAN;  // non-finite initial guess
                 c.ph = PH_FAIL;
                 break;
@@ -960,7 +951,7 @@ __device__ void ctl_advance(const Params& P, Ctl& c) {
         case PH_D: c.ph = PH_E; break;
         case PH_R1:
         case PH_RI: {
-            const double nrm = bits_dbl(ldcg(&P.norms[c.ev]));
+            const double nrm = bits_dbl(ldcg(&P.norms[(size_t)bank * P.nslots + c.ev]));
             c.lastev = c.ev;
             c.ev++;
             c.resid = nrm;
@@ -969,7 +960,20 @@ __device__ void ctl_advance(const Params& P, Ctl& c) {
             if (c.ph == PH_R1) c.base_nrm = nrm;
             const bool fp32_norm = P.precision == P_MIXED && !t64 && c.ph == PH_RI;
             if (nrm <= P.tol && !fp32_norm) {
-                c.ph = PH_ACCEPT;
+                if (c.step + 1 < P.nsteps) {
+                    // accepted inside the next step's phase B
+                    c.acc = 1;
+                    c.acc_cur = c.cur;
+                    c.acc_it = c.it;
+                    c.acc_lastev = c.lastev;
+                    c.acc_ev = c.ev;
+                    c.acc_resid = nrm;
+                    c.step++;
+                    c.cur ^= 1;
+                    c.ph = PH_B;
+                } else {
+                    c.ph = PH_ACCEPT;
+                }
             } else if (c.ev >= P.max_iter || c.ev + 1 >= P.nslots) {
                 c.fail = ST_ENOCONV;
                 c.ph = PH_FAIL;
@@ -977,22 +981,20 @@ __device__ void ctl_advance(const Params& P, Ctl& c) {
                                      c.ev - c.best_ev >= kStagnation)) {
                 if (c.rech >= P.max_recheck) { c.fail = ST_ENOCONV; c.ph = PH_FAIL; break; }
                 c.rech++;
-                c.ph = PH_REBASE;
+                c.reb = 1;
+                c.ph = PH_B;
             } else {
                 c.ph = PH_CI;
             }
             break;
         }
         case PH_CI: c.ph = PH_RI; c.it++; break;
-        case PH_REBASE: c.ph = PH_B; break;
-        case PH_ACCEPT:
+        case PH_ACCEPT: c.step++; c.cur ^= 1; c.ph = PH_DONE; break;
         case PH_IM_R2:
             c.step++;
             c.cur ^= 1;
-            if (c.step >= P.nsteps) c.ph = PH_DONE;
-            else c.ph = (c.ph == PH_ACCEPT) ? PH_A : PH_IM_A;
+            c.ph = (c.step >= P.nsteps) ? PH_DONE : PH_IM_R0;
             break;
-        case PH_IM_A: c.ph = PH_IM_R0; break;
         case PH_IM_R0: c.ph = PH_IM_C0; break;
         case PH_IM_C0: c.ph = (P.model == M_PFC) ? PH_IM_R2 : PH_IM_R1; break;
         case PH_IM_R1: c.ph = PH_IM_C1; break;
@@ -1006,52 +1008,51 @@ __device__ void ctl_advance(const Params& P, Ctl& c) {
 }
 
 template <class T>
-__device__ void exec_phase(const Params& P, const Ctl& c, char* smem, double* red) {
+__device__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red) {
     switch (c.ph) {
-        case PH_A: phase_A<T>(P, c, red); break;
-        case PH_B: phase_B(P, smem); break;
-        case PH_C: phase_C<T>(P, c, smem); break;
-        case PH_D: phase_D<T>(P, smem); break;
-        case PH_E: phase_E<T>(P, c, smem); break;
-        case PH_R1: phase_R<double, T>(P, c, smem, red, P.DB64); break;
-        case PH_RI: phase_R<T, T>(P, c, smem, red, (const cx<T>*)P.DB); break;
-        case PH_CI: phase_CI<T>(P, c, smem); break;
-        case PH_REBASE: phase_rebase<T>(P, c); break;
+        case PH_B: phase_B<T>(P, c, tw, smem, red); break;
+        case PH_C: phase_C<T>(P, c, tw, smem); break;
+        case PH_D: phase_D<T>(P, tw, smem); break;
+        case PH_E: phase_E<T>(P, c, tw, smem); break;
+        case PH_R1: phase_R<double, T>(P, c, tw, smem, red, P.DB64); break;
+        case PH_RI: phase_R<T, T>(P, c, tw, smem, red, (const cx<T>*)P.DB); break;
+        case PH_CI: phase_CI<T>(P, c, tw, smem); break;
         case PH_ACCEPT: phase_accept<T>(P, c); break;
         case PH_FAIL: phase_fail(P, c); break;
-        case PH_FWD_R: phase_fwd_r(P, smem); break;
-        case PH_FWD_C: phase_fwd_c(P, smem); break;
-        case PH_INV_C: phase_inv_c(P, smem); break;
-        case PH_INV_R: phase_inv_r(P, smem); break;
-        case PH_EN_R: phase_en_r(P, smem, red); break;
-        case PH_EN_C: phase_en_c(P, smem, red); break;
-        case PH_EN_R2: phase_en_r2(P, smem, red); break;
+        case PH_FWD_R: phase_fwd_r(P, tw, smem); break;
+        case PH_FWD_C: phase_fwd_c(P, tw, smem); break;
+        case PH_INV_C: phase_inv_c(P, tw, smem); break;
+        case PH_INV_R: phase_inv_r(P, tw, smem); break;
+        case PH_EN_R: phase_en_r(P, tw, smem, red); break;
+        case PH_EN_C: phase_en_c(P, tw, smem, red); break;
+        case PH_EN_R2: phase_en_r2(P, tw, smem, red); break;
         case PH_MASS: phase_mass(P, red); break;
-        case PH_IM_A: phase_im_a(P, c); break;
-        case PH_IM_R0: phase_im_r0(P, c, smem); break;
-        case PH_IM_C0: phase_im_c0(P, c, smem); break;
-        case PH_IM_R1: phase_im_r1(P, smem); break;
-        case PH_IM_C1: phase_im_c1(P, c, smem); break;
-        case PH_IM_R2: phase_im_r2(P, c, smem); break;
+        case PH_IM_R0: phase_im_r0(P, c, tw, smem); break;
+        case PH_IM_C0: phase_im_c0(P, c, tw, smem); break;
+        case PH_IM_R1: phase_im_r1(P, tw, smem); break;
+        case PH_IM_C1: phase_im_c1(P, c, tw, smem); break;
+        case PH_IM_R2: phase_im_r2(P, c, tw, smem); break;
         default: break;
     }
 }
 
-// shared memory needed by any phase of a program (bytes)
-inline size_t program_smem(const Params& P, int tsize) {
-    const int n0 = P.n0, n1 = P.n1, rb = P.rb, cb = P.cb;
+// shared memory per warp needed by any phase (bytes, 16-byte multiple)
+inline size_t warp_smem_bytes(int n0, int n1, int model, int tsize) {
     size_t m = 0;
     auto upd = [&](size_t v) { if (v > m) m = v; };
-    const int ki = k_iter(P.model), kb = k_base(P.model);
-    upd(row_smem(n1, rb, 0, 16, 3, 16));       // B / IMEX R0 / DFT / energy
-    upd(row_smem(n1, rb, 1, 16, 2, 16));       // D / IMEX R1 / energy R2
-    upd(row_smem(n1, rb, ki, 16, ki, tsize));  // R1
-    upd(row_smem(n1, rb, ki, tsize, ki, tsize));
-    upd(col_smem(n0, cb, kb, 16, 1, 16));      // C
-    upd(col_smem(n0, cb, 3, 16, 1, 16));       // IMEX C0
-    upd(col_smem(n0, cb, 2, 16, 2, 16));       // E
-    upd(col_smem(n0, cb, ki, tsize, ki, tsize));
-    return m;
+    const int ki = k_iter(model);
+    upd(row_warp_smem(n1, 0, 8, 3, 8));            // B (PFC: 3 fields) / IMEX R0
+    upd(row_warp_smem(n1, 1, 8, 2, 8));            // D / IMEX R1 / energy / DFT
+    upd(row_warp_smem(n1, 0, 8, 1, 8));
+    upd(row_warp_smem(n1, ki, 8, ki, tsize));      // R1
+    upd(row_warp_smem(n1, ki, tsize, ki, tsize));  // RI
+    upd(col_warp_smem(n0, 3, 8));                  // C / IMEX C0
+    upd(col_warp_smem(n0, 2, 8));                  // E
+    upd(col_warp_smem(n0, ki, tsize));             // CI
+    return (m + 15) & ~(size_t)15;
 }
+
+// twiddle tables in shared memory: 1 << logtw entries, FP64 then FP32
+__host__ __device__ inline size_t tw_smem_bytes(int logtw) { return ((size_t)1 << logtw) * (16 + 8); }
 
 }  // namespace pagd
