@@ -331,7 +331,7 @@ static void make_plan(pagd_solver* s) {
 #else
     const int wpb = kThreads / 32;
 #endif
-    const int units = s->n[0] > s->h1 ? s->n[0] : s->h1;
+    const int units = s->n[0] / 2 > s->h1 ? s->n[0] / 2 : s->h1;
     s->grid = (units + wpb - 1) / wpb;
     if (s->grid < 1) s->grid = 1;
     const int l0 = ilog2(s->n[0]), l1 = ilog2(s->n[1]);

@@ -245,7 +245,11 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // ---------------------------------------------------------- pass templates
 
 __host__ __device__ __forceinline__ int pitch_of(int n) { return n + 2; }
-__host__ __device__ __forceinline__ int row_unit(int kin, int kout) { return ((kin | kout) & 1) ? 2 : 1; }
+// A row unit is two rows: the two real lines packed into one complex transform
+// are always the same field on neighbouring rows, so both halves have the same
+// magnitude (packing two different fields, e.g. d and Lap y, would put the FP32
+// rounding of the larger one onto the smaller one).
+__host__ __device__ __forceinline__ int row_unit(int, int) { return 2; }
 
 // shared memory of one warp in a row pass / column pass (bytes)
 __host__ __device__ __forceinline__ size_t row_warp_smem(int n1, int kin, int szin, int kout, int szout) {
@@ -273,7 +277,7 @@ __device__ __forceinline__ WarpCtx warp_ctx(const Params& P, char* smem) {
 }
 
 // Row pass.  src/dst: column-major half spectra, field f, column k, row r at
-// f*h1*n0 + k*n0 + r.  A unit is ru rows (2 when a field count is odd);
+// f*h1*n0 + k*n0 + r.  A unit is ru = 2 rows;
 // real line l = f*ru + rr; lines 2j and 2j+1 are packed as the real and
 // imaginary parts of complex line j.  fn(p, row, x, const TI* in, TO* out).
 template <class TI, class TO, class Fn>

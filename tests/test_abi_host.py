@@ -205,3 +205,19 @@ def test_emulated_precond_failure(emu):
     with pytest.raises(pagd.PagdError) as e:
         S.run(100.0, 1, 1e-10)
     assert e.value.status == 5
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_emulated_mixed_precision_costs_few_extra_evaluations(emu, case):
+    """FP32 rounding must stay relative to the correction: if it leaked in at
+    O(1) (e.g. two fields of very different size packed into one transform) the
+    FP32 norm would stall far above tol and force many FP64 rebases."""
+    model, n, L, eps, e1, e2, tau, scheme, dt, mean = case
+    u0 = I.noisy_field(n, mean, 0.05, 21)
+    counts = {}
+    for prec in ("fp64", "fp32_mixed"):
+        S = pagd.Solver(model, n, L, eps, e1, e2, tau, scheme=scheme, precision=prec, lib=emu)
+        S.set_state(u0)
+        its, _ = S.run(dt, 3, 1e-8, S.empty_field())
+        counts[prec] = its
+    assert all(m <= f + 6 for m, f in zip(counts["fp32_mixed"], counts["fp64"])), counts
