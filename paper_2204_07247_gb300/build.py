@@ -18,8 +18,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpagd.so")
 EMU = os.path.join(BUILD, "libpagd_emu.so")
-SOURCES = ["pagd.cu"]
-HEADERS = ["compat.cuh", "fft.cuh", "solver.cuh"]
+# host code + one kernel translation unit per fixed line length (0: runtime length)
+SOURCES = ["pagd.cu", "pagd_k0.cu", "pagd_k64.cu", "pagd_k128.cu", "pagd_k256.cu", "pagd_k512.cu"]
+HEADERS = ["compat.cuh", "fft.cuh", "solver.cuh", "kernels.cuh"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 
@@ -44,16 +45,28 @@ def nvcc():
 
 
 def build_library(force: bool = False, verbose: bool = False) -> str:
+    """nvcc each translation unit for sm_103a in parallel, then link the .so."""
+    from concurrent.futures import ThreadPoolExecutor
     os.makedirs(BUILD, exist_ok=True)
     if not force and not _stale(LIB):
         return LIB
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc(), "-gencode", GENCODE, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-shared", "-o", tmp, os.path.join(CSRC, "pagd.cu")]
+    tag = os.getpid()
+    flags = ["-gencode", GENCODE, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.check_call(cmd)
+        flags.append("-Xptxas=-v")
+
+    def compile_one(src):
+        obj = os.path.join(BUILD, f"{os.path.splitext(src)[0]}.{tag}.o")
+        subprocess.check_call([nvcc(), *flags, "-c", "-o", obj, os.path.join(CSRC, src)])
+        return obj
+
+    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
+    tmp = LIB + f".{tag}.tmp"
+    subprocess.check_call([nvcc(), "-gencode", GENCODE, "-shared", "-o", tmp, *objs])
     os.replace(tmp, LIB)
+    for o in objs:
+        os.remove(o)
     return LIB
 
 

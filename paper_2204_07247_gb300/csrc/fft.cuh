@@ -141,3 +141,83 @@ __device__ int fft_line_w(cx<T>* b0, cx<T>* b1, int logN, const cx<T>* tw, int l
 }
 
 }  // namespace pagd
+
+namespace pagd {
+
+// ---------------------------------------------------------------------------
+// Compile-time line length: the radix sequence, the per-lane butterfly loops and
+// the line loop unroll, so the loads of all lines a warp owns are in flight
+// together.  Lines l < nl (nl <= MAXL) sit at `pitch` apart in each buffer.
+
+template <int R, int S, class T, int LOGN, int LOGNS, int MAXL>
+__device__ __forceinline__ void stage_fixed(const cx<T>* src, cx<T>* dst, int pitch, int nl,
+                                            const cx<T>* tw, int logTw, int lane) {
+    using C = cx<T>;
+    constexpr int LR = (R == 2) ? 1 : (R == 4) ? 2 : 3;
+    constexpr int NB = 1 << (LOGN - LR);
+    constexpr int NS = 1 << LOGNS;
+    constexpr int PER = (NB + kWarp - 1) / kWarp;
+    const int twshift = logTw - (LOGNS + LR);
+#pragma unroll
+    for (int i = 0; i < PER; i++) {
+        const int j = lane + kWarp * i;
+        if ((NB % kWarp) != 0 && j >= NB) break;
+        const int jm = j & (NS - 1);
+        C w[R];
+        if (LOGNS > 0) {
+#pragma unroll
+            for (int r = 1; r < R; r++) {
+                w[r] = tw[(jm * r) << twshift];
+                if (S > 0) w[r].y = -w[r].y;
+            }
+        }
+        const int idxD = ((j - jm) << LR) + jm;
+#pragma unroll
+        for (int l = 0; l < MAXL; l++) {
+            if (l < nl) {
+                const C* s = src + l * pitch;
+                C* d = dst + l * pitch;
+                C v[R];
+#pragma unroll
+                for (int r = 0; r < R; r++) v[r] = s[j + r * NB];
+                if (LOGNS > 0) {
+#pragma unroll
+                    for (int r = 1; r < R; r++) v[r] = cmul(v[r], w[r]);
+                }
+                dftR<R, S>(v);
+#pragma unroll
+                for (int r = 0; r < R; r++) d[idxD + r * NS] = v[r];
+            }
+        }
+    }
+}
+
+template <int S, class T, int LOGN, int LOGNS, int MAXL>
+struct FixedStages {
+    static __device__ __forceinline__ int run(cx<T>* b0, cx<T>* b1, int pitch, int nl, const cx<T>* tw,
+                                              int logTw, int lane, int cur) {
+        if constexpr (LOGNS >= LOGN) {
+            return cur;
+        } else {
+            constexpr int REM = LOGN - LOGNS;
+            constexpr int R = (REM >= 3 && REM != 4) ? 8 : (REM >= 2 ? 4 : 2);
+            constexpr int LR = (R == 2) ? 1 : (R == 4) ? 2 : 3;
+            warp_sync();
+            stage_fixed<R, S, T, LOGN, LOGNS, MAXL>(cur ? b1 : b0, cur ? b0 : b1, pitch, nl, tw, logTw, lane);
+            return FixedStages<S, T, LOGN, LOGNS + LR, MAXL>::run(b0, b1, pitch, nl, tw, logTw, lane, cur ^ 1);
+        }
+    }
+};
+
+// nl lines of length 1 << LOGN in b0 -> result in b0 (returns 0) or b1 (1)
+template <int S, class T, int LOGN, int MAXL>
+__device__ __forceinline__ int fft_lines_fixed(cx<T>* b0, cx<T>* b1, int pitch, int nl, const cx<T>* tw,
+                                               int logTw, int lane) {
+    const int r = FixedStages<S, T, LOGN, 0, MAXL>::run(b0, b1, pitch, nl, tw, logTw, lane, 0);
+    warp_sync();
+    return r;
+}
+
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
+
+}  // namespace pagd

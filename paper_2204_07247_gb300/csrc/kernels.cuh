@@ -1,0 +1,112 @@
+// kernels.cuh -- the persistent cooperative kernel and its launcher.
+//
+// Included by one translation unit per fixed line length (pagd_k*.cu), which
+// instantiate pagd_launch<T, NF> for T = float and double; the units compile in
+// parallel and link into libpagd.so.
+#pragma once
+#include "solver.cuh"
+
+namespace pagd {
+
+
+constexpr unsigned long long kBarrierTimeoutNs = 5000000000ull;  // 5 s per wait
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Device-wide barrier for a cooperative launch (all CTAs co-resident).  The
+// wait is bounded: after kBarrierTimeoutNs, or once another CTA has flagged an
+// error, the CTA records the error and returns false instead of spinning on.
+static __device__ bool grid_barrier(Scal* sc, unsigned& gen) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = gen;
+        __threadfence();
+        const unsigned prev = atomicAdd(&sc->bar_count, 1u);
+        if (prev == gridDim.x - 1) {
+            atomicExch(&sc->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&sc->bar_gen, 1u);
+        } else {
+            const unsigned long long t0 = gtimer();
+            volatile unsigned* vg = &sc->bar_gen;
+            volatile int* ve = &sc->bar_error;
+            while (*vg == g) {
+                if (*ve) { ok = 0; break; }
+                __nanosleep(32);
+                if (gtimer() - t0 > kBarrierTimeoutNs) {
+                    atomicOr(&sc->bar_error, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    gen++;
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <class T, int NF>
+__global__ void __launch_bounds__(kThreads, 1) pagd_kernel(Params P) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ double red[32];
+    // twiddles exp(-2 pi i m / 2^logtw) staged from the global table
+    const int ntw = 1 << P.logtw;
+    double2* t64 = (double2*)smem;
+    float2* t32 = (float2*)(smem + (size_t)ntw * sizeof(double2));
+    const int stride = kNMax >> P.logtw;
+    for (int m = threadIdx.x; m < ntw; m += blockDim.x) {
+        t64[m] = P.tw64[m * stride];
+        t32[m] = P.tw32[m * stride];
+    }
+    __syncthreads();
+    const Tw tw{t64, t32, P.logtw};
+    char* wsm = smem + tw_smem_bytes(P.logtw);
+    Ctl c = ctl_init(P);
+    unsigned gen = 0;
+    while (c.ph != PH_DONE) {
+        exec_phase<T, NF>(P, c, tw, wsm, red);
+        if (!grid_barrier(P.sc, gen)) break;
+        ctl_advance<T>(P, c);
+    }
+}
+
+
+// Launch pagd_kernel<T, NF> cooperatively: the grid is capped at the number of
+// co-resident CTAs so that the device-wide barrier is safe.
+template <class T, int NF>
+cudaError_t pagd_launch(const Params& P, int grid, size_t smem, void* stream, int* grid_used) {
+    void (*kern)(Params) = pagd_kernel<T, NF>;
+    cudaError_t e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int dev = 0, sms = 1;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int cap = per_sm * sms;
+    if (grid > cap) grid = cap;
+    if (grid_used) *grid_used = grid;
+    Params Pc = P;
+    void* args[] = {(void*)&Pc};
+    return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kThreads), args, smem,
+                                       (cudaStream_t)stream);
+}
+
+}  // namespace pagd
+
+#define PAGD_INSTANTIATE(NF)                                                                             \
+    template cudaError_t pagd::pagd_launch<float, NF>(const pagd::Params&, int, size_t, void*, int*);   \
+    template cudaError_t pagd::pagd_launch<double, NF>(const pagd::Params&, int, size_t, void*, int*);

@@ -20,78 +20,9 @@ using namespace pagd;
 
 #ifndef PAGD_EMU
 namespace pagd {
-
-constexpr unsigned long long kBarrierTimeoutNs = 5000000000ull;  // 5 s per wait
-
-__device__ __forceinline__ unsigned long long gtimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
+template <class T, int NF>
+cudaError_t pagd_launch(const Params& P, int grid, size_t smem, void* stream, int* grid_used);
 }
-
-// Device-wide barrier for a cooperative launch (all CTAs co-resident).  The
-// wait is bounded: after kBarrierTimeoutNs, or once another CTA has flagged an
-// error, the CTA records the error and returns false instead of spinning on.
-__device__ bool grid_barrier(Scal* sc, unsigned& gen) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned g = gen;
-        __threadfence();
-        const unsigned prev = atomicAdd(&sc->bar_count, 1u);
-        if (prev == gridDim.x - 1) {
-            atomicExch(&sc->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&sc->bar_gen, 1u);
-        } else {
-            const unsigned long long t0 = gtimer();
-            volatile unsigned* vg = &sc->bar_gen;
-            volatile int* ve = &sc->bar_error;
-            while (*vg == g) {
-                if (*ve) { ok = 0; break; }
-                __nanosleep(32);
-                if (gtimer() - t0 > kBarrierTimeoutNs) {
-                    atomicOr(&sc->bar_error, 1);
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    gen++;
-    __syncthreads();
-    return s_ok != 0;
-}
-
-template <class T>
-__global__ void __launch_bounds__(kThreads, 1) pagd_kernel(Params P) {
-    extern __shared__ __align__(16) char smem[];
-    __shared__ double red[32];
-    // twiddles exp(-2 pi i m / 2^logtw) staged from the global table
-    const int ntw = 1 << P.logtw;
-    double2* t64 = (double2*)smem;
-    float2* t32 = (float2*)(smem + (size_t)ntw * sizeof(double2));
-    const int stride = kNMax >> P.logtw;
-    for (int m = threadIdx.x; m < ntw; m += blockDim.x) {
-        t64[m] = P.tw64[m * stride];
-        t32[m] = P.tw32[m * stride];
-    }
-    __syncthreads();
-    const Tw tw{t64, t32, P.logtw};
-    char* wsm = smem + tw_smem_bytes(P.logtw);
-    Ctl c = ctl_init(P);
-    unsigned gen = 0;
-    while (c.ph != PH_DONE) {
-        exec_phase<T>(P, c, tw, wsm, red);
-        if (!grid_barrier(P.sc, gen)) break;
-        ctl_advance<T>(P, c);
-    }
-}
-
-}  // namespace pagd
 #else
 thread_local EmuDim3 threadIdx{0, 0, 0}, blockIdx{0, 0, 0}, blockDim{1, 1, 1}, gridDim{1, 1, 1};
 #endif
@@ -260,10 +191,17 @@ template <class T> static pagd_status launch(pagd_solver* s, const Params& P) {
     const Tw tw{t64, t32, P.logtw};
     char* wsm = base + tw_smem_bytes(P.logtw);
     Ctl c = ctl_init(P);
+    const int nf = fixed_len(P.n0, P.n1);
     while (c.ph != PH_DONE) {
         for (int b = 0; b < s->grid; b++) {
             blockIdx.x = (unsigned)b;
-            exec_phase<T>(P, c, tw, wsm, red);
+            switch (nf) {
+                case 64: exec_phase<T, 64>(P, c, tw, wsm, red); break;
+                case 128: exec_phase<T, 128>(P, c, tw, wsm, red); break;
+                case 256: exec_phase<T, 256>(P, c, tw, wsm, red); break;
+                case 512: exec_phase<T, 512>(P, c, tw, wsm, red); break;
+                default: exec_phase<T, 0>(P, c, tw, wsm, red); break;
+            }
         }
         ctl_advance<T>(P, c);
     }
@@ -294,22 +232,16 @@ static int num_sms() {
     return v > 0 ? v : 1;
 }
 template <class T> static pagd_status launch(pagd_solver* s, const Params& P) {
-    void (*kern)(Params) = pagd_kernel<T>;
-    cudaError_t e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)s->smem);
-    if (e != cudaSuccess) return cuda_fail(s, e, "cudaFuncSetAttribute");
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, kThreads, s->smem);
-    if (e != cudaSuccess) return cuda_fail(s, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    if (per_sm < 1) return fail(s, PAGD_EINVAL, "kernel does not fit on an SM with this tile plan");
-    int grid = s->grid;
-    const int cap = per_sm * num_sms();
-    if (grid > cap) grid = cap;
-    Params Pc = P;
-    void* args[] = {(void*)&Pc};
-    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kThreads), args, s->smem,
-                                    (cudaStream_t)s->stream);
-    if (e != cudaSuccess) return cuda_fail(s, e, "cudaLaunchCooperativeKernel");
+    cudaError_t e;
+    int used = 0;
+    switch (fixed_len(P.n0, P.n1)) {
+        case 64: e = pagd_launch<T, 64>(P, s->grid, s->smem, s->stream, &used); break;
+        case 128: e = pagd_launch<T, 128>(P, s->grid, s->smem, s->stream, &used); break;
+        case 256: e = pagd_launch<T, 256>(P, s->grid, s->smem, s->stream, &used); break;
+        case 512: e = pagd_launch<T, 512>(P, s->grid, s->smem, s->stream, &used); break;
+        default: e = pagd_launch<T, 0>(P, s->grid, s->smem, s->stream, &used); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(s, e, "cooperative launch of pagd_kernel");
     return PAGD_OK;
 }
 #endif
@@ -336,7 +268,7 @@ static void make_plan(pagd_solver* s) {
     if (s->grid < 1) s->grid = 1;
     const int l0 = ilog2(s->n[0]), l1 = ilog2(s->n[1]);
     s->logtw = l0 > l1 ? l0 : l1;
-    s->warp_bytes = warp_smem_bytes(s->n[0], s->n[1], s->model, s->tsize);
+    s->warp_bytes = warp_smem_bytes(s->n[0], s->n[1], s->model, s->tsize, fixed_len(s->n[0], s->n[1]));
     s->smem = tw_smem_bytes(s->logtw) + (size_t)wpb * s->warp_bytes;
 }
 

@@ -390,6 +390,217 @@ __device__ void col_pass(const Params& P, const Tw& tw, int kin, int kout, const
     }
 }
 
+// ------------------------------------------------- fixed-length pass variants
+//
+// The same passes with the line length a compile-time constant NF (square
+// grids of 64..512): the per-lane loops unroll, every lane issues all its loads
+// of a line before using any of them, the lines a warp owns are transformed in
+// lockstep, and the pointwise work is split into a batched load step `ld` and an
+// apply step `ap`, so the global loads of up to 16 points are in flight at once.
+
+constexpr int kChunk = 16;  // points per batched load
+
+template <int NF> __host__ __device__ __forceinline__ size_t row_fixed_smem(int kin, int szin, int kout, int szout) {
+    return 2 * (size_t)(NF + 2) * ((size_t)kin * 2 * szin + (size_t)kout * 2 * szout);
+}
+template <int NF> __host__ __device__ __forceinline__ size_t col_fixed_smem(int k, int sz) {
+    return 2 * (size_t)(NF + 2) * (size_t)k * 2 * sz;
+}
+
+template <class TI, class TO, int NF, class Ld, class Ap>
+__device__ void row_pass_fixed(const Params& P, const Tw& tw, int kin, int kout, const cx<TI>* src,
+                               cx<TO>* dst, char* smem, Ld&& ld, Ap&& ap) {
+    using CI = cx<TI>;
+    using CO = cx<TO>;
+    using S = decltype(ld(0ll, 0, 0));
+    constexpr int LOGN = ilog2c(NF), HALF = NF / 2, H1 = HALF + 1, PITCH = NF + 2;
+    constexpr int E = NF / kWarp, EH = (H1 + kWarp - 1) / kWarp;
+    constexpr int GCH = E < 8 ? E : 8;
+    constexpr int NPT = 2 * E, PCH = NPT < kChunk ? NPT : kChunk;
+    const int n0 = P.n0;
+    const WarpCtx w = warp_ctx(P, smem);
+    CI* X0 = (CI*)w.mem;
+    CI* X1 = X0 + (size_t)kin * PITCH;
+    CO* Y0 = (CO*)(X1 + (size_t)kin * PITCH);
+    CO* Y1 = Y0 + (size_t)kout * PITCH;
+    const TI iscale = (TI)(1.0 / ((double)n0 * (double)NF));
+    for (int u = w.gw; u < n0 / 2; u += w.nw) {
+        const int r0 = 2 * u;
+        for (int l = 0; l < kin; l++) {
+            const CI* s0 = src + (size_t)l * H1 * n0 + r0;
+#pragma unroll
+            for (int c = 0; c < E; c += GCH) {
+                CI a[GCH], b[GCH];
+#pragma unroll
+                for (int i = 0; i < GCH; i++) {
+                    const int x = w.lane + kWarp * (c + i);
+                    const int k = (x <= HALF) ? x : NF - x;
+                    a[i] = s0[(size_t)k * n0];
+                    b[i] = s0[(size_t)k * n0 + 1];
+                }
+#pragma unroll
+                for (int i = 0; i < GCH; i++) {
+                    const int x = w.lane + kWarp * (c + i);
+                    CI A = a[i], B = b[i];
+                    if (x == 0 || x == HALF) { A.y = 0; B.y = 0; }
+                    X0[(size_t)l * PITCH + x] = (x <= HALF) ? CI{A.x - B.y, A.y + B.x} : CI{A.x + B.y, B.x - A.y};
+                }
+            }
+        }
+        const CI* Xr = X0;
+        if (kin > 0)
+            Xr = fft_lines_fixed<+1, TI, LOGN, kMaxK>(X0, X1, PITCH, kin, tw_of<TI>(tw), tw.log, w.lane) ? X1 : X0;
+#pragma unroll 1
+        for (int c0 = 0; c0 < NPT; c0 += PCH) {
+            S st[PCH];
+#pragma unroll
+            for (int q = 0; q < PCH; q++) {
+                const int i = (c0 + q) >> 1, rr = (c0 + q) & 1;
+                const int x = w.lane + kWarp * i;
+                st[q] = ld((long long)(r0 + rr) * NF + x, r0 + rr, x);
+            }
+#pragma unroll
+            for (int q = 0; q < PCH; q++) {
+                const int i = (c0 + q) >> 1, rr = (c0 + q) & 1;
+                const int x = w.lane + kWarp * i;
+                TI in[kMaxK];
+                TO out[kMaxK];
+#pragma unroll
+                for (int f = 0; f < kMaxK; f++) {
+                    if (f < kin) {
+                        const CI z = Xr[(size_t)f * PITCH + x];
+                        in[f] = (rr ? z.y : z.x) * iscale;
+                    }
+                }
+                ap((long long)(r0 + rr) * NF + x, r0 + rr, x, st[q], in, out);
+#pragma unroll
+                for (int g = 0; g < kMaxK; g++) {
+                    if (g < kout) {
+                        CO* qq = Y0 + (size_t)g * PITCH + x;
+                        if (rr) qq->y = out[g];
+                        else qq->x = out[g];
+                    }
+                }
+            }
+        }
+        if (kout > 0) {
+            const CO* Yr =
+                fft_lines_fixed<-1, TO, LOGN, kMaxK>(Y0, Y1, PITCH, kout, tw_of<TO>(tw), tw.log, w.lane) ? Y1 : Y0;
+            const TO hf = (TO)0.5;
+            for (int g = 0; g < kout; g++) {
+                CO* d0 = dst + (size_t)g * H1 * n0 + r0;
+                const CO* zl = Yr + (size_t)g * PITCH;
+#pragma unroll
+                for (int i = 0; i < EH; i++) {
+                    const int k = w.lane + kWarp * i;
+                    if (k <= HALF) {
+                        const CO zk = zl[k];
+                        const CO zn = zl[(NF - k) & (NF - 1)];
+                        d0[(size_t)k * n0] = CO{hf * (zk.x + zn.x), hf * (zk.y - zn.y)};
+                        d0[(size_t)k * n0 + 1] = CO{hf * (zk.y + zn.y), hf * (zn.x - zk.x)};
+                    }
+                }
+            }
+        }
+        warp_sync();
+    }
+}
+
+template <class T, int NF, class Ld, class Ap>
+__device__ void col_pass_fixed(const Params& P, const Tw& tw, int kin, int kout, const cx<T>* src, cx<T>* dst,
+                               char* smem, Ld&& ld, Ap&& ap) {
+    using C = cx<T>;
+    using S = decltype(ld(0, 0));
+    constexpr int LOGN = ilog2c(NF), PITCH = NF + 2, E = NF / kWarp;
+    constexpr int GCH = E < 8 ? E : 8;
+    constexpr int PCH = E < kChunk ? E : kChunk;
+    const int h1 = P.h1;
+    const int kl = kin > kout ? kin : kout;
+    const WarpCtx w = warp_ctx(P, smem);
+    C* B0 = (C*)w.mem;
+    C* B1 = B0 + (size_t)kl * PITCH;
+    for (int k1 = w.gw; k1 < h1; k1 += w.nw) {
+        for (int f = 0; f < kin; f++) {
+            const C* s = src + (size_t)f * h1 * NF + (size_t)k1 * NF;
+#pragma unroll
+            for (int c = 0; c < E; c += GCH) {
+                C v[GCH];
+#pragma unroll
+                for (int i = 0; i < GCH; i++) v[i] = s[w.lane + kWarp * (c + i)];
+#pragma unroll
+                for (int i = 0; i < GCH; i++) B0[(size_t)f * PITCH + w.lane + kWarp * (c + i)] = v[i];
+            }
+        }
+        const C* Xr = B0;
+        C* Xo = B1;
+        if (kin > 0) {
+            const int r = fft_lines_fixed<-1, T, LOGN, kMaxK>(B0, B1, PITCH, kin, tw_of<T>(tw), tw.log, w.lane);
+            Xr = r ? B1 : B0;
+            Xo = r ? B0 : B1;
+        }
+#pragma unroll 1
+        for (int c0 = 0; c0 < E; c0 += PCH) {
+            S st[PCH];
+#pragma unroll
+            for (int q = 0; q < PCH; q++) st[q] = ld(k1, w.lane + kWarp * (c0 + q));
+#pragma unroll
+            for (int q = 0; q < PCH; q++) {
+                const int k0 = w.lane + kWarp * (c0 + q);
+                C in[kMaxK];
+                C out[kMaxK];
+#pragma unroll
+                for (int f = 0; f < kMaxK; f++)
+                    if (f < kin) in[f] = Xr[(size_t)f * PITCH + k0];
+                ap(k1, k0, st[q], in, out);
+#pragma unroll
+                for (int g = 0; g < kMaxK; g++)
+                    if (g < kout) Xo[(size_t)g * PITCH + k0] = out[g];
+            }
+        }
+        if (kout > 0) {
+            C* scratch = (C*)Xr;
+            const int r = fft_lines_fixed<+1, T, LOGN, kMaxK>(Xo, scratch, PITCH, kout, tw_of<T>(tw), tw.log, w.lane);
+            const C* Yr = r ? scratch : Xo;
+            for (int g = 0; g < kout; g++) {
+                C* d = dst + (size_t)g * h1 * NF + (size_t)k1 * NF;
+#pragma unroll
+                for (int i = 0; i < E; i++) d[w.lane + kWarp * i] = Yr[(size_t)g * PITCH + w.lane + kWarp * i];
+            }
+        }
+        warp_sync();
+    }
+}
+
+// dispatch: NF = 0 runs the runtime-length passes
+template <class TI, class TO, int NF, class Ld, class Ap>
+__device__ __forceinline__ void rowp(const Params& P, const Tw& tw, int kin, int kout, const cx<TI>* src,
+                                     cx<TO>* dst, char* smem, Ld&& ld, Ap&& ap) {
+    if constexpr (NF == 0) {
+        row_pass<TI, TO>(P, tw, kin, kout, src, dst, smem,
+                         [&](long long p, int row, int x, const TI* in, TO* out) {
+                             const auto s = ld(p, row, x);
+                             ap(p, row, x, s, in, out);
+                         });
+    } else {
+        row_pass_fixed<TI, TO, NF>(P, tw, kin, kout, src, dst, smem, ld, ap);
+    }
+}
+
+template <class T, int NF, class Ld, class Ap>
+__device__ __forceinline__ void colp(const Params& P, const Tw& tw, int kin, int kout, const cx<T>* src,
+                                     cx<T>* dst, char* smem, Ld&& ld, Ap&& ap) {
+    if constexpr (NF == 0) {
+        col_pass<T>(P, tw, kin, kout, src, dst, smem, [&](int k1, int k0, const cx<T>* in, cx<T>* out) {
+            const auto s = ld(k1, k0);
+            ap(k1, k0, s, in, out);
+        });
+    } else {
+        col_pass_fixed<T, NF>(P, tw, kin, kout, src, dst, smem, ld, ap);
+    }
+}
+
+struct Nil {};
+
 // ------------------------------------------------------------ phase bodies
 
 // number of fields in the iteration passes: PFC transforms v^3 differences and
@@ -402,7 +613,7 @@ __host__ __device__ __forceinline__ int k_base(int model) { return model == M_PF
 // base argument VB, history term g and preconditioner sums, or a move of the
 // base to the current candidate (mixed precision), (3) the forward x-DFT of the
 // FP64 base fields (VB, g[, VB^3]).
-template <class T>
+template <class T, int NF>
 __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red) {
     const StepK k = step_coeffs(P, c.step);
     const int bank = c.step & 1;
@@ -438,40 +649,56 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
     const double e2 = P.eps * P.eps;
     const int kb = k_base(P.model);
     const bool pfc = P.model == M_PFC;
+    const bool reb = c.reb != 0, acc = c.acc != 0;
     const double ith = 1.0 / k.thv, wth = 1.0 - k.thv;
-    row_pass<double, double>(P, tw, 0, kb, (const double2*)nullptr, P.NB64, smem,
-                             [&](long long p, int, int, const double*, double* out) {
-                                 double vb, g;
-                                 if (c.reb) {
-                                     vb = P.VB[p] + ((double)dreb[p] - mreb);
-                                     g = P.G64[p];
-                                 } else {
-                                     if (c.acc) {
-                                         const double va = P.VB[p] + ((double)dacc[p] - macc);
-                                         P.U[c.acc_cur ^ 1][p] = (va - wth * P.U[c.acc_cur][p]) * ith;
-                                     }
-                                     const double a = P.U[c.cur][p], b = P.U[c.cur ^ 1][p];
-                                     const double x0 = a + k.rho * (a - b);
-                                     vb = k.thv * x0 + (1.0 - k.thv) * a;
-                                     g = k.b * a + k.c * b - k.gun * a;
-                                     P.G64[p] = g;
-                                     if (pfc) {
-                                         s0 += 3.0 * vb * vb + 1.0 - P.eps;
-                                     } else {
-                                         const double f1 = dF1(vb, P.tau), f2 = dF2(vb, P.tau), f3 = dF3(vb, P.tau);
-                                         s0 += f2 * f2 - P.eta2 * f2 + f3 * f1;
-                                         s2 += e2 * (f2 - P.eta1);
-                                     }
-                                 }
-                                 P.VB[p] = vb;
-                                 vbt[p] = (T)vb;
-                                 d0[p] = (T)0;
-                                 d1[p] = (T)0;
-                                 out[0] = vb;
-                                 out[1] = g;
-                                 if (pfc) out[2] = vb * vb * vb;
-                             });
-    if (!c.reb) {
+    double* U0 = P.U[c.cur];
+    double* U1 = P.U[c.cur ^ 1];
+    struct St { double vb, g, a, b, d; };
+    rowp<double, double, NF>(
+        P, tw, 0, kb, (const double2*)nullptr, P.NB64, smem,
+        [&](long long p, int, int) {
+            St s;
+            s.vb = P.VB[p];
+            s.g = P.G64[p];
+            s.d = reb ? (double)dreb[p] : (acc ? (double)dacc[p] : 0.0);
+            s.a = reb ? 0.0 : U0[p];   // (before acceptance) u^n of the previous step if acc
+            s.b = reb ? 0.0 : U1[p];
+            return s;
+        },
+        [&](long long p, int, int, const St& s, const double*, double* out) {
+            double vb, g;
+            if (reb) {
+                vb = s.vb + (s.d - mreb);
+                g = s.g;
+            } else {
+                double a = s.a, b = s.b;
+                if (acc) {
+                    // U1 is the previous step's u^n; the accepted u^{n+1} goes to U0
+                    const double va = s.vb + (s.d - macc);
+                    a = (va - wth * s.b) * ith;
+                    U0[p] = a;
+                }
+                const double x0 = a + k.rho * (a - b);
+                vb = k.thv * x0 + (1.0 - k.thv) * a;
+                g = k.b * a + k.c * b - k.gun * a;
+                P.G64[p] = g;
+                if (pfc) {
+                    s0 += 3.0 * vb * vb + 1.0 - P.eps;
+                } else {
+                    const double f1 = dF1(vb, P.tau), f2 = dF2(vb, P.tau), f3 = dF3(vb, P.tau);
+                    s0 += f2 * f2 - P.eta2 * f2 + f3 * f1;
+                    s2 += e2 * (f2 - P.eta1);
+                }
+            }
+            P.VB[p] = vb;
+            vbt[p] = (T)vb;
+            d0[p] = (T)0;
+            d1[p] = (T)0;
+            out[0] = vb;
+            out[1] = g;
+            if (pfc) out[2] = vb * vb * vb;
+        });
+    if (!reb) {
         s0 = block_sum(s0, red);
         if (threadIdx.x == 0) atomicAdd(&P.sc->beta_sum[bank][0], s0);
         if (!pfc) {
@@ -503,7 +730,7 @@ __device__ __forceinline__ void base_direction(const Params& P, const StepK& k, 
     S1[idx] = cx<T>{(T)(k.ts * d.x), (T)(k.ts * d.y)};
 }
 
-template <class T>
+template <class T, int NF>
 __device__ void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     const StepK k = step_coeffs(P, c.step);
     const Beta B = betas(P, k, c.step);
@@ -511,8 +738,8 @@ __device__ void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem)
     const double iM = 1.0 / P.M;
     const double e4 = P.eps * P.eps * P.eps * P.eps;
     if (P.model == M_PFC) {
-        col_pass<double>(P, tw, kb, 1, P.NB64, P.DB64, smem,
-                         [&](int k1, int k0, const double2* in, double2* out) {
+        colp<double, NF>(P, tw, kb, 1, P.NB64, P.DB64, smem, [&](int, int) { return Nil{}; },
+                         [&](int k1, int k0, const Nil&, const double2* in, double2* out) {
                              const double kap = kappa_at(P, k1, k0);
                              const double2 v = in[0], g = in[1], nl = in[2];
                              double2 G{0.0, 0.0};
@@ -527,8 +754,8 @@ __device__ void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem)
                              out[0] = d;
                          });
     } else {
-        col_pass<double>(P, tw, kb, 1, P.NB64, P.DB64, smem,
-                         [&](int k1, int k0, const double2* in, double2* out) {
+        colp<double, NF>(P, tw, kb, 1, P.NB64, P.DB64, smem, [&](int, int) { return Nil{}; },
+                         [&](int k1, int k0, const Nil&, const double2* in, double2* out) {
                              const double kap = kappa_at(P, k1, k0);
                              const double2 v = in[0], g = in[1];
                              double2 G{0.0, 0.0};
@@ -545,31 +772,31 @@ __device__ void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem)
 
 // FCH: physical Lap VB, then forward x-DFT of (F'(VB), P(VB)) where
 // P = -eps^2 (F'' - eta1) Lap v + (F'' - eta2) F'  (the non-Laplacian part of mu).
-template <class T>
+template <class T, int NF>
 __device__ void phase_D(const Params& P, const Tw& tw, char* smem) {
     T* lbt = (T*)P.LBt;
     const double e2 = P.eps * P.eps;
-    row_pass<double, double>(P, tw, 1, 2, P.DB64, P.NB64, smem,
-                             [&](long long p, int, int, const double* in, double* out) {
+    rowp<double, double, NF>(P, tw, 1, 2, P.DB64, P.NB64, smem,
+                             [&](long long p, int, int) { return P.VB[p]; },
+                             [&](long long p, int, int, const double& vb, const double* in, double* out) {
                                  const double lb = in[0];
                                  lbt[p] = (T)lb;
-                                 const double vb = P.VB[p];
                                  const double f1 = dF1(vb, P.tau), f2 = dF2(vb, P.tau);
                                  out[0] = f1;
                                  out[1] = -e2 * (f2 - P.eta1) * lb + (f2 - P.eta2) * f1;
                              });
 }
 
-template <class T>
+template <class T, int NF>
 __device__ void phase_E(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     const StepK k = step_coeffs(P, c.step);
     const Beta B = betas(P, k, c.step);
     const double e2 = P.eps * P.eps;
     const double l1 = lam_at(P, 1);
-    col_pass<double>(P, tw, 2, 2, P.NB64, P.DB64, smem,
-                     [&](int k1, int k0, const double2* in, double2* out) {
+    colp<double, NF>(P, tw, 2, 2, P.NB64, P.DB64, smem,
+                     [&](int k1, int k0) { return P.CL64[(long long)k1 * P.n0 + k0]; },
+                     [&](int k1, int k0, const double2& lin, const double2* in, double2* out) {
                          const double kap = kappa_at(P, k1, k0);
-                         const double2 lin = P.CL64[(long long)k1 * P.n0 + k0];
                          double2 G{0.0, 0.0};
                          if (kap != 0.0) {
                              G.x = lin.x + e2 * kap * in[0].x + in[1].x;
@@ -586,7 +813,7 @@ __device__ void phase_E(const Params& P, const Ctl& c, const Tw& tw, char* smem)
 // Iteration row pass (R1 reads the FP64 base direction, RI the T one):
 // delta_it = ybar_{it-1} + theta_v s d_{it-1}; ||d_{it-1}||_inf; then the
 // nonlinear differences at ybar_it and their forward x-DFT.
-template <class TI, class T>
+template <class TI, class T, int NF>
 __device__ void phase_R(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red,
                         const cx<TI>* src) {
     const StepK k = step_coeffs(P, c.step);
@@ -601,29 +828,37 @@ __device__ void phase_R(const Params& P, const Ctl& c, const Tw& tw, char* smem,
     const T tau = (T)P.tau, e2 = (T)(P.eps * P.eps), eta1 = (T)P.eta1, eta2 = (T)P.eta2;
     double amax = 0.0, asum = 0.0;
     const bool pfc = P.model == M_PFC;
-    row_pass<TI, T>(P, tw, K, K, src, (cx<T>*)P.NB, smem,
-                    [&](long long p, int, int, const TI* in, T* out) {
-                        const TI dd = in[0];
-                        const T dp = dprev[p], dpp = dcur[p];
-                        const T de = dp + lp * (dp - dpp) + ts * (T)dd;
-                        dcur[p] = de;
-                        amax = nanmax(amax, fabs((double)dd));
-                        asum += (double)de;
-                        const T y = de + l * (de - dp);
-                        const T b = vbt[p];
-                        if (pfc) {
-                            out[0] = y * ((T)3 * b * b + (T)3 * b * y + y * y);
-                        } else {
-                            const T lb = lbt[p];
-                            const T ly = (T)in[1];
-                            const T f1b = dF1(b, tau), f2b = dF2(b, tau);
-                            const T df1 = y * ((T)3 * b * b + (T)3 * b * y + y * y + tau * ((T)2 * b + y) - (T)1);
-                            const T df2 = y * ((T)6 * b + (T)3 * y + (T)2 * tau);
-                            const T f1n = f1b + df1, f2n = f2b + df2;
-                            out[0] = df1;
-                            out[1] = -e2 * (df2 * lb + (f2n - eta1) * ly) + df2 * f1n + (f2b - eta2) * df1;
-                        }
-                    });
+    struct St { T dp, dpp, b, lb; };
+    rowp<TI, T, NF>(
+        P, tw, K, K, src, (cx<T>*)P.NB, smem,
+        [&](long long p, int, int) {
+            St s;
+            s.dp = dprev[p];
+            s.dpp = dcur[p];
+            s.b = vbt[p];
+            s.lb = pfc ? (T)0 : lbt[p];
+            return s;
+        },
+        [&](long long p, int, int, const St& s, const TI* in, T* out) {
+            const TI dd = in[0];
+            const T de = s.dp + lp * (s.dp - s.dpp) + ts * (T)dd;
+            dcur[p] = de;
+            amax = nanmax(amax, fabs((double)dd));
+            asum += (double)de;
+            const T y = de + l * (de - s.dp);
+            const T b = s.b;
+            if (pfc) {
+                out[0] = y * ((T)3 * b * b + (T)3 * b * y + y * y);
+            } else {
+                const T ly = (T)in[1];
+                const T f1b = dF1(b, tau), f2b = dF2(b, tau);
+                const T df1 = y * ((T)3 * b * b + (T)3 * b * y + y * y + tau * ((T)2 * b + y) - (T)1);
+                const T df2 = y * ((T)6 * b + (T)3 * y + (T)2 * tau);
+                const T f1n = f1b + df1, f2n = f2b + df2;
+                out[0] = df1;
+                out[1] = -e2 * (df2 * s.lb + (f2n - eta1) * ly) + df2 * f1n + (f2b - eta2) * df1;
+            }
+        });
     amax = block_max(amax, red);
     if (threadIdx.x == 0) atomicMax(&P.norms[(size_t)bank * P.nslots + c.ev], dbl_bits(amax));
     asum = block_sum(asum, red);
@@ -633,7 +868,7 @@ __device__ void phase_R(const Params& P, const Ctl& c, const Tw& tw, char* smem,
 // Iteration column pass: ybar_hat, spectral residual (Eq. obj:G' with the
 // zero mode removed), d_hat = r_hat / Lcal_hat (Algorithm 2), the spectral
 // state update, and the inverse y-DFT of d (and of Lap ybar_{it+1} for FCH).
-template <class T>
+template <class T, int NF>
 __device__ void phase_CI(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     using C = cx<T>;
     const StepK k = step_coeffs(P, c.step);
@@ -646,36 +881,42 @@ __device__ void phase_CI(const Params& P, const Ctl& c, const Tw& tw, char* smem
     const int K = k_iter(P.model);
     const bool pfc = P.model == M_PFC;
     const double iM = 1.0 / P.M, e2 = P.eps * P.eps, e4 = e2 * e2;
-    col_pass<T>(P, tw, K, K, (const C*)P.NB, (C*)P.DB, smem,
-                [&](int k1, int k0, const C* in, C* out) {
-                    const long long idx = (long long)k1 * P.n0 + k0;
-                    const double kap = kappa_at(P, k1, k0);
-                    const C sc = scur[idx], sp = sprev[idx];
-                    const C yh = C{sc.x + l * (sc.x - sp.x), sc.y + l * (sc.y - sp.y)};
-                    C d{(T)0, (T)0};
-                    if (kap != 0.0) {
-                        const C g0 = C0[idx];
-                        const double Lk = B.m2 / kap + B.b0 + B.b2 * kap + B.b4 * kap * kap;
-                        const T il = (T)(-1.0 / Lk);
-                        if (pfc) {
-                            const T m = (T)(k.Ai * iM / kap + 1.0 - P.eps - 2.0 * kap + kap * kap);
-                            d.x = il * (g0.x + m * yh.x + in[0].x);
-                            d.y = il * (g0.y + m * yh.y + in[0].y);
-                        } else {
-                            const T m = (T)(k.Ai * iM / kap + e4 * kap * kap);
-                            const T e2k = (T)(e2 * kap);
-                            d.x = il * (g0.x + m * yh.x + e2k * in[0].x + in[1].x);
-                            d.y = il * (g0.y + m * yh.y + e2k * in[0].y + in[1].y);
-                        }
-                    }
-                    const C sn = C{yh.x + ts * d.x, yh.y + ts * d.y};
-                    sprev[idx] = sn;
-                    out[0] = d;
-                    if (!pfc) {
-                        const T f = (T)(-kap);
-                        out[1] = C{f * (sn.x + ln * (sn.x - sc.x)), f * (sn.y + ln * (sn.y - sc.y))};
-                    }
-                });
+    struct St { C sc, sp, g0; };
+    colp<T, NF>(
+        P, tw, K, K, (const C*)P.NB, (C*)P.DB, smem,
+        [&](int k1, int k0) {
+            const long long idx = (long long)k1 * P.n0 + k0;
+            return St{scur[idx], sprev[idx], C0[idx]};
+        },
+        [&](int k1, int k0, const St& s, const C* in, C* out) {
+            const long long idx = (long long)k1 * P.n0 + k0;
+            const double kap = kappa_at(P, k1, k0);
+            const C sc = s.sc, sp = s.sp;
+            const C yh = C{sc.x + l * (sc.x - sp.x), sc.y + l * (sc.y - sp.y)};
+            C d{(T)0, (T)0};
+            if (kap != 0.0) {
+                const C g0 = s.g0;
+                const double Lk = B.m2 / kap + B.b0 + B.b2 * kap + B.b4 * kap * kap;
+                const T il = (T)(-1.0 / Lk);
+                if (pfc) {
+                    const T m = (T)(k.Ai * iM / kap + 1.0 - P.eps - 2.0 * kap + kap * kap);
+                    d.x = il * (g0.x + m * yh.x + in[0].x);
+                    d.y = il * (g0.y + m * yh.y + in[0].y);
+                } else {
+                    const T m = (T)(k.Ai * iM / kap + e4 * kap * kap);
+                    const T e2k = (T)(e2 * kap);
+                    d.x = il * (g0.x + m * yh.x + e2k * in[0].x + in[1].x);
+                    d.y = il * (g0.y + m * yh.y + e2k * in[0].y + in[1].y);
+                }
+            }
+            const C sn = C{yh.x + ts * d.x, yh.y + ts * d.y};
+            sprev[idx] = sn;
+            out[0] = d;
+            if (!pfc) {
+                const T f = (T)(-kap);
+                out[1] = C{f * (sn.x + ln * (sn.x - sc.x)), f * (sn.y + ln * (sn.y - sc.y))};
+            }
+        });
 }
 
 // Accept of the last step of a launch: u^{n+1} = (VB + delta - mean(delta)
@@ -707,7 +948,7 @@ __device__ void phase_accept(const Params& P, const Ctl& c) {
     }
 }
 
-__device__ void phase_fail(const Params& P, const Ctl& c) {
+inline __device__ void phase_fail(const Params& P, const Ctl& c) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.sc->status = c.fail;
         P.sc->fail_step = c.step;
@@ -719,39 +960,43 @@ __device__ void phase_fail(const Params& P, const Ctl& c) {
 
 // ------------------------------------------------ DFT / energy / mass programs
 
+template <int NF>
 __device__ void phase_fwd_r(const Params& P, const Tw& tw, char* smem) {
-    row_pass<double, double>(P, tw, 0, 1, (const double2*)nullptr, P.NB64, smem,
-                             [&](long long p, int, int, const double*, double* out) {
-                                 out[0] = P.in_real[p];
-                             });
+    rowp<double, double, NF>(P, tw, 0, 1, (const double2*)nullptr, P.NB64, smem,
+                             [&](long long p, int, int) { return P.in_real[p]; },
+                             [&](long long, int, int, const double& u, const double*, double* out) { out[0] = u; });
 }
+template <int NF>
 __device__ void phase_fwd_c(const Params& P, const Tw& tw, char* smem) {
-    col_pass<double>(P, tw, 1, 0, P.NB64, (double2*)nullptr, smem,
-                     [&](int k1, int k0, const double2* in, double2*) {
+    colp<double, NF>(P, tw, 1, 0, P.NB64, (double2*)nullptr, smem, [&](int, int) { return Nil{}; },
+                     [&](int k1, int k0, const Nil&, const double2* in, double2*) {
                          P.out_spec[(long long)k0 * P.h1 + k1] = in[0];
                      });
 }
+template <int NF>
 __device__ void phase_inv_c(const Params& P, const Tw& tw, char* smem) {
-    col_pass<double>(P, tw, 0, 1, (const double2*)nullptr, P.DB64, smem,
-                     [&](int k1, int k0, const double2*, double2* out) {
-                         out[0] = P.in_spec[(long long)k0 * P.h1 + k1];
-                     });
+    colp<double, NF>(P, tw, 0, 1, (const double2*)nullptr, P.DB64, smem,
+                     [&](int k1, int k0) { return P.in_spec[(long long)k0 * P.h1 + k1]; },
+                     [&](int, int, const double2& v, const double2*, double2* out) { out[0] = v; });
 }
+template <int NF>
 __device__ void phase_inv_r(const Params& P, const Tw& tw, char* smem) {
-    row_pass<double, double>(P, tw, 1, 0, P.DB64, (double2*)nullptr, smem,
-                             [&](long long p, int, int, const double* in, double*) {
+    rowp<double, double, NF>(P, tw, 1, 0, P.DB64, (double2*)nullptr, smem,
+                             [&](long long, int, int) { return Nil{}; },
+                             [&](long long p, int, int, const Nil&, const double* in, double*) {
                                  P.out_real[p] = in[0];
                              });
 }
 
 // energy (Eqs. obj:PFC-egy / obj:FCHegy with Fourier differentiation and the
 // trapezoidal rule): red[0] pointwise part, red[1] spectral part
+template <int NF>
 __device__ void phase_en_r(const Params& P, const Tw& tw, char* smem, double* red) {
     double acc = 0.0;
     const bool pfc = P.model == M_PFC;
-    row_pass<double, double>(P, tw, 0, 1, (const double2*)nullptr, P.NB64, smem,
-                             [&](long long p, int, int, const double*, double* out) {
-                                 const double u = P.in_real[p];
+    rowp<double, double, NF>(P, tw, 0, 1, (const double2*)nullptr, P.NB64, smem,
+                             [&](long long p, int, int) { return P.in_real[p]; },
+                             [&](long long, int, int, const double& u, const double*, double* out) {
                                  out[0] = u;
                                  if (pfc) acc += 0.25 * u * u * u * u + 0.5 * (1.0 - P.eps) * u * u;
                              });
@@ -760,12 +1005,13 @@ __device__ void phase_en_r(const Params& P, const Tw& tw, char* smem, double* re
         if (threadIdx.x == 0) atomicAdd(&P.sc->red[0], acc);
     }
 }
+template <int NF>
 __device__ void phase_en_c(const Params& P, const Tw& tw, char* smem, double* red) {
     double acc = 0.0;
     const bool pfc = P.model == M_PFC;
     const int half = P.n1 >> 1;
-    col_pass<double>(P, tw, 1, pfc ? 0 : 1, P.NB64, P.DB64, smem,
-                     [&](int k1, int k0, const double2* in, double2* out) {
+    colp<double, NF>(P, tw, 1, pfc ? 0 : 1, P.NB64, P.DB64, smem, [&](int, int) { return Nil{}; },
+                     [&](int k1, int k0, const Nil&, const double2* in, double2* out) {
                          const double kap = kappa_at(P, k1, k0);
                          const double w = (k1 == 0 || k1 == half) ? 1.0 : 2.0;
                          const double a2 = in[0].x * in[0].x + in[0].y * in[0].y;
@@ -779,19 +1025,20 @@ __device__ void phase_en_c(const Params& P, const Tw& tw, char* smem, double* re
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) atomicAdd(&P.sc->red[1], acc);
 }
+template <int NF>
 __device__ void phase_en_r2(const Params& P, const Tw& tw, char* smem, double* red) {
     double acc = 0.0;
     const double e2 = P.eps * P.eps;
-    row_pass<double, double>(P, tw, 1, 0, P.DB64, (double2*)nullptr, smem,
-                             [&](long long p, int, int, const double* in, double*) {
-                                 const double u = P.in_real[p];
+    rowp<double, double, NF>(P, tw, 1, 0, P.DB64, (double2*)nullptr, smem,
+                             [&](long long p, int, int) { return P.in_real[p]; },
+                             [&](long long, int, int, const double& u, const double* in, double*) {
                                  const double w = e2 * in[0] - dF1(u, P.tau);
                                  acc += 0.5 * w * w - P.eta2 * Fwell(u, P.tau);
                              });
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) atomicAdd(&P.sc->red[0], acc);
 }
-__device__ void phase_mass(const Params& P, double* red) {
+inline __device__ void phase_mass(const Params& P, double* red) {
     double acc = 0.0;
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gs = (long long)gridDim.x * blockDim.x;
@@ -810,15 +1057,17 @@ __device__ void phase_mass(const Params& P, double* red) {
 //   IM_R1: (FCH) Lap ubreve physical, forward x-DFT of (F'(ub), Q(ub))
 //   IM_C1: (FCH) solve
 //   IM_R2: inverse x-DFT of u^{n+1} -> written over u^{n-1}
+template <int NF>
 __device__ void phase_im_r0(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     const StepK k = step_coeffs(P, c.step);
     const double* un = P.U[c.cur];
     const double* um = P.U[c.cur ^ 1];
     const bool pfc = P.model == M_PFC;
     const bool lmp = P.scheme == S_LMP;
-    row_pass<double, double>(P, tw, 0, 3, (const double2*)nullptr, P.NB64, smem,
-                             [&](long long p, int, int, const double*, double* out) {
-                                 const double a = un[p], b = um[p];
+    rowp<double, double, NF>(P, tw, 0, 3, (const double2*)nullptr, P.NB64, smem,
+                             [&](long long p, int, int) { return double2{un[p], um[p]}; },
+                             [&](long long p, int, int, const double2& ab, const double*, double* out) {
+                                 const double a = ab.x, b = ab.y;
                                  const double ub = lmp ? 0.5 * ((2.0 + k.rho) * a - k.rho * b)
                                                        : a + k.rho * (a - b);
                                  P.VB[p] = ub;
@@ -847,17 +1096,18 @@ __device__ __forceinline__ double2 imex_solve(const Params& P, const StepK& k, d
     const double den = k.a + M * kap * half * Lh;
     return double2{rx / den, ry / den};
 }
+template <int NF>
 __device__ void phase_im_c0(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     const StepK k = step_coeffs(P, c.step);
     if (P.model == M_PFC) {
-        col_pass<double>(P, tw, 3, 1, P.NB64, P.DB64, smem,
-                         [&](int k1, int k0, const double2* in, double2* out) {
+        colp<double, NF>(P, tw, 3, 1, P.NB64, P.DB64, smem, [&](int, int) { return Nil{}; },
+                         [&](int k1, int k0, const Nil&, const double2* in, double2* out) {
                              const double kap = kappa_at(P, k1, k0);
                              out[0] = imex_solve(P, k, kap, in[0], in[1], in[2]);
                          });
     } else {
-        col_pass<double>(P, tw, 3, 1, P.NB64, P.DB64, smem,
-                         [&](int k1, int k0, const double2* in, double2* out) {
+        colp<double, NF>(P, tw, 3, 1, P.NB64, P.DB64, smem, [&](int, int) { return Nil{}; },
+                         [&](int k1, int k0, const Nil&, const double2* in, double2* out) {
                              const double kap = kappa_at(P, k1, k0);
                              const long long idx = (long long)k1 * P.n0 + k0;
                              P.CL64[idx] = in[1];
@@ -866,36 +1116,43 @@ __device__ void phase_im_c0(const Params& P, const Ctl& c, const Tw& tw, char* s
                          });
     }
 }
+template <int NF>
 __device__ void phase_im_r1(const Params& P, const Tw& tw, char* smem) {
     // N(u) = -kappa0 u - eps^2 Lap F'(u) - (eps^2 (F'' - eta1) - kappa2) Lap u + (F'' - eta2) F'
     const double e2 = P.eps * P.eps, kap0 = 1.0 - 2.0 * P.tau * P.tau + P.eta2;
-    row_pass<double, double>(P, tw, 1, 2, P.DB64, P.NB64, smem,
-                             [&](long long p, int, int, const double* in, double* out) {
-                                 const double ub = P.VB[p], lu = in[0];
+    rowp<double, double, NF>(P, tw, 1, 2, P.DB64, P.NB64, smem,
+                             [&](long long p, int, int) { return P.VB[p]; },
+                             [&](long long, int, int, const double& ub, const double* in, double* out) {
+                                 const double lu = in[0];
                                  const double f1 = dF1(ub, P.tau), f2 = dF2(ub, P.tau);
                                  out[0] = f1;
                                  out[1] = -kap0 * ub - (e2 * (f2 - P.eta1) - 1.0) * lu + (f2 - P.eta2) * f1;
                              });
 }
+template <int NF>
 __device__ void phase_im_c1(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     const StepK k = step_coeffs(P, c.step);
     const double e2 = P.eps * P.eps;
-    col_pass<double>(P, tw, 2, 1, P.NB64, P.DB64, smem,
-                     [&](int k1, int k0, const double2* in, double2* out) {
-                         const double kap = kappa_at(P, k1, k0);
+    struct St { double2 un, um; };
+    colp<double, NF>(P, tw, 2, 1, P.NB64, P.DB64, smem,
+                     [&](int k1, int k0) {
                          const long long idx = (long long)k1 * P.n0 + k0;
-                         const double2 unh = P.CL64[idx];
-                         const double2 umh = P.CL64[idx + (long long)P.h1 * P.n0];
+                         return St{P.CL64[idx], P.CL64[idx + (long long)P.h1 * P.n0]};
+                     },
+                     [&](int k1, int k0, const St& s, const double2* in, double2* out) {
+                         const double kap = kappa_at(P, k1, k0);
                          // -eps^2 Lap F' -> + eps^2 kappa F'_hat
                          const double2 nh{e2 * kap * in[0].x + in[1].x, e2 * kap * in[0].y + in[1].y};
-                         out[0] = imex_solve(P, k, kap, nh, unh, umh);
+                         out[0] = imex_solve(P, k, kap, nh, s.un, s.um);
                      });
 }
+template <int NF>
 __device__ void phase_im_r2(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     double* unew = P.U[c.cur ^ 1];
     const bool last = (c.step + 1 == P.nsteps) && P.out_real;
-    row_pass<double, double>(P, tw, 1, 0, P.DB64, (double2*)nullptr, smem,
-                             [&](long long p, int, int, const double* in, double*) {
+    rowp<double, double, NF>(P, tw, 1, 0, P.DB64, (double2*)nullptr, smem,
+                             [&](long long, int, int) { return Nil{}; },
+                             [&](long long p, int, int, const Nil&, const double* in, double*) {
                                  unew[p] = in[0];
                                  if (last) P.out_real[p] = in[0];
                              });
@@ -1011,52 +1268,74 @@ __device__ void ctl_advance(const Params& P, Ctl& c) {
     }
 }
 
-template <class T>
+template <class T, int NF>
 __device__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red) {
     switch (c.ph) {
-        case PH_B: phase_B<T>(P, c, tw, smem, red); break;
-        case PH_C: phase_C<T>(P, c, tw, smem); break;
-        case PH_D: phase_D<T>(P, tw, smem); break;
-        case PH_E: phase_E<T>(P, c, tw, smem); break;
-        case PH_R1: phase_R<double, T>(P, c, tw, smem, red, P.DB64); break;
-        case PH_RI: phase_R<T, T>(P, c, tw, smem, red, (const cx<T>*)P.DB); break;
-        case PH_CI: phase_CI<T>(P, c, tw, smem); break;
+        case PH_B: phase_B<T, NF>(P, c, tw, smem, red); break;
+        case PH_C: phase_C<T, NF>(P, c, tw, smem); break;
+        case PH_D: phase_D<T, NF>(P, tw, smem); break;
+        case PH_E: phase_E<T, NF>(P, c, tw, smem); break;
+        case PH_R1: phase_R<double, T, NF>(P, c, tw, smem, red, P.DB64); break;
+        case PH_RI: phase_R<T, T, NF>(P, c, tw, smem, red, (const cx<T>*)P.DB); break;
+        case PH_CI: phase_CI<T, NF>(P, c, tw, smem); break;
         case PH_ACCEPT: phase_accept<T>(P, c); break;
         case PH_FAIL: phase_fail(P, c); break;
-        case PH_FWD_R: phase_fwd_r(P, tw, smem); break;
-        case PH_FWD_C: phase_fwd_c(P, tw, smem); break;
-        case PH_INV_C: phase_inv_c(P, tw, smem); break;
-        case PH_INV_R: phase_inv_r(P, tw, smem); break;
-        case PH_EN_R: phase_en_r(P, tw, smem, red); break;
-        case PH_EN_C: phase_en_c(P, tw, smem, red); break;
-        case PH_EN_R2: phase_en_r2(P, tw, smem, red); break;
+        case PH_FWD_R: phase_fwd_r<NF>(P, tw, smem); break;
+        case PH_FWD_C: phase_fwd_c<NF>(P, tw, smem); break;
+        case PH_INV_C: phase_inv_c<NF>(P, tw, smem); break;
+        case PH_INV_R: phase_inv_r<NF>(P, tw, smem); break;
+        case PH_EN_R: phase_en_r<NF>(P, tw, smem, red); break;
+        case PH_EN_C: phase_en_c<NF>(P, tw, smem, red); break;
+        case PH_EN_R2: phase_en_r2<NF>(P, tw, smem, red); break;
         case PH_MASS: phase_mass(P, red); break;
-        case PH_IM_R0: phase_im_r0(P, c, tw, smem); break;
-        case PH_IM_C0: phase_im_c0(P, c, tw, smem); break;
-        case PH_IM_R1: phase_im_r1(P, tw, smem); break;
-        case PH_IM_C1: phase_im_c1(P, c, tw, smem); break;
-        case PH_IM_R2: phase_im_r2(P, c, tw, smem); break;
+        case PH_IM_R0: phase_im_r0<NF>(P, c, tw, smem); break;
+        case PH_IM_C0: phase_im_c0<NF>(P, c, tw, smem); break;
+        case PH_IM_R1: phase_im_r1<NF>(P, tw, smem); break;
+        case PH_IM_C1: phase_im_c1<NF>(P, c, tw, smem); break;
+        case PH_IM_R2: phase_im_r2<NF>(P, c, tw, smem); break;
         default: break;
     }
 }
 
-// shared memory per warp needed by any phase (bytes, 16-byte multiple)
-inline size_t warp_smem_bytes(int n0, int n1, int model, int tsize) {
+// shared memory per warp needed by any phase (bytes, 16-byte multiple);
+// nf = 0: runtime-length passes, else the fixed-length ones
+inline size_t warp_smem_bytes(int n0, int n1, int model, int tsize, int nf) {
     size_t m = 0;
     auto upd = [&](size_t v) { if (v > m) m = v; };
     const int ki = k_iter(model);
-    upd(row_warp_smem(n1, 0, 8, 3, 8));            // B (PFC: 3 fields) / IMEX R0
-    upd(row_warp_smem(n1, 1, 8, 2, 8));            // D / IMEX R1 / energy / DFT
-    upd(row_warp_smem(n1, 0, 8, 1, 8));
-    upd(row_warp_smem(n1, ki, 8, ki, tsize));      // R1
-    upd(row_warp_smem(n1, ki, tsize, ki, tsize));  // RI
-    upd(col_warp_smem(n0, 3, 8));                  // C / IMEX C0
-    upd(col_warp_smem(n0, 2, 8));                  // E
-    upd(col_warp_smem(n0, ki, tsize));             // CI
+    if (nf == 0) {
+        upd(row_warp_smem(n1, 0, 8, 3, 8));            // B (PFC: 3 fields) / IMEX R0
+        upd(row_warp_smem(n1, 1, 8, 2, 8));            // D / IMEX R1 / energy / DFT
+        upd(row_warp_smem(n1, 0, 8, 1, 8));
+        upd(row_warp_smem(n1, ki, 8, ki, tsize));      // R1
+        upd(row_warp_smem(n1, ki, tsize, ki, tsize));  // RI
+        upd(col_warp_smem(n0, 3, 8));                  // C / IMEX C0
+        upd(col_warp_smem(n0, 2, 8));                  // E
+        upd(col_warp_smem(n0, ki, tsize));             // CI
+    } else {
+        const size_t p = (size_t)(nf + 2);
+        auto rowf = [&](int kin, int szin, int kout, int szout) {
+            return 2 * p * ((size_t)kin * 2 * szin + (size_t)kout * 2 * szout);
+        };
+        auto colf = [&](int k, int sz) { return 2 * p * (size_t)k * 2 * sz; };
+        upd(rowf(0, 8, 3, 8));
+        upd(rowf(1, 8, 2, 8));
+        upd(rowf(ki, 8, ki, tsize));
+        upd(rowf(ki, tsize, ki, tsize));
+        upd(colf(3, 8));
+        upd(colf(2, 8));
+        upd(colf(ki, tsize));
+    }
     return (m + 15) & ~(size_t)15;
 }
 
 // twiddle tables in shared memory: 1 << logtw entries, FP64 then FP32
 __host__ __device__ inline size_t tw_smem_bytes(int logtw) { return ((size_t)1 << logtw) * (16 + 8); }
+
+// the fixed line length used for an n0 x n1 grid (0: runtime-length passes)
+inline int fixed_len(int n0, int n1) {
+    if (n0 != n1) return 0;
+    return (n0 == 64 || n0 == 128 || n0 == 256 || n0 == 512) ? n0 : 0;
+}
 
 }  // namespace pagd

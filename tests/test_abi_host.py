@@ -97,7 +97,7 @@ def _oracle_problem(model, n, L, eps, eta1, eta2, tau, scheme):
                      scheme={"bdf2": O.BDF2, "mp": O.MP, "lbdf2": O.LBDF2, "lmp": O.LMP}[scheme])
 
 
-@pytest.mark.parametrize("n", [(8, 8), (16, 32), (64, 16)])
+@pytest.mark.parametrize("n", [(8, 8), (16, 32), (64, 16), (64, 64), (128, 128)])
 def test_emulated_dft_matches_oracle(emu, n):
     S = pagd.Solver("pfc", n, (3.0, 5.0), 0.1, lib=emu)
     u = I.noisy_field(n, 0.1, 0.5, 3)
@@ -110,6 +110,10 @@ def test_emulated_dft_matches_oracle(emu, n):
 
 CASES = [
     ("pfc", (16, 16), (8 * math.pi,) * 2, 0.25, 0, 0, 0, "mp", 0.5, 0.1),
+    # square 64 / 128 grids run the fixed-length passes
+    ("pfc", (64, 64), (32 * math.pi,) * 2, 0.25, 0, 0, 0, "bdf2", 0.5, 0.1),
+    ("fch", (64, 64), (4 * math.pi,) * 2, 0.1, 0.1, 0.1, 0.0, "bdf2", 0.001, -0.3),
+    ("fch", (128, 128), (4 * math.pi,) * 2, 0.1, 0.05, 0.07, 0.1, "mp", 0.001, -0.3),
     ("pfc", (16, 32), (8 * math.pi, 16 * math.pi), 0.25, 0, 0, 0, "bdf2", 0.5, 0.1),
     ("fch", (16, 16), (2 * math.pi,) * 2, 0.18, 0.0324, 0.0324, 0, "bdf2", 0.01, -0.3),
     ("fch", (32, 16), (2 * math.pi, math.pi), 0.18, 0.05, 0.07, 0.1, "mp", 0.01, -0.3),
