@@ -55,7 +55,7 @@ struct pagd_solver {
 
 enum {
     O_SC, O_NORMS, O_SUMS, O_STATS, O_TW64, O_TW32, O_U0, O_U1, O_VB, O_G64, O_VBT, O_LBT, O_DD0,
-    O_DD1, O_SS0, O_SS1, O_C0, O_NB, O_DB, O_CL64, O_NB64, O_DB64, O_END
+    O_DD1, O_SS0, O_SS1, O_C0, O_NB, O_DB, O_CL64, O_NB64, O_DB64, O_MASS, O_END
 };
 
 static pagd_status fail(pagd_solver* s, pagd_status st, const char* msg) {
@@ -89,6 +89,7 @@ static void plan_layout(pagd_solver* s) {
     sz[O_CL64] = sizeof(double2) * H * 3;
     sz[O_NB64] = sizeof(double2) * H * 3;
     sz[O_DB64] = sizeof(double2) * H * 2;
+    sz[O_MASS] = sizeof(double) * 2;
     size_t o = 0;
     for (int i = 0; i < O_END; i++) {
         s->off[i] = o;
@@ -154,6 +155,7 @@ static Params base_params(const pagd_solver* s) {
     P.CL64 = (double2*)(w + s->off[O_CL64]);
     P.NB64 = (double2*)(w + s->off[O_NB64]);
     P.DB64 = (double2*)(w + s->off[O_DB64]);
+    P.mass = (double*)(w + s->off[O_MASS]);
     return P;
 }
 
@@ -387,6 +389,7 @@ pagd_status pagd_set_state(pagd_solver* s, const double* u0_dev) {
     s->cur = 0;
     pagd_status st = dcopy(s, s->ws + s->off[O_U0], u0_dev, b);
     if (st == PAGD_OK) st = dcopy(s, s->ws + s->off[O_U1], u0_dev, b);
+    if (st == PAGD_OK) st = dzero(s, s->ws + s->off[O_MASS], 2 * sizeof(double));
     if (st == PAGD_OK) st = dsync(s);
     if (st != PAGD_OK) return st;
     s->have_state = 1;
@@ -480,6 +483,7 @@ pagd_status pagd_run_host(pagd_solver* s, const double* u0_host, double* u_host_
     s->cur = 0;
     pagd_status st = dcopy(s, s->ws + s->off[O_U0], u0_host, b);
     if (st == PAGD_OK) st = dcopy(s, s->ws + s->off[O_U1], u0_host, b);
+    if (st == PAGD_OK) st = dzero(s, s->ws + s->off[O_MASS], 2 * sizeof(double));
     if (st != PAGD_OK) return st;
     s->have_state = 1;
     s->step = 0;

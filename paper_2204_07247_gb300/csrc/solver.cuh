@@ -93,6 +93,7 @@ struct Params {
     const double2* tw64;
     const float2* tw32;
     Scal* sc;
+    double* mass;  // persistent {K, D}: mass excess since set_state and this step's change
     unsigned long long* norms;
     double* sums;
     StepStat* stats;
@@ -622,10 +623,16 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
     T* d1 = (T*)P.DD[1];
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gs = (long long)gridDim.x * blockDim.x;
-    // acceptance of step c.step - 1 (same scheme, so the same theta_v)
+    // acceptance of step c.step - 1 (same scheme, so the same theta_v).  The
+    // FP64 mean of the correction and the running mass excess K are removed; the
+    // exact change sum(u^{n+1} - u^n) is fed back into K (error feedback keeps
+    // the rounding of the removal from accumulating over steps).
     const T* dacc = (const T*)P.DD[c.acc_it & 1];
     const double macc =
-        c.acc ? ldcg(&P.sums[(size_t)(bank ^ 1) * P.nslots + c.acc_lastev]) / (double)P.npts : 0.0;
+        c.acc ? ldcg(&P.sums[(size_t)(bank ^ 1) * P.nslots + c.acc_lastev]) / (double)P.npts +
+                    ldcg(&P.mass[0]) / (double)P.npts
+              : 0.0;
+    double dmass = 0.0;
     // rebase: the candidate of this step
     const T* dreb = (const T*)P.DD[c.it & 1];
     const double mreb = c.reb ? ldcg(&P.sums[(size_t)bank * P.nslots + c.lastev]) / (double)P.npts : 0.0;
@@ -677,6 +684,7 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
                     const double va = s.vb + (s.d - macc);
                     a = (va - wth * s.b) * ith;
                     U0[p] = a;
+                    dmass += a - s.b;
                 }
                 const double x0 = a + k.rho * (a - b);
                 vb = k.thv * x0 + (1.0 - k.thv) * a;
@@ -706,6 +714,10 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
             if (threadIdx.x == 0) atomicAdd(&P.sc->beta_sum[bank][1], s2);
         }
     }
+    if (acc) {
+        dmass = block_sum(dmass, red);
+        if (threadIdx.x == 0) atomicAdd(&P.mass[1], dmass);
+    }
 }
 
 // Spectral base gradient C0 = G'_N(VB) (Eqs. misc07 / obj:G'), its
@@ -732,6 +744,11 @@ __device__ __forceinline__ void base_direction(const Params& P, const StepK& k, 
 
 template <class T, int NF>
 __device__ void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // fold the last acceptance's mass change into the running excess
+        P.mass[0] += P.mass[1];
+        P.mass[1] = 0.0;
+    }
     const StepK k = step_coeffs(P, c.step);
     const Beta B = betas(P, k, c.step);
     const int kb = k_base(P.model);
@@ -924,22 +941,27 @@ __device__ void phase_CI(const Params& P, const Ctl& c, const Tw& tw, char* smem
 // accepted inside the next step's phase B.)  The mean of delta is zero in exact
 // arithmetic (Remark on discrete mass conservation) and is removed in FP64.
 template <class T>
-__device__ void phase_accept(const Params& P, const Ctl& c) {
+__device__ void phase_accept(const Params& P, const Ctl& c, double* red) {
     const StepK k = step_coeffs(P, c.step);
     const int bank = c.step & 1;
     const T* dc = (const T*)P.DD[c.it & 1];
     const double* un = P.U[c.cur];
     double* unew = P.U[c.cur ^ 1];
-    const double m = ldcg(&P.sums[(size_t)bank * P.nslots + c.lastev]) / (double)P.npts;
+    const double m = (ldcg(&P.sums[(size_t)bank * P.nslots + c.lastev]) + ldcg(&P.mass[0])) / (double)P.npts;
     const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long gs = (long long)gridDim.x * blockDim.x;
     const double ith = 1.0 / k.thv, w = (1.0 - k.thv);
+    double dmass = 0.0;
     for (long long p = gt; p < P.npts; p += gs) {
         const double v = P.VB[p] + ((double)dc[p] - m);
-        const double x = (v - w * un[p]) * ith;
+        const double a = un[p];
+        const double x = (v - w * a) * ith;
         unew[p] = x;
+        dmass += x - a;
         if (P.out_real) P.out_real[p] = x;
     }
+    dmass = block_sum(dmass, red);
+    if (threadIdx.x == 0) atomicAdd(&P.mass[1], dmass);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         P.stats[c.step].iters = c.ev;
         P.stats[c.step].status = ST_OK;
@@ -1278,7 +1300,7 @@ __device__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* sm
         case PH_R1: phase_R<double, T, NF>(P, c, tw, smem, red, P.DB64); break;
         case PH_RI: phase_R<T, T, NF>(P, c, tw, smem, red, (const cx<T>*)P.DB); break;
         case PH_CI: phase_CI<T, NF>(P, c, tw, smem); break;
-        case PH_ACCEPT: phase_accept<T>(P, c); break;
+        case PH_ACCEPT: phase_accept<T>(P, c, red); break;
         case PH_FAIL: phase_fail(P, c); break;
         case PH_FWD_R: phase_fwd_r<NF>(P, tw, smem); break;
         case PH_FWD_C: phase_fwd_c<NF>(P, tw, smem); break;

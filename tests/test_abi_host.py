@@ -225,3 +225,21 @@ def test_emulated_mixed_precision_costs_few_extra_evaluations(emu, case):
         its, _ = S.run(dt, 3, 1e-8, S.empty_field())
         counts[prec] = its
     assert all(m <= f + 6 for m, f in zip(counts["fp32_mixed"], counts["fp64"])), counts
+
+
+def test_emulated_mass_error_does_not_accumulate(emu):
+    """Removing the mean of an FP32 correction from FP64 points rounds every
+    point the same way; the acceptance feeds the exact mass change back, so the
+    drift stays at rounding level instead of growing with the step count."""
+    n = (64, 64)
+    S = pagd.Solver("fch", n, (4 * math.pi,) * 2, 0.1, 0.1, 0.1, 0.0, scheme="bdf2",
+                    precision="fp32_mixed", lib=emu)
+    u0 = I.noisy_field(n, -0.3, 0.05, 3)
+    S.set_state(u0)
+    out = S.empty_field()
+    m0 = math.fsum(u0.ravel())
+    drift = []
+    for _ in range(8):
+        S.run(1e-3, 25, 1e-8, out)
+        drift.append(abs(math.fsum(out.ravel()) - m0) / abs(m0))
+    assert max(drift) <= 2e-15, drift
