@@ -266,7 +266,9 @@ static void make_plan(pagd_solver* s) {
     const int wpb = kThreads / 32;
 #endif
     const int units = s->n[0] / 2 > s->h1 ? s->n[0] / 2 : s->h1;
-    s->grid = (units + wpb - 1) / wpb;
+    const int sms = num_sms();
+    s->grid = units < sms ? units : sms;
+    if (s->grid < (units + wpb - 1) / wpb) s->grid = (units + wpb - 1) / wpb;
     if (s->grid < 1) s->grid = 1;
     const int l0 = ilog2(s->n[0]), l1 = ilog2(s->n[1]);
     s->logtw = l0 > l1 ? l0 : l1;

@@ -271,7 +271,10 @@ __device__ __forceinline__ WarpCtx warp_ctx(const Params& P, char* smem) {
     WarpCtx w;
     w.lane = threadIdx.x % kWarp;
     const int wib = threadIdx.x / kWarp, wpb = blockDim.x / kWarp;
-    w.gw = blockIdx.x * wpb + wib;
+    // units go round-robin over CTAs first, so with one CTA per SM each SM gets
+    // one busy warp before any SM gets a second (FP64 work is bound by the
+    // per-SM FP64 pipe on this part)
+    w.gw = wib * gridDim.x + blockIdx.x;
     w.nw = gridDim.x * wpb;
     w.mem = smem + (size_t)wib * P.warp_bytes;
     return w;
