@@ -133,6 +133,29 @@ pagd_status pagd_fft_c2r(pagd_solver* s, const double* spec_dev, double* u_dev);
  * number of steps taken since pagd_set_state. */
 pagd_status pagd_get_state(pagd_solver* s, double* un_dev, double* unm1_dev, int* step);
 
+/* One time step with no device allocation and no caller workspace.  The paper
+ * has no counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they need a step (code recording a CUDA graph, runtimes
+ * that own the device allocator, fixed-budget embedded uses).  It uses a
+ * file-scope static device array of 4 MiB as scratch (enough for every model,
+ * scheme and precision up to 128 x 128); grids whose pagd_workspace_size
+ * exceeds that are rejected with PAGD_EINVAL.  Every GPU that loads the
+ * library holds the array until the process exits.  The solver object comes
+ * from pfc_init / fch_init and supplies only the model, grid and solver
+ * settings: its own state and workspace are neither needed nor touched.
+ * Inputs: un_dev = u^n, unm1_dev = u^{n-1} (device, n_pts doubles; for
+ * step_index 0 pass u^0 twice), step_index = n, dt = dt_{n+1}, dt_prev = dt_n
+ * (ignored when step_index is 0).  Output: unp1_dev = u^{n+1} (device); it may
+ * not alias un_dev or unm1_dev.  iters_out / resid_out as for pagd_step.
+ * The first call on each device looks up the array's device address (make it
+ * before any stream capture).  All calls share the array and it keeps the
+ * previous call's contents (each call clears what must start at zero); calls
+ * that overlap on the GPU race on it, so the caller must serialise them.
+ * Synchronises the stream. */
+pagd_status pagd_step_static(pagd_solver* s, const double* un_dev, const double* unm1_dev,
+                             int step_index, double dt, double dt_prev, double tol, double* unp1_dev,
+                             int* iters_out, double* resid_out);
+
 const char* pagd_last_error(const pagd_solver* s);
 void pagd_destroy(pagd_solver* s);
 

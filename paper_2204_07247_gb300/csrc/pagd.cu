@@ -98,7 +98,7 @@ static void plan_layout(pagd_solver* s) {
     s->ws_bytes = o;
 }
 
-static Params base_params(const pagd_solver* s) {
+static Params params_for(const pagd_solver* s, char* w) {
     Params P;
     std::memset(&P, 0, sizeof(P));
     P.model = s->model;
@@ -132,7 +132,6 @@ static Params base_params(const pagd_solver* s) {
     P.nslots = s->nslots;
     P.cur0 = s->cur;
     P.step0 = s->step;
-    char* w = s->ws;
     P.sc = (Scal*)(w + s->off[O_SC]);
     P.norms = (unsigned long long*)(w + s->off[O_NORMS]);
     P.sums = (double*)(w + s->off[O_SUMS]);
@@ -158,6 +157,8 @@ static Params base_params(const pagd_solver* s) {
     P.mass = (double*)(w + s->off[O_MASS]);
     return P;
 }
+
+static Params base_params(const pagd_solver* s) { return params_for(s, s->ws); }
 
 // ------------------------------------------------------- device plumbing
 
@@ -572,6 +573,120 @@ pagd_status pagd_fft_c2r(pagd_solver* s, const double* spec_dev, double* u_dev) 
     pagd_status st = run_program(s, P);
     if (st == PAGD_OK) st = dsync(s);
     return st;
+}
+
+// ------------------------------------------------------------------------
+// Allocation-free single step.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// step: code running inside a CUDA graph being built, host threads of a
+// runtime that owns the device allocator and forbids other allocations, or
+// embedded uses that fix their memory budget up front.  pagd_step_static gives
+// them one time step that uses a file-scope static device array as its
+// workspace instead of a caller-provided one.  The array has a fixed size
+// (kStaticScratchBytes, 4 MiB: enough for any supported model up to 128 x 128
+// in FP64) and every GPU that loads this library holds it until the process
+// exits.  All calls share the one array and it keeps the last call's
+// contents; everything that must start at zero is cleared by each call.  Calls
+// whose work overlaps on the GPU (on different streams, or from different host
+// threads) race on the array and must be serialised by the caller.
+constexpr size_t kStaticScratchBytes = (size_t)4 << 20;
+#ifndef PAGD_EMU
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+#else
+alignas(256) static unsigned char g_static_scratch[kStaticScratchBytes];
+#endif
+constexpr int kMaxDevices = 64;
+static void* g_static_ptr[kMaxDevices];
+static double2 g_static_tw64[kNMax];
+static float2 g_static_tw32[kNMax];
+static bool g_static_tw_ready = false;
+
+// Device address of the static scratch for the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is obtained
+// with cudaGetSymbolAddress, once per device, with that device current; this
+// happens on the first call on each device (make that first call before any
+// stream capture).
+static pagd_status static_scratch(pagd_solver* s, char** out) {
+#ifdef PAGD_EMU
+    (void)s;
+    *out = (char*)g_static_scratch;
+    return PAGD_OK;
+#else
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(s, PAGD_EINVAL, "device index out of range");
+    if (!g_static_ptr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(s, e, "cudaGetSymbolAddress of the static scratch");
+        g_static_ptr[dev] = ptr;
+    }
+    *out = (char*)g_static_ptr[dev];
+    return PAGD_OK;
+#endif
+}
+
+pagd_status pagd_step_static(pagd_solver* s, const double* un_dev, const double* unm1_dev, int step_index,
+                             double dt, double dt_prev, double tol, double* unp1_dev, int* iters_out,
+                             double* resid_out) {
+    if (!s || !un_dev || !unm1_dev || !unp1_dev) return PAGD_EINVAL;
+    if (step_index < 0 || !(dt > 0.0) || !std::isfinite(dt) || !(tol >= 0.0) ||
+        (step_index > 0 && !(dt_prev > 0.0)))
+        return fail(s, PAGD_EINVAL, "bad step index / dt / dt_prev / tol");
+    if (s->ws_bytes > kStaticScratchBytes) {
+        char buf[200];
+        std::snprintf(buf, sizeof(buf),
+                      "grid too large for the static scratch: needs %zu bytes, the maximum is %zu "
+                      "(use pagd_set_workspace and pagd_step)",
+                      s->ws_bytes, kStaticScratchBytes);
+        return fail(s, PAGD_EINVAL, buf);
+    }
+    char* w = nullptr;
+    pagd_status st = static_scratch(s, &w);
+    if (st != PAGD_OK) return st;
+    if (!g_static_tw_ready) {
+        for (int m = 0; m < kNMax; m++) {
+            const long double ang = -2.0L * 3.141592653589793238462643383279502884L * (long double)m / (long double)kNMax;
+            g_static_tw64[m].x = (double)cosl(ang);
+            g_static_tw64[m].y = (double)sinl(ang);
+            g_static_tw32[m].x = (float)g_static_tw64[m].x;
+            g_static_tw32[m].y = (float)g_static_tw64[m].y;
+        }
+        g_static_tw_ready = true;
+    }
+    const size_t b = sizeof(double) * s->npts;
+    st = dcopy(s, w + s->off[O_TW64], g_static_tw64, sizeof(g_static_tw64));
+    if (st == PAGD_OK) st = dcopy(s, w + s->off[O_TW32], g_static_tw32, sizeof(g_static_tw32));
+    if (st == PAGD_OK) st = dcopy(s, w + s->off[O_U0], un_dev, b);
+    if (st == PAGD_OK) st = dcopy(s, w + s->off[O_U1], unm1_dev, b);
+    if (st == PAGD_OK) st = dzero(s, w + s->off[O_MASS], 2 * sizeof(double));
+    if (st != PAGD_OK) return st;
+    Params P = params_for(s, w);
+    const bool imex = s->scheme == PAGD_LBDF2 || s->scheme == PAGD_LMP;
+    P.prog = imex ? PROG_IMEX : PROG_RUN;
+    P.cur0 = 0;
+    P.step0 = step_index;
+    P.tol = tol;
+    P.dt = dt;
+    P.dt_prev0 = step_index == 0 ? dt : dt_prev;
+    P.nsteps = 1;
+    P.out_real = unp1_dev;
+    st = run_program(s, P);
+    if (st != PAGD_OK) return st;
+    Scal sc;
+    StepStat stat;
+    st = dcopy(s, &sc, P.sc, sizeof(Scal));
+    if (st == PAGD_OK) st = dcopy(s, &stat, P.stats, sizeof(StepStat));
+    if (st == PAGD_OK) st = dsync(s);
+    if (st != PAGD_OK) return st;
+    if (iters_out) *iters_out = stat.iters;
+    if (resid_out) *resid_out = stat.resid;
+    if (sc.bar_error) return fail(s, PAGD_ETIMEOUT, "device barrier timed out");
+    if (sc.status != ST_OK) return fail(s, status_from(sc.status), "static-scratch step failed");
+    if (sc.steps_done != 1) return fail(s, PAGD_ECUDA, "kernel ended early");
+    return PAGD_OK;
 }
 
 const char* pagd_last_error(const pagd_solver* s) { return s ? s->err.c_str() : "null solver"; }

@@ -27,7 +27,8 @@ SCHEMES = {"bdf2": BDF2, "mp": MP, "lbdf2": LBDF2, "lmp": LMP}
 PRECISIONS = {"fp64": FP64, "fp32_mixed": FP32_MIXED}
 EXPORTS = ("pagd_default_opts", "pfc_init", "fch_init", "pagd_workspace_size", "pagd_set_workspace",
            "pagd_set_state", "pagd_step", "pagd_run", "pagd_run_host", "pagd_energy", "pagd_mass",
-           "pagd_fft_r2c", "pagd_fft_c2r", "pagd_get_state", "pagd_last_error", "pagd_destroy")
+           "pagd_fft_r2c", "pagd_fft_c2r", "pagd_get_state", "pagd_step_static", "pagd_last_error",
+           "pagd_destroy")
 
 
 class PagdError(RuntimeError):
@@ -61,6 +62,7 @@ def _declare(lib):
         "pagd_fft_r2c": [P, P, P],
         "pagd_fft_c2r": [P, P, P],
         "pagd_get_state": [P, P, P, IP],
+        "pagd_step_static": [P, P, P, i, d, d, d, P, IP, D],
         "pagd_last_error": [P],
         "pagd_destroy": [P],
     }
@@ -250,6 +252,17 @@ class Solver:
         self._check(self.lib.pagd_get_state(self._h, self._ptr(un), self._ptr(um), ctypes.byref(st)),
                     "get_state")
         return un, um, st.value
+
+    def step_static(self, un, unm1, step_index, dt, dt_prev, tol, u_out):
+        """One step on the library's static device scratch (no workspace use):
+        u_out = u^{n+1} from un = u^n, unm1 = u^{n-1}.  For callers that cannot
+        allocate device memory; see pagd_step_static in include/pagd.h."""
+        it = ctypes.c_int()
+        r = ctypes.c_double()
+        self._check(self.lib.pagd_step_static(self._h, self._ptr(un), self._ptr(unm1), step_index, dt,
+                                              dt_prev, tol, self._ptr(u_out), ctypes.byref(it),
+                                              ctypes.byref(r)), "step_static")
+        return it.value, r.value
 
     def close(self):
         if self._h:
