@@ -156,6 +156,17 @@ pagd_status pagd_step_static(pagd_solver* s, const double* un_dev, const double*
                              int step_index, double dt, double dt_prev, double tol, double* unp1_dev,
                              int* iters_out, double* resid_out);
 
+/* Phase tracing (instrumentation, not in the paper).  With tracing enabled,
+ * every launch records, for each phase of the persistent kernel, the phase
+ * identifier and the device time at which all CTAs finished it (up to 8192
+ * records per launch).  pagd_get_trace copies the records of the last launch:
+ * phase[i] and t_us[i] (microseconds since the launch started; record 0 is the
+ * start marker), at most cap records, and the number recorded to *count.
+ * Phase identifiers are those of the kernel's control machine (see
+ * paper_2204_07247_gb300/pagd.py PHASES). */
+pagd_status pagd_set_trace(pagd_solver* s, int enable);
+pagd_status pagd_get_trace(pagd_solver* s, int* phase, double* t_us, int cap, int* count);
+
 const char* pagd_last_error(const pagd_solver* s);
 void pagd_destroy(pagd_solver* s);
 

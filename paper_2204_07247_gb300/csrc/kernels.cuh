@@ -72,11 +72,23 @@ __global__ void __launch_bounds__(kThreads, 1) pagd_kernel(Params P) {
     char* wsm = smem + tw_smem_bytes(P.logtw);
     Ctl c = ctl_init(P);
     unsigned gen = 0;
+    int ntr = 0;
+    if (P.trace && blockIdx.x == 0 && threadIdx.x == 0) {
+        P.trace[0] = (unsigned long long)PH_DONE;  // start marker
+        P.trace[1] = gtimer();
+        ntr = 1;
+    }
     while (c.ph != PH_DONE) {
         exec_phase<T, NF>(P, c, tw, wsm, red);
         if (!grid_barrier(P.sc, gen)) break;
+        if (P.trace && blockIdx.x == 0 && threadIdx.x == 0 && ntr < P.trace_cap) {
+            P.trace[2 * ntr] = (unsigned long long)c.ph;
+            P.trace[2 * ntr + 1] = gtimer();
+            ntr++;
+        }
         ctl_advance<T>(P, c);
     }
+    if (P.trace && blockIdx.x == 0 && threadIdx.x == 0) P.sc->ntrace = ntr;
 }
 
 

@@ -30,6 +30,7 @@ thread_local EmuDim3 threadIdx{0, 0, 0}, blockIdx{0, 0, 0}, blockDim{1, 1, 1}, g
 // ------------------------------------------------------------ solver object
 
 constexpr int kMaxChunk = 4096;
+constexpr int kTraceCap = 8192;  // phase records kept per launch when tracing
 
 struct pagd_solver {
     int model, dim, n[3];
@@ -48,14 +49,14 @@ struct pagd_solver {
     int grid, logtw;
     size_t smem, warp_bytes;
     // state
-    int have_state, step, cur;
+    int have_state, step, cur, trace;
     double dt_prev;
     std::string err;
 };
 
 enum {
     O_SC, O_NORMS, O_SUMS, O_STATS, O_TW64, O_TW32, O_U0, O_U1, O_VB, O_G64, O_VBT, O_LBT, O_DD0,
-    O_DD1, O_SS0, O_SS1, O_C0, O_NB, O_DB, O_CL64, O_NB64, O_DB64, O_MASS, O_END
+    O_DD1, O_SS0, O_SS1, O_C0, O_NB, O_DB, O_CL64, O_NB64, O_DB64, O_MASS, O_TRACE, O_END
 };
 
 static pagd_status fail(pagd_solver* s, pagd_status st, const char* msg) {
@@ -90,6 +91,7 @@ static void plan_layout(pagd_solver* s) {
     sz[O_NB64] = sizeof(double2) * H * 3;
     sz[O_DB64] = sizeof(double2) * H * 2;
     sz[O_MASS] = sizeof(double) * 2;
+    sz[O_TRACE] = sizeof(unsigned long long) * 2 * kTraceCap;
     size_t o = 0;
     for (int i = 0; i < O_END; i++) {
         s->off[i] = o;
@@ -155,6 +157,8 @@ static Params params_for(const pagd_solver* s, char* w) {
     P.NB64 = (double2*)(w + s->off[O_NB64]);
     P.DB64 = (double2*)(w + s->off[O_DB64]);
     P.mass = (double*)(w + s->off[O_MASS]);
+    P.trace = s->trace ? (unsigned long long*)(w + s->off[O_TRACE]) : nullptr;
+    P.trace_cap = kTraceCap;
     return P;
 }
 
@@ -338,6 +342,7 @@ static pagd_status init_common(pagd_solver** out, int model, int dim, const int*
     s->have_state = 0;
     s->step = 0;
     s->cur = 0;
+    s->trace = 0;
     s->dt_prev = 0.0;
     plan_layout(s);
     make_plan(s);
@@ -686,6 +691,38 @@ pagd_status pagd_step_static(pagd_solver* s, const double* un_dev, const double*
     if (sc.bar_error) return fail(s, PAGD_ETIMEOUT, "device barrier timed out");
     if (sc.status != ST_OK) return fail(s, status_from(sc.status), "static-scratch step failed");
     if (sc.steps_done != 1) return fail(s, PAGD_ECUDA, "kernel ended early");
+    return PAGD_OK;
+}
+
+pagd_status pagd_set_trace(pagd_solver* s, int enable) {
+    if (!s) return PAGD_EINVAL;
+    s->trace = enable ? 1 : 0;
+    return PAGD_OK;
+}
+
+pagd_status pagd_get_trace(pagd_solver* s, int* phase, double* t_us, int cap, int* count) {
+    if (!s || !count || cap < 0 || (cap > 0 && (!phase || !t_us))) return PAGD_EINVAL;
+    if (!s->ws) return fail(s, PAGD_ESTATE, "no workspace");
+    Scal sc;
+    pagd_status st = dcopy(s, &sc, s->ws + s->off[O_SC], sizeof(Scal));
+    if (st == PAGD_OK) st = dsync(s);
+    if (st != PAGD_OK) return st;
+    const int n = sc.ntrace < kTraceCap ? sc.ntrace : kTraceCap;
+    *count = n;
+    unsigned long long rec[2 * 256];
+    unsigned long long t0 = 0;
+    for (int base = 0; base < n && base < cap; base += 256) {
+        const int m = (n - base < 256) ? n - base : 256;
+        st = dcopy(s, rec, s->ws + s->off[O_TRACE] + sizeof(unsigned long long) * 2 * base,
+                   sizeof(unsigned long long) * 2 * m);
+        if (st == PAGD_OK) st = dsync(s);
+        if (st != PAGD_OK) return st;
+        for (int i = 0; i < m && base + i < cap; i++) {
+            if (base + i == 0) t0 = rec[1];
+            phase[base + i] = (int)rec[2 * i];
+            t_us[base + i] = (double)(rec[2 * i + 1] - t0) * 1e-3;
+        }
+    }
     return PAGD_OK;
 }
 

@@ -50,7 +50,7 @@ enum Phase {
 struct Scal {
     unsigned bar_count, bar_gen;
     int bar_error, flags;
-    int status, steps_done, fail_step, pad;
+    int status, steps_done, fail_step, ntrace;
     double beta_sum[2][2];  // [step parity][field]
     double red[4];
 };
@@ -94,6 +94,8 @@ struct Params {
     const float2* tw32;
     Scal* sc;
     double* mass;  // persistent {K, D}: mass excess since set_state and this step's change
+    unsigned long long* trace;  // nullable: (phase, globaltimer) pairs, one per completed phase
+    int trace_cap;
     unsigned long long* norms;
     double* sums;
     StepStat* stats;
@@ -191,6 +193,12 @@ __device__ __forceinline__ double lam_at(const Params& P, int i) {
 __device__ __forceinline__ double kappa_at(const Params& P, int k1, int k0) {
     const int r0 = (k0 <= (P.n0 >> 1)) ? k0 : k0 - P.n0;
     return P.k1sq * (double)k1 * (double)k1 + P.k0sq * (double)r0 * (double)r0;
+}
+
+// kappa in the iteration precision (FP32 iterations carry no FP64 arithmetic)
+template <class T> __device__ __forceinline__ T kappa_t(const Params& P, int k1, int k0) {
+    const int r0 = (k0 <= (P.n0 >> 1)) ? k0 : k0 - P.n0;
+    return (T)P.k1sq * (T)(k1 * k1) + (T)P.k0sq * (T)(r0 * r0);
 }
 
 // double well derivatives, expanded: F'(z) = (z^2 - 1)(z + tau),
@@ -738,7 +746,8 @@ __device__ __forceinline__ void base_direction(const Params& P, const StepK& k, 
     } else {
         const double Lk = B.m2 / kap + B.b0 + B.b2 * kap + B.b4 * kap * kap;
         if (!(Lk > 0.0)) atomicOr(&P.sc->flags, FLAG_PRECOND);
-        d = double2{-G.x / Lk, -G.y / Lk};
+        const double il = -1.0 / Lk;
+        d = double2{il * G.x, il * G.y};
     }
     C0[idx] = cx<T>{(T)G.x, (T)G.y};
     S0[idx] = cx<T>{(T)0, (T)0};
@@ -846,7 +855,8 @@ __device__ void phase_R(const Params& P, const Ctl& c, const Tw& tw, char* smem,
     const T* lbt = (const T*)P.LBt;
     const int K = k_iter(P.model);
     const T tau = (T)P.tau, e2 = (T)(P.eps * P.eps), eta1 = (T)P.eta1, eta2 = (T)P.eta2;
-    double amax = 0.0, asum = 0.0;
+    TI amax = (TI)0;
+    double asum = 0.0;
     const bool pfc = P.model == M_PFC;
     struct St { T dp, dpp, b, lb; };
     rowp<TI, T, NF>(
@@ -863,7 +873,8 @@ __device__ void phase_R(const Params& P, const Ctl& c, const Tw& tw, char* smem,
             const TI dd = in[0];
             const T de = s.dp + lp * (s.dp - s.dpp) + ts * (T)dd;
             dcur[p] = de;
-            amax = nanmax(amax, fabs((double)dd));
+            const TI ad = fabs(dd);
+            amax = (ad > amax || ad != ad) ? ad : amax;
             asum += (double)de;
             const T y = de + l * (de - s.dp);
             const T b = s.b;
@@ -879,8 +890,8 @@ __device__ void phase_R(const Params& P, const Ctl& c, const Tw& tw, char* smem,
                 out[1] = -e2 * (df2 * s.lb + (f2n - eta1) * ly) + df2 * f1n + (f2b - eta2) * df1;
             }
         });
-    amax = block_max(amax, red);
-    if (threadIdx.x == 0) atomicMax(&P.norms[(size_t)bank * P.nslots + c.ev], dbl_bits(amax));
+    const double amx = block_max((double)amax, red);
+    if (threadIdx.x == 0) atomicMax(&P.norms[(size_t)bank * P.nslots + c.ev], dbl_bits(amx));
     asum = block_sum(asum, red);
     if (threadIdx.x == 0) atomicAdd(&P.sums[(size_t)bank * P.nslots + c.ev], asum);
 }
@@ -900,7 +911,9 @@ __device__ void phase_CI(const Params& P, const Ctl& c, const Tw& tw, char* smem
     const C* C0 = (const C*)P.C0;
     const int K = k_iter(P.model);
     const bool pfc = P.model == M_PFC;
-    const double iM = 1.0 / P.M, e2 = P.eps * P.eps, e4 = e2 * e2;
+    // spectral factors in the iteration precision
+    const T m2 = (T)B.m2, b0 = (T)B.b0, b2 = (T)B.b2, b4 = (T)B.b4;
+    const T aim = (T)(k.Ai / P.M), c0 = (T)(1.0 - P.eps), e2 = (T)(P.eps * P.eps), e4 = e2 * e2;
     struct St { C sc, sp, g0; };
     colp<T, NF>(
         P, tw, K, K, (const C*)P.NB, (C*)P.DB, smem,
@@ -910,21 +923,21 @@ __device__ void phase_CI(const Params& P, const Ctl& c, const Tw& tw, char* smem
         },
         [&](int k1, int k0, const St& s, const C* in, C* out) {
             const long long idx = (long long)k1 * P.n0 + k0;
-            const double kap = kappa_at(P, k1, k0);
+            const T kap = kappa_t<T>(P, k1, k0);
             const C sc = s.sc, sp = s.sp;
             const C yh = C{sc.x + l * (sc.x - sp.x), sc.y + l * (sc.y - sp.y)};
             C d{(T)0, (T)0};
-            if (kap != 0.0) {
+            if (kap != (T)0) {
                 const C g0 = s.g0;
-                const double Lk = B.m2 / kap + B.b0 + B.b2 * kap + B.b4 * kap * kap;
-                const T il = (T)(-1.0 / Lk);
+                const T ik = (T)1 / kap;
+                const T il = (T)-1 / (m2 * ik + b0 + b2 * kap + b4 * kap * kap);
                 if (pfc) {
-                    const T m = (T)(k.Ai * iM / kap + 1.0 - P.eps - 2.0 * kap + kap * kap);
+                    const T m = aim * ik + c0 - (T)2 * kap + kap * kap;
                     d.x = il * (g0.x + m * yh.x + in[0].x);
                     d.y = il * (g0.y + m * yh.y + in[0].y);
                 } else {
-                    const T m = (T)(k.Ai * iM / kap + e4 * kap * kap);
-                    const T e2k = (T)(e2 * kap);
+                    const T m = aim * ik + e4 * kap * kap;
+                    const T e2k = e2 * kap;
                     d.x = il * (g0.x + m * yh.x + e2k * in[0].x + in[1].x);
                     d.y = il * (g0.y + m * yh.y + e2k * in[0].y + in[1].y);
                 }
@@ -933,7 +946,7 @@ __device__ void phase_CI(const Params& P, const Ctl& c, const Tw& tw, char* smem
             sprev[idx] = sn;
             out[0] = d;
             if (!pfc) {
-                const T f = (T)(-kap);
+                const T f = -kap;
                 out[1] = C{f * (sn.x + ln * (sn.x - sc.x)), f * (sn.y + ln * (sn.y - sc.y))};
             }
         });

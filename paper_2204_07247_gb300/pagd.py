@@ -27,8 +27,11 @@ SCHEMES = {"bdf2": BDF2, "mp": MP, "lbdf2": LBDF2, "lmp": LMP}
 PRECISIONS = {"fp64": FP64, "fp32_mixed": FP32_MIXED}
 EXPORTS = ("pagd_default_opts", "pfc_init", "fch_init", "pagd_workspace_size", "pagd_set_workspace",
            "pagd_set_state", "pagd_step", "pagd_run", "pagd_run_host", "pagd_energy", "pagd_mass",
-           "pagd_fft_r2c", "pagd_fft_c2r", "pagd_get_state", "pagd_step_static", "pagd_last_error",
-           "pagd_destroy")
+           "pagd_fft_r2c", "pagd_fft_c2r", "pagd_get_state", "pagd_step_static", "pagd_set_trace",
+           "pagd_get_trace", "pagd_last_error", "pagd_destroy")
+# phase identifiers of the persistent kernel's control machine (for traces)
+PHASES = ("B", "C", "D", "E", "R1", "CI", "RI", "ACCEPT", "FAIL", "FWD_R", "FWD_C", "INV_C", "INV_R",
+          "EN_R", "EN_C", "EN_R2", "MASS", "IM_R0", "IM_C0", "IM_R1", "IM_C1", "IM_R2", "START")
 
 
 class PagdError(RuntimeError):
@@ -63,6 +66,8 @@ def _declare(lib):
         "pagd_fft_c2r": [P, P, P],
         "pagd_get_state": [P, P, P, IP],
         "pagd_step_static": [P, P, P, i, d, d, d, P, IP, D],
+        "pagd_set_trace": [P, i],
+        "pagd_get_trace": [P, IP, D, i, IP],
         "pagd_last_error": [P],
         "pagd_destroy": [P],
     }
@@ -263,6 +268,18 @@ class Solver:
                                               dt_prev, tol, self._ptr(u_out), ctypes.byref(it),
                                               ctypes.byref(r)), "step_static")
         return it.value, r.value
+
+    def set_trace(self, enable=True):
+        self._check(self.lib.pagd_set_trace(self._h, 1 if enable else 0), "set_trace")
+
+    def get_trace(self, cap=8192):
+        """(phase names, end times in us) of the last launch's phases."""
+        ph = (ctypes.c_int * cap)()
+        t = (ctypes.c_double * cap)()
+        cnt = ctypes.c_int()
+        self._check(self.lib.pagd_get_trace(self._h, ph, t, cap, ctypes.byref(cnt)), "get_trace")
+        n = min(cnt.value, cap)
+        return [PHASES[ph[i]] for i in range(n)], np.array(t[:n])
 
     def close(self):
         if self._h:
