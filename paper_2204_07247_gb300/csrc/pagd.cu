@@ -31,6 +31,8 @@ thread_local EmuDim3 threadIdx{0, 0, 0}, blockIdx{0, 0, 0}, blockDim{1, 1, 1}, g
 
 constexpr int kMaxChunk = 4096;
 constexpr int kTraceCap = 8192;  // phase records kept per launch when tracing
+// FP32-mixed: steps between exact FP64 recomputations of the reference spectra
+constexpr int kRefreshSteps = 32;
 
 struct pagd_solver {
     int model, dim, n[3];
@@ -49,14 +51,14 @@ struct pagd_solver {
     int grid, logtw;
     size_t smem, warp_bytes;
     // state
-    int have_state, step, cur, trace;
+    int have_state, step, cur, trace, ref_valid;
     double dt_prev;
     std::string err;
 };
 
 enum {
     O_SC, O_NORMS, O_SUMS, O_STATS, O_TW64, O_TW32, O_U0, O_U1, O_VB, O_G64, O_VBT, O_LBT, O_DD0,
-    O_DD1, O_SS0, O_SS1, O_C0, O_NB, O_DB, O_CL64, O_NB64, O_DB64, O_MASS, O_TRACE, O_END
+    O_DD1, O_SS0, O_SS1, O_C0, O_NB, O_DB, O_CL64, O_NB64, O_DB64, O_MASS, O_TRACE, O_VR64, O_NR64, O_WR64, O_LB64, O_YB, O_END
 };
 
 static pagd_status fail(pagd_solver* s, pagd_status st, const char* msg) {
@@ -86,12 +88,18 @@ static void plan_layout(pagd_solver* s) {
     sz[O_U0] = sz[O_U1] = sz[O_VB] = sz[O_G64] = sizeof(double) * N;
     sz[O_VBT] = sz[O_LBT] = sz[O_DD0] = sz[O_DD1] = (size_t)T * N;
     sz[O_SS0] = sz[O_SS1] = sz[O_C0] = (size_t)2 * T * H;
-    sz[O_NB] = sz[O_DB] = (size_t)2 * T * H * 2;
+    sz[O_NB] = (size_t)2 * T * H * 3;
+    sz[O_DB] = (size_t)2 * T * H * 2;
     sz[O_CL64] = sizeof(double2) * H * 3;
     sz[O_NB64] = sizeof(double2) * H * 3;
     sz[O_DB64] = sizeof(double2) * H * 2;
     sz[O_MASS] = sizeof(double) * 2;
     sz[O_TRACE] = sizeof(unsigned long long) * 2 * kTraceCap;
+    sz[O_VR64] = sizeof(double2) * H;
+    sz[O_NR64] = sizeof(double2) * H * 2;
+    sz[O_WR64] = sizeof(double2) * H;
+    sz[O_LB64] = sizeof(double) * N;
+    sz[O_YB] = (size_t)T * N;
     size_t o = 0;
     for (int i = 0; i < O_END; i++) {
         s->off[i] = o;
@@ -159,6 +167,13 @@ static Params params_for(const pagd_solver* s, char* w) {
     P.mass = (double*)(w + s->off[O_MASS]);
     P.trace = s->trace ? (unsigned long long*)(w + s->off[O_TRACE]) : nullptr;
     P.trace_cap = kTraceCap;
+    P.VR64 = (double2*)(w + s->off[O_VR64]);
+    P.NR64 = (double2*)(w + s->off[O_NR64]);
+    P.WR64 = (double2*)(w + s->off[O_WR64]);
+    P.LB64 = (double*)(w + s->off[O_LB64]);
+    P.YB = w + s->off[O_YB];
+    P.ref_valid = s->ref_valid;
+    P.refresh = kRefreshSteps;
     return P;
 }
 
@@ -343,6 +358,7 @@ static pagd_status init_common(pagd_solver** out, int model, int dim, const int*
     s->step = 0;
     s->cur = 0;
     s->trace = 0;
+    s->ref_valid = 0;
     s->dt_prev = 0.0;
     plan_layout(s);
     make_plan(s);
@@ -403,6 +419,7 @@ pagd_status pagd_set_state(pagd_solver* s, const double* u0_dev) {
     s->have_state = 1;
     s->step = 0;
     s->dt_prev = 0.0;
+    s->ref_valid = 0;
     return PAGD_OK;
 }
 
@@ -449,6 +466,9 @@ static pagd_status run_chunk(pagd_solver* s, double* u_out, double dt, int nstep
         s->cur ^= (ndone & 1);
         s->dt_prev = dt;
     }
+    // the reference spectra of the incremental base evaluation stay valid only
+    // after a run that ended on an accepted step
+    s->ref_valid = (!imex && sc.status == ST_OK && !sc.bar_error && ndone == nsteps && nsteps > 0) ? 1 : 0;
     if (sc.bar_error) return fail(s, PAGD_ETIMEOUT, "device barrier timed out");
     if (sc.status != ST_OK) {
         char buf[160];
@@ -496,6 +516,7 @@ pagd_status pagd_run_host(pagd_solver* s, const double* u0_host, double* u_host_
     s->have_state = 1;
     s->step = 0;
     s->dt_prev = 0.0;
+    s->ref_valid = 0;
     st = pagd_run(s, nullptr, dt, nsteps, tol, iters_out, resid_out);
     if (st != PAGD_OK) return st;
     st = dcopy(s, u_host_out, s->ws + (s->cur ? s->off[O_U1] : s->off[O_U0]), b);
@@ -671,6 +692,7 @@ pagd_status pagd_step_static(pagd_solver* s, const double* un_dev, const double*
     Params P = params_for(s, w);
     const bool imex = s->scheme == PAGD_LBDF2 || s->scheme == PAGD_LMP;
     P.prog = imex ? PROG_IMEX : PROG_RUN;
+    P.ref_valid = 0;  // the static scratch holds no reference spectra
     P.cur0 = 0;
     P.step0 = step_index;
     P.tol = tol;

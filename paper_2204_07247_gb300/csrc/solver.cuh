@@ -26,6 +26,8 @@
 // linear in delta plus the nonlinear difference N(VB + delta) - N(VB), written
 // so that every term is proportional to delta (no cancellation in FP32).
 #pragma once
+#include <type_traits>
+
 #include "fft.cuh"
 
 namespace pagd {
@@ -90,6 +92,15 @@ struct Params {
     double2* CL64;
     double2* NB64;
     double2* DB64;
+    // reference point of the incremental (FP32-transform) base evaluation: the
+    // FP64 spectra of the last evaluated base VB (VR64: v, NR64: PFC v^3 / FCH
+    // F'(v), P(v)), its FP64 Laplacian (LB64, FCH) and the last shift (YB)
+    double2* VR64;
+    double2* NR64;
+    double2* WR64;  // FP64 spectrum of A_i v + g at the reference
+    double* LB64;
+    void* YB;
+    int ref_valid, refresh;
     const double2* tw64;
     const float2* tw32;
     Scal* sc;
@@ -108,7 +119,7 @@ struct Params {
 
 struct Ctl {
     int ph, step, it, ev, lastev, cur, rech, fail, best_ev;
-    int acc, acc_cur, acc_it, acc_lastev, acc_ev, reb;
+    int acc, acc_cur, acc_it, acc_lastev, acc_ev, reb, ereb, inc, ref_ok, exact_done;
     double resid, base_nrm, best_nrm, acc_resid;
 };
 
@@ -625,8 +636,14 @@ __host__ __device__ __forceinline__ int k_base(int model) { return model == M_PF
 // base argument VB, history term g and preconditioner sums, or a move of the
 // base to the current candidate (mixed precision), (3) the forward x-DFT of the
 // FP64 base fields (VB, g[, VB^3]).
-template <class T, int NF>
+// INC: incremental base evaluation (FP32-mixed).  Instead of (VB, g[, VB^3]) in
+// FP64 it transforms, in T, the fields that are small at the new base: the
+// linear residual W = A_i VB + g = a x + b u^n + c u^{n-1} (O(u_t)), the shift
+// y = VB_new - VB_old from the reference point, and (PFC) the nonlinear change
+// VB_new^3 - VB_old^3 = y (3 r^2 + 3 r y + y^2), r = VB_old.
+template <class T, int NF, bool INC>
 __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red) {
+    using TO = typename std::conditional<INC, T, double>::type;
     const StepK k = step_coeffs(P, c.step);
     const int bank = c.step & 1;
     T* vbt = (T*)P.VBt;
@@ -672,8 +689,12 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
     double* U0 = P.U[c.cur];
     double* U1 = P.U[c.cur ^ 1];
     struct St { double vb, g, a, b, d; };
-    rowp<double, double, NF>(
-        P, tw, 0, kb, (const double2*)nullptr, P.NB64, smem,
+    T* yb = (T*)P.YB;
+    cx<TO>* dst = INC ? (cx<TO>*)P.NB : (cx<TO>*)P.NB64;
+    const double Ai = k.Ai;
+    const int kout = (INC && reb) ? kb - 1 : kb;
+    rowp<double, TO, NF>(
+        P, tw, 0, kout, (const double2*)nullptr, dst, smem,
         [&](long long p, int, int) {
             St s;
             s.vb = P.VB[p];
@@ -683,7 +704,7 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
             s.b = reb ? 0.0 : U1[p];
             return s;
         },
-        [&](long long p, int, int, const St& s, const double*, double* out) {
+        [&](long long p, int, int, const St& s, const double*, TO* out) {
             double vb, g;
             if (reb) {
                 vb = s.vb + (s.d - mreb);
@@ -713,9 +734,20 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
             vbt[p] = (T)vb;
             d0[p] = (T)0;
             d1[p] = (T)0;
-            out[0] = vb;
-            out[1] = g;
-            if (pfc) out[2] = vb * vb * vb;
+            if constexpr (INC) {
+                // a rebase keeps g, so W moves by A_i y (added spectrally); a new
+                // step transforms its W
+                const double y = vb - s.vb, r = s.vb;
+                yb[p] = (T)y;
+                const int o = reb ? 0 : 1;
+                if (!reb) out[0] = (TO)(Ai * vb + g);
+                out[o] = (TO)y;
+                if (pfc) out[o + 1] = (TO)(y * (3.0 * r * r + 3.0 * r * y + y * y));
+            } else {
+                out[0] = vb;
+                out[1] = g;
+                if (pfc) out[2] = vb * vb * vb;
+            }
         });
     if (!reb) {
         s0 = block_sum(s0, red);
@@ -771,6 +803,9 @@ __device__ void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem)
                          [&](int k1, int k0, const Nil&, const double2* in, double2* out) {
                              const double kap = kappa_at(P, k1, k0);
                              const double2 v = in[0], g = in[1], nl = in[2];
+                             P.VR64[(long long)k1 * P.n0 + k0] = v;
+                             P.NR64[(long long)k1 * P.n0 + k0] = nl;
+                             P.WR64[(long long)k1 * P.n0 + k0] = double2{k.Ai * v.x + g.x, k.Ai * v.y + g.y};
                              double2 G{0.0, 0.0};
                              if (kap != 0.0) {
                                  const double Lh = 1.0 - P.eps - 2.0 * kap + kap * kap;
@@ -787,6 +822,8 @@ __device__ void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem)
                          [&](int k1, int k0, const Nil&, const double2* in, double2* out) {
                              const double kap = kappa_at(P, k1, k0);
                              const double2 v = in[0], g = in[1];
+                             P.VR64[(long long)k1 * P.n0 + k0] = v;
+                             P.WR64[(long long)k1 * P.n0 + k0] = double2{k.Ai * v.x + g.x, k.Ai * v.y + g.y};
                              double2 G{0.0, 0.0};
                              if (kap != 0.0) {
                                  const double ik = iM / kap;
@@ -810,6 +847,7 @@ __device__ void phase_D(const Params& P, const Tw& tw, char* smem) {
                              [&](long long p, int, int, const double& vb, const double* in, double* out) {
                                  const double lb = in[0];
                                  lbt[p] = (T)lb;
+                                 P.LB64[p] = lb;
                                  const double f1 = dF1(vb, P.tau), f2 = dF2(vb, P.tau);
                                  out[0] = f1;
                                  out[1] = -e2 * (f2 - P.eta1) * lb + (f2 - P.eta2) * f1;
@@ -826,6 +864,9 @@ __device__ void phase_E(const Params& P, const Ctl& c, const Tw& tw, char* smem)
                      [&](int k1, int k0) { return P.CL64[(long long)k1 * P.n0 + k0]; },
                      [&](int k1, int k0, const double2& lin, const double2* in, double2* out) {
                          const double kap = kappa_at(P, k1, k0);
+                         const long long idx = (long long)k1 * P.n0 + k0;
+                         P.NR64[idx] = in[0];
+                         P.NR64[idx + (long long)P.h1 * P.n0] = in[1];
                          double2 G{0.0, 0.0};
                          if (kap != 0.0) {
                              G.x = lin.x + e2 * kap * in[0].x + in[1].x;
@@ -837,6 +878,133 @@ __device__ void phase_E(const Params& P, const Ctl& c, const Tw& tw, char* smem)
                          const double f = -kap * (1.0 + l1) * k.ts;
                          out[1] = double2{f * d.x, f * d.y};
                      });
+}
+
+// Incremental base evaluation, column part: the FP64 reference spectra move to
+// the new base (v_hat += y_hat, PFC: N_hat += dN_hat) and the base gradient is
+// assembled in FP64 from them and the T-transformed small fields.
+template <class T, int NF>
+__device__ void phase_CN(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
+    using C = cx<T>;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.mass[0] += P.mass[1];
+        P.mass[1] = 0.0;
+    }
+    const StepK k = step_coeffs(P, c.step);
+    const Beta B = betas(P, k, c.step);
+    const bool reb = c.ereb != 0;
+    const int kb = k_base(P.model);
+    const int kin = reb ? kb - 1 : kb;
+    const int o = reb ? 0 : 1;  // in[o] = y_hat, in[o + 1] = dN_hat (PFC), in[0] = W_hat (new step)
+    const double iM = 1.0 / P.M, Ai = k.Ai;
+    const double e4 = P.eps * P.eps * P.eps * P.eps;
+    const bool pfc = P.model == M_PFC;
+    struct St { double2 v, n, w; };
+    colp<T, NF>(
+        P, tw, kin, 1, (const C*)P.NB, (C*)P.DB, smem,
+        [&](int k1, int k0) {
+            const long long idx = (long long)k1 * P.n0 + k0;
+            return St{P.VR64[idx], pfc ? P.NR64[idx] : double2{0.0, 0.0}, P.WR64[idx]};
+        },
+        [&](int k1, int k0, const St& s, const C* in, C* out) {
+            const long long idx = (long long)k1 * P.n0 + k0;
+            const double kap = kappa_at(P, k1, k0);
+            const double2 yh{(double)in[o].x, (double)in[o].y};
+            const double2 v{s.v.x + yh.x, s.v.y + yh.y};
+            P.VR64[idx] = v;
+            const double2 w = reb ? double2{s.w.x + Ai * yh.x, s.w.y + Ai * yh.y}
+                                  : double2{(double)in[0].x, (double)in[0].y};
+            P.WR64[idx] = w;
+            if (pfc) {
+                const double2 nl{s.n.x + (double)in[o + 1].x, s.n.y + (double)in[o + 1].y};
+                P.NR64[idx] = nl;
+                double2 G{0.0, 0.0};
+                if (kap != 0.0) {
+                    const double Lh = 1.0 - P.eps - 2.0 * kap + kap * kap;
+                    const double ik = iM / kap;
+                    G.x = w.x * ik + Lh * v.x + nl.x;
+                    G.y = w.y * ik + Lh * v.y + nl.y;
+                }
+                double2 d;
+                base_direction<T>(P, k, B, k1, k0, kap, G, d);
+                out[0] = C{(T)d.x, (T)d.y};
+            } else {
+                double2 G{0.0, 0.0};
+                if (kap != 0.0) {
+                    const double ik = iM / kap;
+                    G.x = w.x * ik + e4 * kap * kap * v.x;
+                    G.y = w.y * ik + e4 * kap * kap * v.y;
+                }
+                P.CL64[idx] = G;
+                const T f = (T)(-kap);
+                out[0] = C{f * in[o].x, f * in[o].y};
+            }
+        });
+}
+
+// FCH incremental: Lap VB_new = Lap VB_old + Lap y (FP64 physical), then the T
+// transforms of the nonlinear changes F'(VB_new) - F'(VB_old) and
+// P(VB_new) - P(VB_old), written as the iteration's difference formulas.
+template <class T, int NF>
+__device__ void phase_DN(const Params& P, const Tw& tw, char* smem) {
+    using C = cx<T>;
+    T* lbt = (T*)P.LBt;
+    const T* yb = (const T*)P.YB;
+    const T tau = (T)P.tau, e2 = (T)(P.eps * P.eps), eta1 = (T)P.eta1, eta2 = (T)P.eta2;
+    struct St { double vb, lb; T y; };
+    rowp<T, T, NF>(
+        P, tw, 1, 2, (const C*)P.DB, (C*)P.NB, smem,
+        [&](long long p, int, int) { return St{P.VB[p], P.LB64[p], yb[p]}; },
+        [&](long long p, int, int, const St& s, const T* in, T* out) {
+            const T ly = in[0];
+            const double lbn = s.lb + (double)ly;
+            P.LB64[p] = lbn;
+            lbt[p] = (T)lbn;
+            const T y = s.y;
+            const T b = (T)(s.vb - (double)s.y);
+            const T lb = (T)s.lb;
+            const T f1b = dF1(b, tau), f2b = dF2(b, tau);
+            const T df1 = y * ((T)3 * b * b + (T)3 * b * y + y * y + tau * ((T)2 * b + y) - (T)1);
+            const T df2 = y * ((T)6 * b + (T)3 * y + (T)2 * tau);
+            const T f1n = f1b + df1, f2n = f2b + df2;
+            out[0] = df1;
+            out[1] = -e2 * (df2 * lb + (f2n - eta1) * ly) + df2 * f1n + (f2b - eta2) * df1;
+        });
+}
+
+template <class T, int NF>
+__device__ void phase_EN(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
+    using C = cx<T>;
+    const StepK k = step_coeffs(P, c.step);
+    const Beta B = betas(P, k, c.step);
+    const double e2 = P.eps * P.eps;
+    const double l1 = lam_at(P, 1);
+    const long long H = (long long)P.h1 * P.n0;
+    struct St { double2 lin, f1, pp; };
+    colp<T, NF>(
+        P, tw, 2, 2, (const C*)P.NB, (C*)P.DB, smem,
+        [&](int k1, int k0) {
+            const long long idx = (long long)k1 * P.n0 + k0;
+            return St{P.CL64[idx], P.NR64[idx], P.NR64[idx + H]};
+        },
+        [&](int k1, int k0, const St& s, const C* in, C* out) {
+            const long long idx = (long long)k1 * P.n0 + k0;
+            const double kap = kappa_at(P, k1, k0);
+            const double2 f1{s.f1.x + (double)in[0].x, s.f1.y + (double)in[0].y};
+            const double2 pp{s.pp.x + (double)in[1].x, s.pp.y + (double)in[1].y};
+            P.NR64[idx] = f1;
+            P.NR64[idx + H] = pp;
+            double2 G{0.0, 0.0};
+            if (kap != 0.0) {
+                G.x = s.lin.x + e2 * kap * f1.x + pp.x;
+                G.y = s.lin.y + e2 * kap * f1.y + pp.y;
+            }
+            double2 d;
+            base_direction<T>(P, k, B, k1, k0, kap, G, d);
+            out[0] = C{(T)d.x, (T)d.y};
+            const double f = -kap * (1.0 + l1) * k.ts;
+            out[1] = C{(T)(f * d.x), (T)(f * d.y)};
+        });
 }
 
 // Iteration row pass (R1 reads the FP64 base direction, RI the T one):
@@ -1204,10 +1372,26 @@ __device__ void phase_im_r2(const Params& P, const Ctl& c, const Tw& tw, char* s
 
 // ------------------------------------------------------------ control
 
+// Whether the next base evaluation is incremental: FP32-mixed only, once a
+// reference point exists, except for the first evaluation of every refresh-th
+// step, which recomputes the reference spectra exactly in FP64.  The
+// incremental evaluation errs by about 1e-7 of the base shift, so it only seeds
+// iterations: the first acceptance check of every step is an exact FP64
+// evaluation (the caller passes new_step = 0 and requires exact_done).
+__host__ __device__ inline int inc_eval(const Params& P, int ref_ok, int gstep, int new_step) {
+    if (P.precision != P_MIXED || !ref_ok) return 0;
+    if (new_step && P.refresh > 0 && gstep % P.refresh == 0) return 0;
+    return 1;
+}
+
 __host__ __device__ inline Ctl ctl_init(const Params& P) {
     Ctl c;
     c.step = 0; c.it = 0; c.ev = 0; c.lastev = 0; c.cur = P.cur0; c.rech = 0; c.fail = 0;
     c.best_ev = 0; c.acc = 0; c.acc_cur = 0; c.acc_it = 0; c.acc_lastev = 0; c.acc_ev = 0; c.reb = 0;
+    c.ref_ok = P.ref_valid;
+    c.exact_done = 0;
+    c.ereb = 0;
+    c.inc = inc_eval(P, c.ref_ok, P.step0, 1);
     c.resid = 0.0; c.base_nrm = 0.0; c.best_nrm = 0.0; c.acc_resid = 0.0;
     switch (P.prog) {
         case PROG_RUN: c.ph = (P.nsteps > 0) ? PH_B : PH_DONE; break;
@@ -1230,6 +1414,7 @@ __device__ void ctl_advance(const Params& P, Ctl& c) {
     switch (c.ph) {
         case PH_B:
             if (!c.reb) { c.ev = 0; c.rech = 0; }
+            c.ereb = c.reb;  // the evaluation started by B is a rebase (kept through C..E)
             c.acc = 0;
             c.reb = 0;
             c.ph = PH_C;
@@ -1238,6 +1423,8 @@ __device__ void ctl_advance(const Params& P, Ctl& c) {
             if (P.model == M_FCH) { c.ph = PH_D; break; }
             [[fallthrough]];
         case PH_E:
+            c.ref_ok = 1;
+            if (!c.inc) c.exact_done = 1;
             if (!(fabs(ldcg(&P.sc->beta_sum[bank][0])) + fabs(ldcg(&P.sc->beta_sum[bank][1])) <= 1.0e300)) {
                 c.fail = ST_ENAN;  // non-finite initial guess
                 c.ph = PH_FAIL;
@@ -1269,6 +1456,8 @@ __device__ void ctl_advance(const Params& P, Ctl& c) {
                     c.acc_resid = nrm;
                     c.step++;
                     c.cur ^= 1;
+                    c.exact_done = 0;
+                    c.inc = t64 ? 0 : inc_eval(P, c.ref_ok, P.step0 + c.step, 1);
                     c.ph = PH_B;
                 } else {
                     c.ph = PH_ACCEPT;
@@ -1281,6 +1470,7 @@ __device__ void ctl_advance(const Params& P, Ctl& c) {
                 if (c.rech >= P.max_recheck) { c.fail = ST_ENOCONV; c.ph = PH_FAIL; break; }
                 c.rech++;
                 c.reb = 1;
+                c.inc = c.exact_done ? inc_eval(P, c.ref_ok, P.step0 + c.step, 0) : 0;
                 c.ph = PH_B;
             } else {
                 c.ph = PH_CI;
@@ -1309,11 +1499,26 @@ __device__ void ctl_advance(const Params& P, Ctl& c) {
 template <class T, int NF>
 __device__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red) {
     switch (c.ph) {
-        case PH_B: phase_B<T, NF>(P, c, tw, smem, red); break;
-        case PH_C: phase_C<T, NF>(P, c, tw, smem); break;
-        case PH_D: phase_D<T, NF>(P, tw, smem); break;
-        case PH_E: phase_E<T, NF>(P, c, tw, smem); break;
-        case PH_R1: phase_R<double, T, NF>(P, c, tw, smem, red, P.DB64); break;
+        case PH_B:
+            if (c.inc) phase_B<T, NF, true>(P, c, tw, smem, red);
+            else phase_B<T, NF, false>(P, c, tw, smem, red);
+            break;
+        case PH_C:
+            if (c.inc) phase_CN<T, NF>(P, c, tw, smem);
+            else phase_C<T, NF>(P, c, tw, smem);
+            break;
+        case PH_D:
+            if (c.inc) phase_DN<T, NF>(P, tw, smem);
+            else phase_D<T, NF>(P, tw, smem);
+            break;
+        case PH_E:
+            if (c.inc) phase_EN<T, NF>(P, c, tw, smem);
+            else phase_E<T, NF>(P, c, tw, smem);
+            break;
+        case PH_R1:
+            if (c.inc) phase_R<T, T, NF>(P, c, tw, smem, red, (const cx<T>*)P.DB);
+            else phase_R<double, T, NF>(P, c, tw, smem, red, P.DB64);
+            break;
         case PH_RI: phase_R<T, T, NF>(P, c, tw, smem, red, (const cx<T>*)P.DB); break;
         case PH_CI: phase_CI<T, NF>(P, c, tw, smem); break;
         case PH_ACCEPT: phase_accept<T>(P, c, red); break;
