@@ -443,6 +443,7 @@ static pagd_status run_chunk(pagd_solver* s, double* u_out, double dt, int nstep
     P.dt_prev0 = (s->step == 0) ? dt : s->dt_prev;
     P.nsteps = nsteps;
     P.out_real = u_out;
+    fill_step_table(P);
     pagd_status st = run_program(s, P);
     if (st != PAGD_OK) return st;
     Scal sc;
@@ -700,6 +701,7 @@ pagd_status pagd_step_static(pagd_solver* s, const double* un_dev, const double*
     P.dt_prev0 = step_index == 0 ? dt : dt_prev;
     P.nsteps = 1;
     P.out_real = unp1_dev;
+    fill_step_table(P);
     st = run_program(s, P);
     if (st != PAGD_OK) return st;
     Scal sc;

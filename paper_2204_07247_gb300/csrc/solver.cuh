@@ -65,6 +65,11 @@ struct StepStat {
 constexpr int kMaxK = 3;        // fields per pass
 constexpr int kThreads = 128;   // CTA size of the persistent kernel (4 warps)
 
+// scheme coefficients of one step (see compute_step_coeffs)
+struct StepK {
+    double a, b, c, thv, ts, Ai, rho, gun, thpc, m2;
+};
+
 struct Params {
     int model, scheme, precision, prog;
     int n0, n1, logn0, logn1, h1, logtw;
@@ -77,6 +82,11 @@ struct Params {
     double lam[16];      // (1 - eta_j sqrt s) / (1 + eta_j sqrt s)
     double tol, dt, dt_prev0;
     int step0, nsteps, cur0, nslots;  // nslots: norm / sum slots per step parity
+    double inv_npts;
+    // step coefficients filled on the host: [0] the first step of the run
+    // (n = 0), [1] the first step of this launch when n > 0 (previous step
+    // dt_prev0), [2] every other step; the device never divides by dt
+    StepK kc[3];
     long long warp_bytes;             // shared memory per warp
     // workspace
     double* U[2];
@@ -141,19 +151,15 @@ template <> __device__ __forceinline__ const cx<float>* tw_of<float>(const Tw& t
 
 // ---------------------------------------------------------------- helpers
 
-struct StepK {
-    double a, b, c, thv, ts, Ai, rho, gun, thpc;
-};
 
 // Scheme coefficients a_n, b_n, c_n (Eqs. obj:BDF2, obj:MP; backward Euler /
 // its IMEX version for the first BDF2 / LBDF2 step, Algorithm 3 caption), the
 // weight theta_v of the new iterate in breve u, and the extrapolation ratio rho.
-__host__ __device__ __forceinline__ StepK step_coeffs(const Params& P, int step) {
+// Host side; the device reads the table P.kc.
+inline StepK compute_step_coeffs(int scheme, int n, double dt, double dtp, double s, int theta_mode,
+                                 double M) {
     StepK k;
-    const int n = P.step0 + step;
-    const double dt = P.dt;
-    const double dtp = (step == 0) ? P.dt_prev0 : P.dt;
-    const bool bdf = (P.scheme == S_BDF2 || P.scheme == S_LBDF2);
+    const bool bdf = (scheme == S_BDF2 || scheme == S_LBDF2);
     if (!bdf || n == 0) {
         k.a = 1.0 / dt; k.b = -1.0 / dt; k.c = 0.0;
     } else {
@@ -161,13 +167,26 @@ __host__ __device__ __forceinline__ StepK step_coeffs(const Params& P, int step)
         k.b = -1.0 / dt - 1.0 / dtp;
         k.c = 1.0 / dtp - 1.0 / (dt + dtp);
     }
-    k.thv = (P.scheme == S_MP) ? 0.5 : 1.0;
-    k.ts = k.thv * P.s;
+    k.thv = (scheme == S_MP) ? 0.5 : 1.0;
+    k.ts = k.thv * s;
     k.Ai = k.a / k.thv;
     k.rho = (n == 0) ? 0.0 : dt / dtp;
     k.gun = k.a * (1.0 - k.thv) / k.thv;
-    k.thpc = (P.scheme == S_MP && P.theta_mode == 0) ? 0.5 : 1.0;
+    k.thpc = (scheme == S_MP && theta_mode == 0) ? 0.5 : 1.0;
+    k.m2 = k.a / M;
     return k;
+}
+
+inline void fill_step_table(Params& P) {
+    P.kc[0] = compute_step_coeffs(P.scheme, 0, P.dt, P.dt, P.s, P.theta_mode, P.M);
+    P.kc[1] = compute_step_coeffs(P.scheme, P.step0 > 0 ? P.step0 : 1, P.dt, P.dt_prev0, P.s, P.theta_mode, P.M);
+    P.kc[2] = compute_step_coeffs(P.scheme, 1, P.dt, P.dt, P.s, P.theta_mode, P.M);
+    P.inv_npts = 1.0 / (double)P.npts;
+}
+
+__host__ __device__ __forceinline__ const StepK& step_coeffs(const Params& P, int step) {
+    const int n = P.step0 + step;
+    return P.kc[n == 0 ? 0 : (step == 0 ? 1 : 2)];
 }
 
 struct Beta {
@@ -178,9 +197,9 @@ struct Beta {
 // of the initial guess of this step.
 __device__ __forceinline__ Beta betas(const Params& P, const StepK& k, int step) {
     Beta B;
-    const double inv = 1.0 / (double)P.npts;
+    const double inv = P.inv_npts;
     const int bank = step & 1;
-    B.m2 = k.a / P.M;
+    B.m2 = k.m2;
     const double s0 = ldcg(&P.sc->beta_sum[bank][0]) * inv;
     if (P.model == M_PFC) {
         B.b0 = k.thpc * fabs(s0);
@@ -644,7 +663,7 @@ __host__ __device__ __forceinline__ int k_base(int model) { return model == M_PF
 template <class T, int NF, bool INC>
 __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red) {
     using TO = typename std::conditional<INC, T, double>::type;
-    const StepK k = step_coeffs(P, c.step);
+    const StepK& k = step_coeffs(P, c.step);
     const int bank = c.step & 1;
     T* vbt = (T*)P.VBt;
     T* d0 = (T*)P.DD[0];
@@ -681,7 +700,8 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
         P.sc->steps_done = c.step;
     }
     double s0 = 0.0, s2 = 0.0;
-    const double e2 = P.eps * P.eps;
+    const float c1e = (float)(1.0 - P.eps), tauf = (float)P.tau, eta1f = (float)P.eta1, eta2f = (float)P.eta2,
+                e2f = (float)(P.eps * P.eps);
     const int kb = k_base(P.model);
     const bool pfc = P.model == M_PFC;
     const bool reb = c.reb != 0, acc = c.acc != 0;
@@ -722,12 +742,14 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
                 vb = k.thv * x0 + (1.0 - k.thv) * a;
                 g = k.b * a + k.c * b - k.gun * a;
                 P.G64[p] = g;
+                // averaged-Newton sums: preconditioner constants, FP32 is enough
+                const float vf = (float)vb;
                 if (pfc) {
-                    s0 += 3.0 * vb * vb + 1.0 - P.eps;
+                    s0 += (double)(3.0f * vf * vf + c1e);
                 } else {
-                    const double f1 = dF1(vb, P.tau), f2 = dF2(vb, P.tau), f3 = dF3(vb, P.tau);
-                    s0 += f2 * f2 - P.eta2 * f2 + f3 * f1;
-                    s2 += e2 * (f2 - P.eta1);
+                    const float f1 = dF1(vf, tauf), f2 = dF2(vf, tauf), f3 = dF3(vf, tauf);
+                    s0 += (double)(f2 * f2 - eta2f * f2 + f3 * f1);
+                    s2 += (double)(e2f * (f2 - eta1f));
                 }
             }
             P.VB[p] = vb;
@@ -742,7 +764,10 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
                 const int o = reb ? 0 : 1;
                 if (!reb) out[0] = (TO)(Ai * vb + g);
                 out[o] = (TO)y;
-                if (pfc) out[o + 1] = (TO)(y * (3.0 * r * r + 3.0 * r * y + y * y));
+                if (pfc) {
+                    const TO yt = (TO)y, rt = (TO)r;
+                    out[o + 1] = yt * ((TO)3 * rt * rt + (TO)3 * rt * yt + yt * yt);
+                }
             } else {
                 out[0] = vb;
                 out[1] = g;
@@ -793,7 +818,7 @@ __device__ void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem)
         P.mass[0] += P.mass[1];
         P.mass[1] = 0.0;
     }
-    const StepK k = step_coeffs(P, c.step);
+    const StepK& k = step_coeffs(P, c.step);
     const Beta B = betas(P, k, c.step);
     const int kb = k_base(P.model);
     const double iM = 1.0 / P.M;
@@ -856,7 +881,7 @@ __device__ void phase_D(const Params& P, const Tw& tw, char* smem) {
 
 template <class T, int NF>
 __device__ void phase_E(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
-    const StepK k = step_coeffs(P, c.step);
+    const StepK& k = step_coeffs(P, c.step);
     const Beta B = betas(P, k, c.step);
     const double e2 = P.eps * P.eps;
     const double l1 = lam_at(P, 1);
@@ -890,7 +915,7 @@ __device__ void phase_CN(const Params& P, const Ctl& c, const Tw& tw, char* smem
         P.mass[0] += P.mass[1];
         P.mass[1] = 0.0;
     }
-    const StepK k = step_coeffs(P, c.step);
+    const StepK& k = step_coeffs(P, c.step);
     const Beta B = betas(P, k, c.step);
     const bool reb = c.ereb != 0;
     const int kb = k_base(P.model);
@@ -975,7 +1000,7 @@ __device__ void phase_DN(const Params& P, const Tw& tw, char* smem) {
 template <class T, int NF>
 __device__ void phase_EN(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     using C = cx<T>;
-    const StepK k = step_coeffs(P, c.step);
+    const StepK& k = step_coeffs(P, c.step);
     const Beta B = betas(P, k, c.step);
     const double e2 = P.eps * P.eps;
     const double l1 = lam_at(P, 1);
@@ -1013,7 +1038,7 @@ __device__ void phase_EN(const Params& P, const Ctl& c, const Tw& tw, char* smem
 template <class TI, class T, int NF>
 __device__ void phase_R(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red,
                         const cx<TI>* src) {
-    const StepK k = step_coeffs(P, c.step);
+    const StepK& k = step_coeffs(P, c.step);
     const int it = c.it;
     const int bank = c.step & 1;
     const T lp = (T)lam_at(P, it - 1), l = (T)lam_at(P, it), ts = (T)k.ts;
@@ -1070,7 +1095,7 @@ __device__ void phase_R(const Params& P, const Ctl& c, const Tw& tw, char* smem,
 template <class T, int NF>
 __device__ void phase_CI(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     using C = cx<T>;
-    const StepK k = step_coeffs(P, c.step);
+    const StepK& k = step_coeffs(P, c.step);
     const Beta B = betas(P, k, c.step);
     const int it = c.it;
     const T l = (T)lam_at(P, it), ln = (T)lam_at(P, it + 1), ts = (T)k.ts;
@@ -1126,7 +1151,7 @@ __device__ void phase_CI(const Params& P, const Ctl& c, const Tw& tw, char* smem
 // arithmetic (Remark on discrete mass conservation) and is removed in FP64.
 template <class T>
 __device__ void phase_accept(const Params& P, const Ctl& c, double* red) {
-    const StepK k = step_coeffs(P, c.step);
+    const StepK& k = step_coeffs(P, c.step);
     const int bank = c.step & 1;
     const T* dc = (const T*)P.DD[c.it & 1];
     const double* un = P.U[c.cur];
@@ -1265,7 +1290,7 @@ inline __device__ void phase_mass(const Params& P, double* red) {
 //   IM_R2: inverse x-DFT of u^{n+1} -> written over u^{n-1}
 template <int NF>
 __device__ void phase_im_r0(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
-    const StepK k = step_coeffs(P, c.step);
+    const StepK& k = step_coeffs(P, c.step);
     const double* un = P.U[c.cur];
     const double* um = P.U[c.cur ^ 1];
     const bool pfc = P.model == M_PFC;
@@ -1304,7 +1329,7 @@ __device__ __forceinline__ double2 imex_solve(const Params& P, const StepK& k, d
 }
 template <int NF>
 __device__ void phase_im_c0(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
-    const StepK k = step_coeffs(P, c.step);
+    const StepK& k = step_coeffs(P, c.step);
     if (P.model == M_PFC) {
         colp<double, NF>(P, tw, 3, 1, P.NB64, P.DB64, smem, [&](int, int) { return Nil{}; },
                          [&](int k1, int k0, const Nil&, const double2* in, double2* out) {
@@ -1337,7 +1362,7 @@ __device__ void phase_im_r1(const Params& P, const Tw& tw, char* smem) {
 }
 template <int NF>
 __device__ void phase_im_c1(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
-    const StepK k = step_coeffs(P, c.step);
+    const StepK& k = step_coeffs(P, c.step);
     const double e2 = P.eps * P.eps;
     struct St { double2 un, um; };
     colp<double, NF>(P, tw, 2, 1, P.NB64, P.DB64, smem,
