@@ -170,6 +170,44 @@ pagd_status pagd_get_trace(pagd_solver* s, int* phase, double* t_us, int cap, in
 const char* pagd_last_error(const pagd_solver* s);
 void pagd_destroy(pagd_solver* s);
 
+/* ---- Batches: many independent instances in one persistent launch.
+ * The paper solves one instance at a time; a batch runs the same per-instance
+ * computation (Algorithm 2 on every time step of every member) for a set of
+ * solvers of possibly different grids, models, parameters, schemes and
+ * initial data.  Members keep running independently: each takes its own number
+ * of PAGD iterations per step, and a member that fails (PAGD_ENOCONV, ...)
+ * stops while the others go on.  Results equal those of pagd_run on each member
+ * up to the summation order of the grid reductions.
+ *
+ * members: solvers from pfc_init / fch_init, all of one precision and one
+ * stream, each with its workspace and state set (pagd_set_state); the batch
+ * borrows them (does not own or copy them) and they must outlive it.  count:
+ * 1..4096, limited further by shared memory (PAGD_EINVAL when the largest
+ * member's passes and the per-member control state do not fit one CTA).  A
+ * member may appear once. */
+typedef struct pagd_batch pagd_batch; /* opaque, library-owned host object */
+
+pagd_status pagd_batch_create(pagd_batch** out, pagd_solver* const* members, int count);
+
+/* Device workspace of the batch (member parameter blocks and the launch's
+ * barrier state), handed in like a solver's workspace (256-byte aligned). */
+pagd_status pagd_batch_workspace_size(const pagd_batch* b, size_t* bytes);
+pagd_status pagd_batch_set_workspace(pagd_batch* b, void* dev_ptr, size_t bytes);
+
+/* Advance every member nsteps steps of size dt to tolerance tol (as pagd_run),
+ * in one device launch per chunk of at most 4096 steps.  Outputs, all
+ * nullable host arrays: iters_out / resid_out [count x nsteps], member-major
+ * (entries after a member's failing step are not written); status_out [count]
+ * per-member status.  Returns PAGD_OK when every member completed, else the
+ * status of the first member (by index) that failed, or the launch's error.
+ * Each member's u^n, u^{n-1} and step count advance as with pagd_run (read them
+ * with pagd_get_state).  Synchronises the stream. */
+pagd_status pagd_batch_run(pagd_batch* b, double dt, int nsteps, double tol, int* iters_out, double* resid_out,
+                           int* status_out);
+
+const char* pagd_batch_last_error(const pagd_batch* b);
+void pagd_batch_destroy(pagd_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,9 +18,11 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpagd.so")
 EMU = os.path.join(BUILD, "libpagd_emu.so")
-# host code + one kernel translation unit per fixed line length (0: runtime length)
-SOURCES = ["pagd.cu", "pagd_k0.cu", "pagd_k64.cu", "pagd_k128.cu", "pagd_k256.cu", "pagd_k512.cu"]
-HEADERS = ["compat.cuh", "fft.cuh", "solver.cuh", "kernels.cuh"]
+# host code, one kernel translation unit per fixed line length (0: runtime length)
+# and the batched kernel per iteration precision
+SOURCES = ["pagd.cu", "pagd_k0.cu", "pagd_k64.cu", "pagd_k128.cu", "pagd_k256.cu", "pagd_k512.cu",
+           "pagd_batch_f32.cu", "pagd_batch_f64.cu"]
+HEADERS = ["compat.cuh", "fft.cuh", "solver.cuh", "kernels.cuh", "batch.cuh"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 

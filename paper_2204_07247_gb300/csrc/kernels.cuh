@@ -17,28 +17,34 @@ __device__ __forceinline__ unsigned long long gtimer() {
     return t;
 }
 
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 // Device-wide barrier for a cooperative launch (all CTAs co-resident).  The
-// wait is bounded: after kBarrierTimeoutNs, or once another CTA has flagged an
-// error, the CTA records the error and returns false instead of spinning on.
+// arrival counter only grows: barrier number g (from 1) is complete once it
+// reaches g * gridDim.x.  Thread 0 publishes the CTA's writes with a release
+// add (ordered after the CTA's other threads by __syncthreads) and waits with
+// acquire loads.  The wait is bounded: after kBarrierTimeoutNs, or once another
+// CTA has flagged an error, the CTA records the error and returns false
+// instead of spinning on.
 static __device__ bool grid_barrier(Scal* sc, unsigned& gen) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned g = gen;
-        __threadfence();
-        const unsigned prev = atomicAdd(&sc->bar_count, 1u);
-        if (prev == gridDim.x - 1) {
-            atomicExch(&sc->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&sc->bar_gen, 1u);
-        } else {
+        const unsigned long long target = (unsigned long long)(gen + 1) * gridDim.x;
+        red_release_add(&sc->bar_count, 1ull);
+        if (ld_acquire(&sc->bar_count) < target) {
             const unsigned long long t0 = gtimer();
-            volatile unsigned* vg = &sc->bar_gen;
             volatile int* ve = &sc->bar_error;
-            while (*vg == g) {
+            while (ld_acquire(&sc->bar_count) < target) {
                 if (*ve) { ok = 0; break; }
-                __nanosleep(32);
                 if (gtimer() - t0 > kBarrierTimeoutNs) {
                     atomicOr(&sc->bar_error, 1);
                     ok = 0;
@@ -46,7 +52,6 @@ static __device__ bool grid_barrier(Scal* sc, unsigned& gen) {
                 }
             }
         }
-        __threadfence();
         s_ok = ok;
     }
     gen++;
@@ -68,7 +73,9 @@ __global__ void __launch_bounds__(kThreads, 1) pagd_kernel(Params P) {
         t32[m] = P.tw32[m * stride];
     }
     __syncthreads();
-    const Tw tw{t64, t32, P.logtw};
+    const int wpb = blockDim.x / kWarp;
+    const Tw tw{t64, t32, P.logtw, (int)(threadIdx.x / kWarp) * (int)gridDim.x + (int)blockIdx.x,
+                (int)gridDim.x * wpb, 0, -1};
     char* wsm = smem + tw_smem_bytes(P.logtw);
     Ctl c = ctl_init(P);
     unsigned gen = 0;

@@ -22,6 +22,8 @@ using namespace pagd;
 namespace pagd {
 template <class T, int NF>
 cudaError_t pagd_launch(const Params& P, int grid, size_t smem, void* stream, int* grid_used);
+template <class T>
+cudaError_t pagd_batch_launch(const BatchParams& B, int grid, size_t smem, void* stream, int* grid_used);
 }
 #else
 thread_local EmuDim3 threadIdx{0, 0, 0}, blockIdx{0, 0, 0}, blockDim{1, 1, 1}, gridDim{1, 1, 1};
@@ -30,6 +32,8 @@ thread_local EmuDim3 threadIdx{0, 0, 0}, blockIdx{0, 0, 0}, blockDim{1, 1, 1}, g
 // ------------------------------------------------------------ solver object
 
 constexpr int kMaxChunk = 4096;
+constexpr size_t kMaxSmem = 227 * 1024;  // dynamic shared memory per CTA on sm_103a
+constexpr int kMaxBatch = 4096;
 constexpr int kTraceCap = 8192;  // phase records kept per launch when tracing
 // FP32-mixed: steps between exact FP64 recomputations of the reference spectra
 constexpr int kRefreshSteps = 32;
@@ -210,13 +214,14 @@ template <class T> static pagd_status launch(pagd_solver* s, const Params& P) {
         t64[m] = P.tw64[m * (kNMax >> P.logtw)];
         t32[m] = P.tw32[m * (kNMax >> P.logtw)];
     }
-    const Tw tw{t64, t32, P.logtw};
+    Tw tw{t64, t32, P.logtw, 0, s->grid, 0, -1};
     char* wsm = base + tw_smem_bytes(P.logtw);
     Ctl c = ctl_init(P);
     const int nf = fixed_len(P.n0, P.n1);
     while (c.ph != PH_DONE) {
         for (int b = 0; b < s->grid; b++) {
             blockIdx.x = (unsigned)b;
+            tw.wr = b;
             switch (nf) {
                 case 64: exec_phase<T, 64>(P, c, tw, wsm, red); break;
                 case 128: exec_phase<T, 128>(P, c, tw, wsm, red); break;
@@ -433,8 +438,8 @@ static pagd_status status_from(int st) {
     }
 }
 
-static pagd_status run_chunk(pagd_solver* s, double* u_out, double dt, int nsteps, double tol, int* iters,
-                             double* resid) {
+// Parameters of a run of nsteps steps of size dt on s (one launch).
+static Params run_params(const pagd_solver* s, double* u_out, double dt, int nsteps, double tol) {
     Params P = base_params(s);
     const bool imex = s->scheme == PAGD_LBDF2 || s->scheme == PAGD_LMP;
     P.prog = imex ? PROG_IMEX : PROG_RUN;
@@ -444,13 +449,21 @@ static pagd_status run_chunk(pagd_solver* s, double* u_out, double dt, int nstep
     P.nsteps = nsteps;
     P.out_real = u_out;
     fill_step_table(P);
-    pagd_status st = run_program(s, P);
-    if (st != PAGD_OK) return st;
+    return P;
+}
+
+// Reads back the outcome of a run launched with P (the stream must be idle):
+// per-step results, the solver's step count and history slot.  bar_error: the
+// launch's device barrier gave up.
+static pagd_status run_finish(pagd_solver* s, const Params& P, double dt, int nsteps, int* iters, double* resid,
+                              bool bar_error) {
+    const bool imex = s->scheme == PAGD_LBDF2 || s->scheme == PAGD_LMP;
     Scal sc;
-    st = dcopy(s, &sc, P.sc, sizeof(Scal));
+    pagd_status st = dcopy(s, &sc, P.sc, sizeof(Scal));
     if (st == PAGD_OK) st = dsync(s);
     if (st != PAGD_OK) return st;
-    std::vector<StepStat> stats(nsteps);
+    bar_error = bar_error || sc.bar_error;
+    std::vector<StepStat> stats(nsteps > 0 ? nsteps : 1);
     const int ndone = sc.steps_done;
     const int nrec = (sc.status != ST_OK) ? ndone + 1 : ndone;
     if (nrec > 0) {
@@ -469,8 +482,8 @@ static pagd_status run_chunk(pagd_solver* s, double* u_out, double dt, int nstep
     }
     // the reference spectra of the incremental base evaluation stay valid only
     // after a run that ended on an accepted step
-    s->ref_valid = (!imex && sc.status == ST_OK && !sc.bar_error && ndone == nsteps && nsteps > 0) ? 1 : 0;
-    if (sc.bar_error) return fail(s, PAGD_ETIMEOUT, "device barrier timed out");
+    s->ref_valid = (!imex && sc.status == ST_OK && !bar_error && ndone == nsteps && nsteps > 0) ? 1 : 0;
+    if (bar_error) return fail(s, PAGD_ETIMEOUT, "device barrier timed out");
     if (sc.status != ST_OK) {
         char buf[160];
         std::snprintf(buf, sizeof(buf), "step %d (global %d) failed with status %d after %d evaluations",
@@ -479,6 +492,14 @@ static pagd_status run_chunk(pagd_solver* s, double* u_out, double dt, int nstep
     }
     if (ndone != nsteps) return fail(s, PAGD_ECUDA, "kernel ended early");
     return PAGD_OK;
+}
+
+static pagd_status run_chunk(pagd_solver* s, double* u_out, double dt, int nsteps, double tol, int* iters,
+                             double* resid) {
+    Params P = run_params(s, u_out, dt, nsteps, tol);
+    pagd_status st = run_program(s, P);
+    if (st != PAGD_OK) return st;
+    return run_finish(s, P, dt, nsteps, iters, resid, false);
 }
 
 pagd_status pagd_run(pagd_solver* s, double* u_dev, double dt, int nsteps, double tol, int* iters_out,
@@ -749,6 +770,234 @@ pagd_status pagd_get_trace(pagd_solver* s, int* phase, double* t_us, int cap, in
     }
     return PAGD_OK;
 }
+
+// ------------------------------------------------------------ batches
+
+}  // extern "C"
+
+struct pagd_batch {
+    std::vector<pagd_solver*> m;
+    int tsize, logtw, grid;
+    size_t warp_bytes, smem, ws_bytes;
+    char* ws;
+    void* stream;
+    std::string err;
+};
+
+static pagd_status bfail(pagd_batch* b, pagd_status st, const char* msg) {
+    if (b) b->err = msg;
+    return st;
+}
+
+static size_t batch_off_params() { return (sizeof(Scal) + 255) & ~(size_t)255; }
+
+#ifdef PAGD_EMU
+template <class T> static void batch_exec_host(const Params& P, const Ctl& c, const Tw& t, char* wsm, double* red) {
+    switch (batch_nf(P.n0, P.n1)) {
+        case 128: exec_phase<T, 128>(P, c, t, wsm, red); break;
+        case 256: exec_phase<T, 256>(P, c, t, wsm, red); break;
+        case 512: exec_phase<T, 512>(P, c, t, wsm, red); break;
+        default: exec_phase<T, 0>(P, c, t, wsm, red); break;
+    }
+}
+// the batched kernel's schedule, one CTA (of one thread) after the other
+template <class T> static pagd_status batch_launch(pagd_batch* b, const BatchParams& B) {
+    std::vector<char> sm(b->smem + 64);
+    char* base = (char*)(((uintptr_t)sm.data() + 15) & ~(uintptr_t)15);
+    double red[32];
+    gridDim.x = (unsigned)b->grid;
+    blockDim.x = 1;
+    threadIdx.x = 0;
+    const int ntw = 1 << B.logtw;
+    double2* t64 = (double2*)base;
+    float2* t32 = (float2*)(base + (size_t)ntw * sizeof(double2));
+    for (int m = 0; m < ntw; m++) {
+        t64[m] = B.tw64[m * (kNMax >> B.logtw)];
+        t32[m] = B.tw32[m * (kNMax >> B.logtw)];
+    }
+    char* wsm = base + tw_smem_bytes(B.logtw) + batch_ctl_bytes(B.count);
+    std::vector<Ctl> ctl(B.count);
+    std::vector<long long> G(B.count + 1);
+    for (int i = 0; i < B.count; i++) ctl[i] = ctl_init(B.PI[i]);
+    const long long nw = b->grid;
+    for (;;) {
+        G[0] = 0;
+        for (int i = 0; i < B.count; i++)
+            G[i + 1] = G[i] + (ctl[i].ph == PH_DONE ? 0
+                                                    : (long long)phase_units(B.PI[i], ctl[i].ph) *
+                                                          unit_cost(B.PI[i], ctl[i].ph));
+        const long long total = G[B.count];
+        if (total == 0) break;
+        for (int blk = 0; blk < b->grid; blk++) {
+            blockIdx.x = (unsigned)blk;
+            const long long clo = cost_start(blk, total, nw), chi = cost_start(blk + 1, total, nw);
+            for (int i = 0; i < B.count; i++) {
+                if (G[i + 1] <= clo || G[i] >= chi || G[i + 1] == G[i]) continue;
+                const Params& P = B.PI[i];
+                Tw t{t64, t32, B.logtw, 0, 0, 0, 0};
+                batch_split(t, blk, nw, total, G[i], G[i + 1] - G[i], phase_units(P, ctl[i].ph),
+                            unit_cost(P, ctl[i].ph));
+                batch_exec_host<T>(P, ctl[i], t, wsm, red);
+            }
+        }
+        for (int i = 0; i < B.count; i++)
+            if (ctl[i].ph != PH_DONE) ctl_advance<T>(B.PI[i], ctl[i]);
+    }
+    return PAGD_OK;
+}
+#else
+template <class T> static pagd_status batch_launch(pagd_batch* b, const BatchParams& B) {
+    int used = 0;
+    cudaError_t e = pagd_batch_launch<T>(B, b->grid, b->smem, b->stream, &used);
+    if (e != cudaSuccess) {
+        char buf[256];
+        std::snprintf(buf, sizeof(buf), "cooperative launch of pagd_batch_kernel: %s", cudaGetErrorString(e));
+        return bfail(b, PAGD_ECUDA, buf);
+    }
+    return PAGD_OK;
+}
+#endif
+
+extern "C" {
+
+pagd_status pagd_batch_create(pagd_batch** out, pagd_solver* const* members, int count) {
+    if (!out) return PAGD_EINVAL;
+    *out = nullptr;
+    if (!members || count < 1 || count > kMaxBatch) return PAGD_EINVAL;
+    for (int i = 0; i < count; i++) {
+        if (!members[i]) return PAGD_EINVAL;
+        if (members[i]->tsize != members[0]->tsize) return PAGD_EINVAL;  // one precision per batch
+        for (int j = 0; j < i; j++)
+            if (members[j] == members[i]) return PAGD_EINVAL;
+    }
+    pagd_batch* b = new (std::nothrow) pagd_batch();
+    if (!b) return PAGD_ENOMEM;
+    b->m.assign(members, members + count);
+    b->tsize = members[0]->tsize;
+    b->stream = members[0]->stream;
+    b->logtw = 0;
+    b->warp_bytes = 0;
+    for (pagd_solver* s : b->m) {
+        const int l0 = ilog2(s->n[0]), l1 = ilog2(s->n[1]);
+        b->logtw = std::max(b->logtw, std::max(l0, l1));
+        b->warp_bytes = std::max(b->warp_bytes, warp_smem_bytes(s->n[0], s->n[1], s->model, s->tsize,
+                                                                batch_nf(s->n[0], s->n[1])));
+    }
+#ifdef PAGD_EMU
+    const int wpb = 1;
+#else
+    const int wpb = kThreads / 32;
+#endif
+    b->smem = tw_smem_bytes(b->logtw) + batch_ctl_bytes(count) + (size_t)wpb * b->warp_bytes;
+    if (b->smem > kMaxSmem) {
+        delete b;
+        return PAGD_EINVAL;
+    }
+    b->grid = num_sms();
+    b->ws_bytes = batch_off_params() + sizeof(Params) * (size_t)count;
+    b->ws = nullptr;
+    *out = b;
+    return PAGD_OK;
+}
+
+pagd_status pagd_batch_workspace_size(const pagd_batch* b, size_t* bytes) {
+    if (!b || !bytes) return PAGD_EINVAL;
+    *bytes = b->ws_bytes;
+    return PAGD_OK;
+}
+
+pagd_status pagd_batch_set_workspace(pagd_batch* b, void* dev_ptr, size_t bytes) {
+    if (!b || !dev_ptr) return PAGD_EINVAL;
+    if (bytes < b->ws_bytes) return bfail(b, PAGD_ENOMEM, "batch workspace too small");
+    if (((uintptr_t)dev_ptr & 255) != 0) return bfail(b, PAGD_EINVAL, "batch workspace not 256-byte aligned");
+    b->ws = (char*)dev_ptr;
+    return PAGD_OK;
+}
+
+static pagd_status batch_chunk(pagd_batch* b, double dt, int nsteps, double tol, std::vector<int>& live,
+                               int done, int total_steps, int* iters_out, double* resid_out, int* status_out) {
+    const int count = (int)b->m.size();
+    std::vector<Params> PI(count);
+    pagd_status st = PAGD_OK;
+    for (int i = 0; i < count; i++) {
+        pagd_solver* s = b->m[i];
+        PI[i] = run_params(s, nullptr, dt, live[i] ? nsteps : 0, tol);
+        PI[i].trace = nullptr;
+        PI[i].warp_bytes = (long long)b->warp_bytes;
+        PI[i].logtw = b->logtw;
+        st = dzero(s, PI[i].sc, sizeof(Scal));
+        if (st != PAGD_OK) return bfail(b, st, s->err.c_str());
+    }
+    pagd_solver* s0 = b->m[0];
+    Scal* bsc = (Scal*)b->ws;
+    Params* dPI = (Params*)(b->ws + batch_off_params());
+    st = dzero(s0, bsc, sizeof(Scal));
+    if (st == PAGD_OK) st = dcopy(s0, dPI, PI.data(), sizeof(Params) * (size_t)count);
+    if (st != PAGD_OK) return bfail(b, st, s0->err.c_str());
+    BatchParams B;
+    B.PI = dPI;
+    B.count = count;
+    B.logtw = b->logtw;
+    B.sc = bsc;
+    B.tw64 = PI[0].tw64;
+    B.tw32 = PI[0].tw32;
+    st = (b->tsize == 8) ? batch_launch<double>(b, B) : batch_launch<float>(b, B);
+    if (st != PAGD_OK) return st;
+    Scal bs;
+    st = dcopy(s0, &bs, bsc, sizeof(Scal));
+    if (st == PAGD_OK) st = dsync(s0);
+    if (st != PAGD_OK) return bfail(b, st, s0->err.c_str());
+    pagd_status first = PAGD_OK;
+    for (int i = 0; i < count; i++) {
+        if (!live[i]) continue;
+        pagd_solver* s = b->m[i];
+        const pagd_status si =
+            run_finish(s, PI[i], dt, nsteps, iters_out ? iters_out + (size_t)i * total_steps + done : nullptr,
+                       resid_out ? resid_out + (size_t)i * total_steps + done : nullptr, bs.bar_error != 0);
+        if (si != PAGD_OK) {
+            live[i] = 0;
+            if (status_out) status_out[i] = si;
+            if (first == PAGD_OK) {
+                first = si;
+                char buf[256];
+                std::snprintf(buf, sizeof(buf), "member %d: %s", i, s->err.c_str());
+                b->err = buf;
+            }
+        }
+    }
+    return first;
+}
+
+pagd_status pagd_batch_run(pagd_batch* b, double dt, int nsteps, double tol, int* iters_out, double* resid_out,
+                           int* status_out) {
+    if (!b) return PAGD_EINVAL;
+    if (!b->ws) return bfail(b, PAGD_ESTATE, "no batch workspace");
+    if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0 || !(tol >= 0.0))
+        return bfail(b, PAGD_EINVAL, "bad dt / nsteps / tol");
+    const int count = (int)b->m.size();
+    for (int i = 0; i < count; i++) {
+        pagd_solver* s = b->m[i];
+        if (!s->ws || !s->have_state) return bfail(b, PAGD_ESTATE, "every member needs a workspace and a state");
+        if (s->stream != b->stream) return bfail(b, PAGD_EINVAL, "members must share one stream");
+    }
+    std::vector<int> live(count, 1);
+    if (status_out)
+        for (int i = 0; i < count; i++) status_out[i] = PAGD_OK;
+    pagd_status first = PAGD_OK;
+    int done = 0;
+    while (done < nsteps) {
+        const int c = (nsteps - done > kMaxChunk) ? kMaxChunk : nsteps - done;
+        const pagd_status st = batch_chunk(b, dt, c, tol, live, done, nsteps, iters_out, resid_out, status_out);
+        if (st != PAGD_OK && first == PAGD_OK) first = st;
+        if (st == PAGD_ECUDA || st == PAGD_ETIMEOUT || st == PAGD_ENOMEM) return st;
+        done += c;
+    }
+    return first;
+}
+
+const char* pagd_batch_last_error(const pagd_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void pagd_batch_destroy(pagd_batch* b) { delete b; }
 
 const char* pagd_last_error(const pagd_solver* s) { return s ? s->err.c_str() : "null solver"; }
 

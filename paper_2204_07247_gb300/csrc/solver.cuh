@@ -50,7 +50,7 @@ enum Phase {
 
 // device-resident scalars; zeroed by the host before every launch
 struct Scal {
-    unsigned bar_count, bar_gen;
+    unsigned long long bar_count;  // grid barrier arrivals (monotonic)
     int bar_error, flags;
     int status, steps_done, fail_step, ntrace;
     double beta_sum[2][2];  // [step parity][field]
@@ -139,12 +139,33 @@ struct Ctl {
 constexpr double kRebaseRatio = 1.0e-6;
 constexpr int kStagnation = 12;
 
-// twiddle tables exp(-2 pi i m / (1 << log)) staged in shared memory
+// Per-thread pass context: the twiddle tables exp(-2 pi i m / (1 << log))
+// staged in shared memory, and how the work of the current phase of one
+// instance is split among warps.  wr / wn: this warp's rank among the warps
+// working on the instance and their number.  uhi < 0: units are dealt round
+// robin by wr / wn (single-instance launches; the rank is CTA-major so that
+// every SM gets a busy warp before any SM gets a second); else the warp owns
+// the contiguous unit range [ulo, uhi) (batched launches).
 struct Tw {
     const double2* t64;
     const float2* t32;
     int log;
+    int wr, wn, ulo, uhi;
 };
+
+struct URange {
+    int b, e, s;
+};
+__device__ __forceinline__ URange units_of(const Tw& t, int units) {
+    if (t.uhi < 0) return URange{t.wr, units, t.wn};
+    return URange{t.ulo, t.uhi < units ? t.uhi : units, 1};
+}
+// the one thread of the instance's warps that writes per-instance scalars
+__device__ __forceinline__ bool leader(const Tw& t) { return t.wr == 0 && (threadIdx.x % kWarp) == 0; }
+__device__ __forceinline__ long long thread_rank(const Tw& t) {
+    return (long long)t.wr * kWarp + (long long)(threadIdx.x % kWarp);
+}
+__device__ __forceinline__ long long thread_count(const Tw& t) { return (long long)t.wn * kWarp; }
 template <class T> __device__ __forceinline__ const cx<T>* tw_of(const Tw& t);
 template <> __device__ __forceinline__ const cx<double>* tw_of<double>(const Tw& t) { return t.t64; }
 template <> __device__ __forceinline__ const cx<float>* tw_of<float>(const Tw& t) { return t.t32; }
@@ -301,20 +322,14 @@ __host__ __device__ __forceinline__ size_t col_warp_smem(int n0, int k, int sz) 
 }
 
 struct WarpCtx {
-    int lane, gw, nw;
+    int lane;
     char* mem;
 };
 
 __device__ __forceinline__ WarpCtx warp_ctx(const Params& P, char* smem) {
     WarpCtx w;
     w.lane = threadIdx.x % kWarp;
-    const int wib = threadIdx.x / kWarp, wpb = blockDim.x / kWarp;
-    // units go round-robin over CTAs first, so with one CTA per SM each SM gets
-    // one busy warp before any SM gets a second (FP64 work is bound by the
-    // per-SM FP64 pipe on this part)
-    w.gw = wib * gridDim.x + blockIdx.x;
-    w.nw = gridDim.x * wpb;
-    w.mem = smem + (size_t)wib * P.warp_bytes;
+    w.mem = smem + (size_t)(threadIdx.x / kWarp) * P.warp_bytes;
     return w;
 }
 
@@ -335,8 +350,8 @@ __device__ void row_pass(const Params& P, const Tw& tw, int kin, int kout, const
     TO* Rout = (TO*)(w.mem + (size_t)kin * ru * n1 * sizeof(TI));
     char* zb = w.mem + (size_t)kin * ru * n1 * sizeof(TI) + (size_t)kout * ru * n1 * sizeof(TO);
     const TI iscale = (TI)(1.0 / ((double)n0 * (double)n1));
-    const int nunits = n0 / ru;
-    for (int u = w.gw; u < nunits; u += w.nw) {
+    const URange ur = units_of(tw, n0 / ru);
+    for (int u = ur.b; u < ur.e; u += ur.s) {
         const int r0 = u * ru;
         for (int j = 0; 2 * j < kin * ru; j++) {
             CI* Z0 = (CI*)zb;
@@ -401,7 +416,8 @@ __device__ void col_pass(const Params& P, const Tw& tw, int kin, int kout, const
     const int pitch = pitch_of(n0);
     const int nb = (kin > kout ? kin : kout) + 1;
     const WarpCtx w = warp_ctx(P, smem);
-    for (int k1 = w.gw; k1 < h1; k1 += w.nw) {
+    const URange ur = units_of(tw, h1);
+    for (int k1 = ur.b; k1 < ur.e; k1 += ur.s) {
         C* buf[kMaxK + 1];
         for (int i = 0; i < nb; i++) buf[i] = (C*)w.mem + (size_t)i * pitch;
         for (int f = 0; f < kin; f++) {
@@ -466,7 +482,8 @@ __device__ void row_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
     CO* Y0 = (CO*)(X1 + (size_t)kin * PITCH);
     CO* Y1 = Y0 + (size_t)kout * PITCH;
     const TI iscale = (TI)(1.0 / ((double)n0 * (double)NF));
-    for (int u = w.gw; u < n0 / 2; u += w.nw) {
+    const URange ur = units_of(tw, n0 / 2);
+    for (int u = ur.b; u < ur.e; u += ur.s) {
         const int r0 = 2 * u;
         for (int l = 0; l < kin; l++) {
             const CI* s0 = src + (size_t)l * H1 * n0 + r0;
@@ -561,7 +578,8 @@ __device__ void col_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
     const WarpCtx w = warp_ctx(P, smem);
     C* B0 = (C*)w.mem;
     C* B1 = B0 + (size_t)kl * PITCH;
-    for (int k1 = w.gw; k1 < h1; k1 += w.nw) {
+    const URange ur = units_of(tw, h1);
+    for (int k1 = ur.b; k1 < ur.e; k1 += ur.s) {
         for (int f = 0; f < kin; f++) {
             const C* s = src + (size_t)f * h1 * NF + (size_t)k1 * NF;
 #pragma unroll
@@ -668,8 +686,8 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
     T* vbt = (T*)P.VBt;
     T* d0 = (T*)P.DD[0];
     T* d1 = (T*)P.DD[1];
-    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long gs = (long long)gridDim.x * blockDim.x;
+    const long long gt = thread_rank(tw);
+    const long long gs = thread_count(tw);
     // acceptance of step c.step - 1 (same scheme, so the same theta_v).  The
     // FP64 mean of the correction and the running mass excess K are removed; the
     // exact change sum(u^{n+1} - u^n) is fed back into K (error feedback keeps
@@ -693,7 +711,7 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
             P.sc->beta_sum[bank ^ 1][1] = 0.0;
         }
     }
-    if (c.acc && blockIdx.x == 0 && threadIdx.x == 0) {
+    if (c.acc && leader(tw)) {
         P.stats[c.step - 1].iters = c.acc_ev;
         P.stats[c.step - 1].status = ST_OK;
         P.stats[c.step - 1].resid = c.acc_resid;
@@ -813,7 +831,7 @@ __device__ __forceinline__ void base_direction(const Params& P, const StepK& k, 
 
 template <class T, int NF>
 __device__ void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (leader(tw)) {
         // fold the last acceptance's mass change into the running excess
         P.mass[0] += P.mass[1];
         P.mass[1] = 0.0;
@@ -911,7 +929,7 @@ __device__ void phase_E(const Params& P, const Ctl& c, const Tw& tw, char* smem)
 template <class T, int NF>
 __device__ void phase_CN(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     using C = cx<T>;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (leader(tw)) {
         P.mass[0] += P.mass[1];
         P.mass[1] = 0.0;
     }
@@ -1150,15 +1168,15 @@ __device__ void phase_CI(const Params& P, const Ctl& c, const Tw& tw, char* smem
 // accepted inside the next step's phase B.)  The mean of delta is zero in exact
 // arithmetic (Remark on discrete mass conservation) and is removed in FP64.
 template <class T>
-__device__ void phase_accept(const Params& P, const Ctl& c, double* red) {
+__device__ void phase_accept(const Params& P, const Ctl& c, const Tw& tw, double* red) {
     const StepK& k = step_coeffs(P, c.step);
     const int bank = c.step & 1;
     const T* dc = (const T*)P.DD[c.it & 1];
     const double* un = P.U[c.cur];
     double* unew = P.U[c.cur ^ 1];
     const double m = (ldcg(&P.sums[(size_t)bank * P.nslots + c.lastev]) + ldcg(&P.mass[0])) / (double)P.npts;
-    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long gs = (long long)gridDim.x * blockDim.x;
+    const long long gt = thread_rank(tw);
+    const long long gs = thread_count(tw);
     const double ith = 1.0 / k.thv, w = (1.0 - k.thv);
     double dmass = 0.0;
     for (long long p = gt; p < P.npts; p += gs) {
@@ -1171,7 +1189,7 @@ __device__ void phase_accept(const Params& P, const Ctl& c, double* red) {
     }
     dmass = block_sum(dmass, red);
     if (threadIdx.x == 0) atomicAdd(&P.mass[1], dmass);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (leader(tw)) {
         P.stats[c.step].iters = c.ev;
         P.stats[c.step].status = ST_OK;
         P.stats[c.step].resid = c.resid;
@@ -1179,8 +1197,8 @@ __device__ void phase_accept(const Params& P, const Ctl& c, double* red) {
     }
 }
 
-inline __device__ void phase_fail(const Params& P, const Ctl& c) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+inline __device__ void phase_fail(const Params& P, const Ctl& c, const Tw& tw) {
+    if (leader(tw)) {
         P.sc->status = c.fail;
         P.sc->fail_step = c.step;
         P.stats[c.step].iters = c.ev;
@@ -1269,10 +1287,10 @@ __device__ void phase_en_r2(const Params& P, const Tw& tw, char* smem, double* r
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) atomicAdd(&P.sc->red[0], acc);
 }
-inline __device__ void phase_mass(const Params& P, double* red) {
+inline __device__ void phase_mass(const Params& P, const Tw& tw, double* red) {
     double acc = 0.0;
-    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long gs = (long long)gridDim.x * blockDim.x;
+    const long long gt = thread_rank(tw);
+    const long long gs = thread_count(tw);
     for (long long p = gt; p < P.npts; p += gs) acc += P.in_real[p];
     acc = block_sum(acc, red);
     if (threadIdx.x == 0) atomicAdd(&P.sc->red[0], acc);
@@ -1387,7 +1405,7 @@ __device__ void phase_im_r2(const Params& P, const Ctl& c, const Tw& tw, char* s
                                  unew[p] = in[0];
                                  if (last) P.out_real[p] = in[0];
                              });
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (leader(tw)) {
         P.stats[c.step].iters = 0;
         P.stats[c.step].status = ST_OK;
         P.stats[c.step].resid = 0.0;
@@ -1546,8 +1564,8 @@ __device__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* sm
             break;
         case PH_RI: phase_R<T, T, NF>(P, c, tw, smem, red, (const cx<T>*)P.DB); break;
         case PH_CI: phase_CI<T, NF>(P, c, tw, smem); break;
-        case PH_ACCEPT: phase_accept<T>(P, c, red); break;
-        case PH_FAIL: phase_fail(P, c); break;
+        case PH_ACCEPT: phase_accept<T>(P, c, tw, red); break;
+        case PH_FAIL: phase_fail(P, c, tw); break;
         case PH_FWD_R: phase_fwd_r<NF>(P, tw, smem); break;
         case PH_FWD_C: phase_fwd_c<NF>(P, tw, smem); break;
         case PH_INV_C: phase_inv_c<NF>(P, tw, smem); break;
@@ -1555,7 +1573,7 @@ __device__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* sm
         case PH_EN_R: phase_en_r<NF>(P, tw, smem, red); break;
         case PH_EN_C: phase_en_c<NF>(P, tw, smem, red); break;
         case PH_EN_R2: phase_en_r2<NF>(P, tw, smem, red); break;
-        case PH_MASS: phase_mass(P, red); break;
+        case PH_MASS: phase_mass(P, tw, red); break;
         case PH_IM_R0: phase_im_r0<NF>(P, c, tw, smem); break;
         case PH_IM_C0: phase_im_c0<NF>(P, c, tw, smem); break;
         case PH_IM_R1: phase_im_r1<NF>(P, tw, smem); break;
@@ -1604,6 +1622,70 @@ __host__ __device__ inline size_t tw_smem_bytes(int logtw) { return ((size_t)1 <
 inline int fixed_len(int n0, int n1) {
     if (n0 != n1) return 0;
     return (n0 == 64 || n0 == 128 || n0 == 256 || n0 == 512) ? n0 : 0;
+}
+
+// ------------------------------------------------------------ batched launches
+//
+// One persistent launch can advance many independent instances (see
+// batch.cuh).  The work of a global phase is laid out on a cost axis: instance
+// i covers [G_i, G_i + units_i q_i), q_i the points one unit touches, and warp w
+// of the grid takes [C_w, C_{w+1}), C_w = floor(total w / NW).
+
+struct BatchParams {
+    Params* PI;  // device array of count instance parameter blocks
+    int count, logtw;
+    Scal* sc;    // barrier state of the launch
+    const double2* tw64;
+    const float2* tw32;
+};
+
+// phases whose units are half-spectrum columns; all others use row pairs
+__host__ __device__ inline bool phase_is_col(int ph) {
+    return ph == PH_C || ph == PH_E || ph == PH_CI || ph == PH_IM_C0 || ph == PH_IM_C1;
+}
+__host__ __device__ inline int phase_units(const Params& P, int ph) { return phase_is_col(ph) ? P.h1 : P.n0 / 2; }
+__host__ __device__ inline int unit_cost(const Params& P, int ph) { return phase_is_col(ph) ? P.n0 : 2 * P.n1; }
+
+// the fixed line lengths compiled into the batched kernel (others: runtime length)
+__host__ __device__ inline int batch_nf(int n0, int n1) {
+    if (n0 != n1) return 0;
+    return (n0 == 128 || n0 == 256 || n0 == 512) ? n0 : 0;
+}
+
+// warp owning cost position x (C_w <= x < C_{w+1})
+__host__ __device__ inline long long cost_owner(long long x, long long total, long long nw) {
+    return ((x + 1) * nw - 1) / total;
+}
+__host__ __device__ inline long long cost_start(long long w, long long total, long long nw) {
+    return (total * w) / nw;
+}
+
+// Tw of warp gw for instance i whose work is [g, g + cost) on the cost axis.
+__host__ __device__ inline void batch_split(Tw& t, long long gw, long long nw, long long total, long long g,
+                                            long long cost, int units, int q) {
+    const long long wa = cost_owner(g, total, nw), wb = cost_owner(g + cost - 1, total, nw);
+    if (gw < wa || gw > wb) {
+        t.wr = 1;
+        t.wn = 0;  // thread_rank >= thread_count: no point work
+        t.ulo = 0;
+        t.uhi = 0;
+        return;
+    }
+    t.wr = (int)(gw - wa);
+    t.wn = (int)(wb - wa + 1);
+    const long long c0 = cost_start(gw, total, nw) - g, c1 = cost_start(gw + 1, total, nw) - g;
+    long long lo = c0 <= 0 ? 0 : (c0 + q - 1) / q;
+    long long hi = c1 <= 0 ? 0 : (c1 + q - 1) / q;
+    if (lo > units) lo = units;
+    if (hi > units) hi = units;
+    t.ulo = (int)lo;
+    t.uhi = (int)hi;
+}
+
+// shared memory of the batched kernel besides the twiddles and the warp slices
+__host__ __device__ inline size_t batch_ctl_bytes(int count) {
+    const size_t c = (size_t)count * sizeof(Ctl) + (size_t)(count + 1) * sizeof(long long);
+    return (c + 15) & ~(size_t)15;
 }
 
 }  // namespace pagd

@@ -89,3 +89,43 @@ FCH256 = Workload("fch2d_256_bdf2_fp32mixed", "fch", (256, 256), (FOURPI, FOURPI
                   steps=1000, tol=1e-8, mean=-0.3, amp=0.05)
 
 WORKLOADS = {w.name: w for w in (PFC64, FCH256)}
+
+
+@dataclass
+class BatchWorkload:
+    """Independent instances advanced together (one dt, step count and tol)."""
+    name: str
+    members: list
+    dt: float
+    steps: int
+    tol: float
+
+    def u0s(self):
+        return [m.u0(m.seeds[0]) for m in self.members]
+
+
+def pfc_batch(sizes=(128, 256, 512), per_size=32, seed0=100, steps=500) -> BatchWorkload:
+    """Uneven PFC batch: per_size instances at each N in sizes, N x N points on
+    [0, N pi / 4]^2 (h = pi / 4), MP, FP32-mixed, dt = 0.1, tol 1e-8.  Instance
+    i (sizes in order) has seed seed0 + i: eps ~ U(0.02, 0.3) and
+    mean ~ U(0.05, 0.2) are the first two draws of the stream seed0 + i + 2^32,
+    and u0 = mean + 0.05 U(-1, 1) comes from the stream seed0 + i."""
+    members = []
+    i = 0
+    for N in sizes:
+        for _ in range(per_size):
+            seed = seed0 + i
+            a, b = uniform01(seed + (1 << 32), 2)
+            eps = 0.02 + 0.28 * float(a)
+            mean = 0.05 + 0.15 * float(b)
+            L = N * math.pi / 4.0
+            members.append(Workload(f"pfc2d_{N}_mp_fp32mixed_i{i}", "pfc", (N, N), (L, L), eps=eps,
+                                    scheme="mp", precision="fp32_mixed", dt=0.1, steps=steps, tol=1e-8,
+                                    mean=mean, amp=0.05, seeds=(seed,)))
+            i += 1
+    name = "pfc2d_batch{}_{}_mp_fp32mixed".format(len(members), "_".join(str(N) for N in sizes))
+    return BatchWorkload(name, members, dt=0.1, steps=steps, tol=1e-8)
+
+
+# 96 PFC instances, 32 each at 128^2, 256^2 and 512^2, 500 steps
+PFC_BATCH96 = pfc_batch()

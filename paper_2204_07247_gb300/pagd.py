@@ -28,7 +28,9 @@ PRECISIONS = {"fp64": FP64, "fp32_mixed": FP32_MIXED}
 EXPORTS = ("pagd_default_opts", "pfc_init", "fch_init", "pagd_workspace_size", "pagd_set_workspace",
            "pagd_set_state", "pagd_step", "pagd_run", "pagd_run_host", "pagd_energy", "pagd_mass",
            "pagd_fft_r2c", "pagd_fft_c2r", "pagd_get_state", "pagd_step_static", "pagd_set_trace",
-           "pagd_get_trace", "pagd_last_error", "pagd_destroy")
+           "pagd_get_trace", "pagd_last_error", "pagd_destroy", "pagd_batch_create",
+           "pagd_batch_workspace_size", "pagd_batch_set_workspace", "pagd_batch_run",
+           "pagd_batch_last_error", "pagd_batch_destroy")
 # phase identifiers of the persistent kernel's control machine (for traces)
 PHASES = ("B", "C", "D", "E", "R1", "CI", "RI", "ACCEPT", "FAIL", "FWD_R", "FWD_C", "INV_C", "INV_R",
           "EN_R", "EN_C", "EN_R2", "MASS", "IM_R0", "IM_C0", "IM_R1", "IM_C1", "IM_R2", "START")
@@ -70,6 +72,12 @@ def _declare(lib):
         "pagd_get_trace": [P, IP, D, i, IP],
         "pagd_last_error": [P],
         "pagd_destroy": [P],
+        "pagd_batch_create": [ctypes.POINTER(P), ctypes.POINTER(P), i],
+        "pagd_batch_workspace_size": [P, ctypes.POINTER(ctypes.c_size_t)],
+        "pagd_batch_set_workspace": [P, P, ctypes.c_size_t],
+        "pagd_batch_run": [P, d, i, d, IP, D, IP],
+        "pagd_batch_last_error": [P],
+        "pagd_batch_destroy": [P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -77,6 +85,8 @@ def _declare(lib):
         fn.restype = ctypes.c_int
     lib.pagd_last_error.restype = ctypes.c_char_p
     lib.pagd_destroy.restype = None
+    lib.pagd_batch_last_error.restype = ctypes.c_char_p
+    lib.pagd_batch_destroy.restype = None
     return lib
 
 
@@ -284,6 +294,66 @@ class Solver:
     def close(self):
         if self._h:
             self.lib.pagd_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many Solvers advanced together by one persistent launch per chunk
+    (pagd_batch_* in include/pagd.h).  The members must share the library,
+    precision and stream, and have their states set; they stay usable on
+    their own (get_state, energy, ...) and must outlive the batch."""
+
+    def __init__(self, members):
+        self.members = list(members)
+        self.lib = self.members[0].lib
+        self.emu = self.members[0].emu
+        self._h = ctypes.c_void_p()
+        arr = (ctypes.c_void_p * len(self.members))(*[m._h.value for m in self.members])
+        st = self.lib.pagd_batch_create(ctypes.byref(self._h), arr, len(self.members))
+        if st != 0:
+            raise PagdError(st, "batch_create")
+        nb = ctypes.c_size_t()
+        self._check(self.lib.pagd_batch_workspace_size(self._h, ctypes.byref(nb)), "batch_workspace_size")
+        self.ws_bytes = nb.value
+        if self.emu:
+            self.ws = np.zeros(self.ws_bytes + 256, dtype=np.uint8)
+            base = self.ws.ctypes.data
+        else:
+            import torch
+            self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device="cuda")
+            base = self.ws.data_ptr()
+        ptr = base + ((-base) % 256)
+        self._check(self.lib.pagd_batch_set_workspace(self._h, ctypes.c_void_p(ptr), self.ws_bytes),
+                    "batch_set_workspace")
+
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.lib.pagd_batch_last_error(self._h) if self._h else b""
+            raise PagdError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def run(self, dt, nsteps, tol, check=True):
+        """Advance every member; returns (iters [count, nsteps], resid, status [count])."""
+        cnt = len(self.members)
+        iters = np.zeros((cnt, max(nsteps, 1)), dtype=np.int32)
+        res = np.zeros((cnt, max(nsteps, 1)), dtype=np.float64)
+        status = np.zeros(cnt, dtype=np.int32)
+        st = self.lib.pagd_batch_run(self._h, dt, nsteps, tol,
+                                     iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                     res.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     status.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        if check:
+            self._check(st, "batch_run")
+        return iters[:, :nsteps], res[:, :nsteps], status
+
+    def close(self):
+        if self._h:
+            self.lib.pagd_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):
