@@ -62,7 +62,7 @@ struct pagd_solver {
 
 enum {
     O_SC, O_NORMS, O_SUMS, O_STATS, O_TW64, O_TW32, O_U0, O_U1, O_VB, O_G64, O_VBT, O_LBT, O_DD0,
-    O_DD1, O_SS0, O_SS1, O_C0, O_NB, O_DB, O_CL64, O_NB64, O_DB64, O_MASS, O_TRACE, O_VR64, O_NR64, O_WR64, O_LB64, O_YB, O_END
+    O_DD1, O_SS0, O_SS1, O_C0, O_NB, O_DB, O_CL64, O_NB64, O_DB64, O_MASS, O_TRACE, O_VR64, O_NR64, O_WR64, O_LB64, O_YB, O_X, O_X64, O_END
 };
 
 static pagd_status fail(pagd_solver* s, pagd_status st, const char* msg) {
@@ -78,9 +78,19 @@ static int ilog2(int v) {
     return l;
 }
 
+// rows of the row passes (all points but the last axis) and the half-spectrum
+// size of one field
+static long long rows_of(const pagd_solver* s) { return s->npts / s->n[s->dim - 1]; }
+
+static double cell_volume(const pagd_solver* s) {
+    double h = 1.0;
+    for (int d = 0; d < s->dim; d++) h *= s->L[d] / s->n[d];
+    return h;
+}
+
 static void plan_layout(pagd_solver* s) {
     const long long N = s->npts;
-    const long long H = (long long)s->h1 * s->n[0];
+    const long long H = (long long)s->h1 * rows_of(s);
     const int T = s->tsize;
     size_t sz[O_END];
     sz[O_SC] = sizeof(Scal);
@@ -104,6 +114,8 @@ static void plan_layout(pagd_solver* s) {
     sz[O_WR64] = sizeof(double2) * H;
     sz[O_LB64] = sizeof(double) * N;
     sz[O_YB] = (size_t)T * N;
+    sz[O_X] = s->dim == 3 ? (size_t)2 * T * H * 3 : 0;
+    sz[O_X64] = s->dim == 3 ? sizeof(double2) * H * 3 : 0;
     size_t o = 0;
     for (int i = 0; i < O_END; i++) {
         s->off[i] = o;
@@ -118,18 +130,27 @@ static Params params_for(const pagd_solver* s, char* w) {
     P.model = s->model;
     P.scheme = s->scheme;
     P.precision = s->precision;
+    const int last = s->dim - 1;
     P.n0 = s->n[0];
-    P.n1 = s->n[1];
-    P.logn0 = ilog2(s->n[0]);
-    P.logn1 = ilog2(s->n[1]);
+    P.n1 = s->n[last];
+    P.nm = s->dim == 3 ? s->n[1] : 1;
+    P.logn0 = ilog2(P.n0);
+    P.logn1 = ilog2(P.n1);
+    P.logm = ilog2(P.nm);
     P.h1 = s->h1;
+    P.rows = (int)rows_of(s);
+    P.ncols = s->h1 * P.nm;
+    P.H = (long long)s->h1 * P.rows;
     P.logtw = s->logtw;
     P.npts = s->npts;
+    P.inv_npts = 1.0 / (double)s->npts;
     P.warp_bytes = (long long)s->warp_bytes;
     const double twopi = 6.283185307179586476925286766559;
     P.k0sq = (twopi / s->L[0]) * (twopi / s->L[0]);
-    P.k1sq = (twopi / s->L[1]) * (twopi / s->L[1]);
-    P.cellvol = (s->L[0] / s->n[0]) * (s->L[1] / s->n[1]);
+    P.k1sq = (twopi / s->L[last]) * (twopi / s->L[last]);
+    P.kmsq = s->dim == 3 ? (twopi / s->L[1]) * (twopi / s->L[1]) : 0.0;
+    P.cellvol = 1.0;
+    for (int d = 0; d < s->dim; d++) P.cellvol *= s->L[d] / s->n[d];
     P.eps = s->eps;
     P.eta1 = s->eta1;
     P.eta2 = s->eta2;
@@ -176,6 +197,8 @@ static Params params_for(const pagd_solver* s, char* w) {
     P.WR64 = (double2*)(w + s->off[O_WR64]);
     P.LB64 = (double*)(w + s->off[O_LB64]);
     P.YB = w + s->off[O_YB];
+    P.X = s->dim == 3 ? (void*)(w + s->off[O_X]) : nullptr;
+    P.X64 = s->dim == 3 ? (double2*)(w + s->off[O_X64]) : nullptr;
     P.ref_valid = s->ref_valid;
     P.refresh = kRefreshSteps;
     return P;
@@ -290,14 +313,20 @@ static void make_plan(pagd_solver* s) {
 #else
     const int wpb = kThreads / 32;
 #endif
-    const int units = s->n[0] / 2 > s->h1 ? s->n[0] / 2 : s->h1;
+    const int last = s->dim - 1, nm = s->dim == 3 ? s->n[1] : 1;
+    const long long rows = rows_of(s);
+    long long units = rows / 2;
+    if ((long long)s->h1 * nm > units) units = (long long)s->h1 * nm;
     const int sms = num_sms();
-    s->grid = units < sms ? units : sms;
-    if (s->grid < (units + wpb - 1) / wpb) s->grid = (units + wpb - 1) / wpb;
+    s->grid = units < sms ? (int)units : sms;
+    if ((long long)s->grid < (units + wpb - 1) / wpb) {
+        const long long g = (units + wpb - 1) / wpb;
+        s->grid = (int)(g < 65536 ? g : 65536);  // capped at the co-resident CTAs when launched
+    }
     if (s->grid < 1) s->grid = 1;
-    const int l0 = ilog2(s->n[0]), l1 = ilog2(s->n[1]);
-    s->logtw = l0 > l1 ? l0 : l1;
-    s->warp_bytes = warp_smem_bytes(s->n[0], s->n[1], s->model, s->tsize, fixed_len(s->n[0], s->n[1]));
+    s->logtw = 0;
+    for (int d = 0; d < s->dim; d++) s->logtw = std::max(s->logtw, ilog2(s->n[d]));
+    s->warp_bytes = warp_smem_bytes(s->n[0], s->n[last], s->model, s->tsize, fixed_len(s->n[0], s->n[last]), nm);
     s->smem = tw_smem_bytes(s->logtw) + (size_t)wpb * s->warp_bytes;
 }
 
@@ -322,7 +351,7 @@ static pagd_status init_common(pagd_solver** out, int model, int dim, const int*
                                int precision, const pagd_opts* opts, void* stream) {
     if (!out) return PAGD_EINVAL;
     *out = nullptr;
-    if (dim != 2 || !n || !L) return PAGD_EINVAL;
+    if ((dim != 2 && dim != 3) || !n || !L) return PAGD_EINVAL;
     for (int d = 0; d < dim; d++) {
         if (!pow2_ok(n[d]) || !(L[d] > 0.0) || !std::isfinite(L[d])) return PAGD_EINVAL;
     }
@@ -354,8 +383,8 @@ static pagd_status init_common(pagd_solver** out, int model, int dim, const int*
     s->precision = precision;
     s->opts = o;
     s->stream = stream;
-    s->npts = (long long)s->n[0] * s->n[1];
-    s->h1 = s->n[1] / 2 + 1;
+    s->npts = (long long)s->n[0] * s->n[1] * s->n[2];
+    s->h1 = s->n[dim - 1] / 2 + 1;
     s->nslots = o.max_iter + 16 * 9 + 16;
     s->tsize = precision == PAGD_FP64 ? 8 : 4;
     s->ws = nullptr;
@@ -582,7 +611,7 @@ pagd_status pagd_energy(pagd_solver* s, const double* u_dev, double* E) {
     double r[2];
     pagd_status st = reduce_program(s, PROG_ENERGY, u_dev, r);
     if (st != PAGD_OK) return st;
-    const double h = (s->L[0] / s->n[0]) * (s->L[1] / s->n[1]);
+    const double h = cell_volume(s);
     const double N = (double)s->npts;
     if (s->model == PAGD_PFC) *E = h * (r[0] + r[1] / N);
     else *E = h * r[0] - 0.5 * s->eps * s->eps * s->eta1 * h * r[1] / N;
@@ -595,7 +624,7 @@ pagd_status pagd_mass(pagd_solver* s, const double* u_dev, double* m) {
     double r[2];
     pagd_status st = reduce_program(s, PROG_MASS, u_dev, r);
     if (st != PAGD_OK) return st;
-    *m = r[0] * (s->L[0] / s->n[0]) * (s->L[1] / s->n[1]);
+    *m = r[0] * cell_volume(s);
     return PAGD_OK;
 }
 
@@ -878,10 +907,10 @@ pagd_status pagd_batch_create(pagd_batch** out, pagd_solver* const* members, int
     b->logtw = 0;
     b->warp_bytes = 0;
     for (pagd_solver* s : b->m) {
-        const int l0 = ilog2(s->n[0]), l1 = ilog2(s->n[1]);
-        b->logtw = std::max(b->logtw, std::max(l0, l1));
-        b->warp_bytes = std::max(b->warp_bytes, warp_smem_bytes(s->n[0], s->n[1], s->model, s->tsize,
-                                                                batch_nf(s->n[0], s->n[1])));
+        const int last = s->dim - 1, nm = s->dim == 3 ? s->n[1] : 1;
+        for (int d = 0; d < s->dim; d++) b->logtw = std::max(b->logtw, ilog2(s->n[d]));
+        b->warp_bytes = std::max(b->warp_bytes, warp_smem_bytes(s->n[0], s->n[last], s->model, s->tsize,
+                                                                batch_nf(s->n[0], s->n[last]), nm));
     }
 #ifdef PAGD_EMU
     const int wpb = 1;

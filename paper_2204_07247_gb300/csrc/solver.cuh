@@ -45,6 +45,7 @@ enum Phase {
     PH_B, PH_C, PH_D, PH_E, PH_R1, PH_CI, PH_RI, PH_ACCEPT, PH_FAIL,
     PH_FWD_R, PH_FWD_C, PH_INV_C, PH_INV_R, PH_EN_R, PH_EN_C, PH_EN_R2, PH_MASS,
     PH_IM_R0, PH_IM_C0, PH_IM_R1, PH_IM_C1, PH_IM_R2,
+    PH_MF, PH_MI,
     PH_DONE
 };
 
@@ -72,10 +73,18 @@ struct StepK {
 
 struct Params {
     int model, scheme, precision, prog;
+    // Grid n0 x nm x n1 (2D: nm = 1), n1 the last (fastest) axis.  The row
+    // passes transform lines along the last axis: rows = n0 nm of them.  Their
+    // half spectra are stored [field][k1][row] (H = h1 rows complex values per
+    // field).  In 3D a middle pass transforms along the middle axis and stores
+    // [field][k1][km][i0], so the column passes always see ncols = h1 nm
+    // contiguous lines of length n0: line l = k1 nm + km.
     int n0, n1, logn0, logn1, h1, logtw;
+    int nm, logm, rows, ncols;
+    long long H;
     long long npts;
-    double k0sq, k1sq;   // (2 pi / L0)^2, (2 pi / L1)^2
-    double cellvol;      // h0 h1
+    double k0sq, k1sq, kmsq;  // (2 pi / L)^2 of the first, last and middle axes
+    double cellvol;           // product of the spacings
     double eps, eta1, eta2, tau, M;
     double s;
     int n_eta, accel, max_iter, max_recheck, theta_mode, pad0;
@@ -102,6 +111,9 @@ struct Params {
     double2* CL64;
     double2* NB64;
     double2* DB64;
+    // 3D only: the middle passes' output, input of the column passes
+    void* X;
+    double2* X64;
     // reference point of the incremental (FP32-transform) base evaluation: the
     // FP64 spectra of the last evaluated base VB (VR64: v, NR64: PFC v^3 / FCH
     // F'(v), P(v)), its FP64 Laplacian (LB64, FCH) and the last shift (YB)
@@ -129,6 +141,7 @@ struct Params {
 
 struct Ctl {
     int ph, step, it, ev, lastev, cur, rech, fail, best_ev;
+    int after, mk, m64;  // 3D middle pass: the phase after it, its fields, FP64 buffers
     int acc, acc_cur, acc_it, acc_lastev, acc_ev, reb, ereb, inc, ref_ok, exact_done;
     double resid, base_nrm, best_nrm, acc_resid;
 };
@@ -240,16 +253,31 @@ __device__ __forceinline__ double lam_at(const Params& P, int i) {
     return P.accel ? P.lam[i % P.n_eta] : 0.0;
 }
 
-// kappa = |k|^2 at half-spectrum index (k1 column, k0 row)
-__device__ __forceinline__ double kappa_at(const Params& P, int k1, int k0) {
+// last-axis wavenumber index of column-pass line l (l = k1 nm + km)
+__host__ __device__ __forceinline__ int kl_of(const Params& P, int l) { return l >> P.logm; }
+
+// kappa = |k|^2 at column-pass line l, first-axis index k0
+__device__ __forceinline__ double kappa_at(const Params& P, int l, int k0) {
+    const int k1 = l >> P.logm, km = l & (P.nm - 1);
     const int r0 = (k0 <= (P.n0 >> 1)) ? k0 : k0 - P.n0;
-    return P.k1sq * (double)k1 * (double)k1 + P.k0sq * (double)r0 * (double)r0;
+    const int rm = (km <= (P.nm >> 1)) ? km : km - P.nm;
+    return P.k1sq * (double)k1 * (double)k1 + P.kmsq * (double)rm * (double)rm +
+           P.k0sq * (double)r0 * (double)r0;
 }
 
 // kappa in the iteration precision (FP32 iterations carry no FP64 arithmetic)
-template <class T> __device__ __forceinline__ T kappa_t(const Params& P, int k1, int k0) {
+template <class T> __device__ __forceinline__ T kappa_t(const Params& P, int l, int k0) {
+    const int k1 = l >> P.logm, km = l & (P.nm - 1);
     const int r0 = (k0 <= (P.n0 >> 1)) ? k0 : k0 - P.n0;
-    return (T)P.k1sq * (T)(k1 * k1) + (T)P.k0sq * (T)(r0 * r0);
+    const int rm = (km <= (P.nm >> 1)) ? km : km - P.nm;
+    return (T)P.k1sq * (T)(k1 * k1) + (T)P.kmsq * (T)(rm * rm) + (T)P.k0sq * (T)(r0 * r0);
+}
+
+// index of half-spectrum entry (line l, k0) in the row-major API layout
+// n0 x nm x h1
+__device__ __forceinline__ long long api_spec_index(const Params& P, int l, int k0) {
+    const int k1 = l >> P.logm, km = l & (P.nm - 1);
+    return ((long long)k0 * P.nm + km) * P.h1 + k1;
 }
 
 // double well derivatives, expanded: F'(z) = (z^2 - 1)(z + tau),
@@ -334,7 +362,7 @@ __device__ __forceinline__ WarpCtx warp_ctx(const Params& P, char* smem) {
 }
 
 // Row pass.  src/dst: column-major half spectra, field f, column k, row r at
-// f*h1*n0 + k*n0 + r.  A unit is ru = 2 rows;
+// f*H + k*rows + r.  A unit is ru = 2 rows;
 // real line l = f*ru + rr; lines 2j and 2j+1 are packed as the real and
 // imaginary parts of complex line j.  fn(p, row, x, const TI* in, TO* out).
 template <class TI, class TO, class Fn>
@@ -342,26 +370,27 @@ __device__ void row_pass(const Params& P, const Tw& tw, int kin, int kout, const
                          cx<TO>* dst, char* smem, Fn&& fn) {
     using CI = cx<TI>;
     using CO = cx<TO>;
-    const int n0 = P.n0, n1 = P.n1, h1 = P.h1, logn1 = P.logn1, half = n1 >> 1;
+    const int rows = P.rows, n1 = P.n1, logn1 = P.logn1, half = n1 >> 1;
+    const long long H = P.H;
     const int pitch = pitch_of(n1);
     const int ru = row_unit(kin, kout);
     const WarpCtx w = warp_ctx(P, smem);
     TI* Rin = (TI*)w.mem;
     TO* Rout = (TO*)(w.mem + (size_t)kin * ru * n1 * sizeof(TI));
     char* zb = w.mem + (size_t)kin * ru * n1 * sizeof(TI) + (size_t)kout * ru * n1 * sizeof(TO);
-    const TI iscale = (TI)(1.0 / ((double)n0 * (double)n1));
-    const URange ur = units_of(tw, n0 / ru);
+    const TI iscale = (TI)P.inv_npts;
+    const URange ur = units_of(tw, rows / ru);
     for (int u = ur.b; u < ur.e; u += ur.s) {
         const int r0 = u * ru;
         for (int j = 0; 2 * j < kin * ru; j++) {
             CI* Z0 = (CI*)zb;
             CI* Z1 = Z0 + pitch;
             const int la = 2 * j, lb = 2 * j + 1;
-            const CI* sa = src + (size_t)(la / ru) * h1 * n0 + r0 + (la % ru);
-            const CI* sb = src + (size_t)(lb / ru) * h1 * n0 + r0 + (lb % ru);
+            const CI* sa = src + (size_t)(la / ru) * H + r0 + (la % ru);
+            const CI* sb = src + (size_t)(lb / ru) * H + r0 + (lb % ru);
             for (int x = w.lane; x < n1; x += kWarp) {
                 const int k = (x <= half) ? x : n1 - x;
-                CI A = sa[(size_t)k * n0], B = sb[(size_t)k * n0];
+                CI A = sa[(size_t)k * rows], B = sb[(size_t)k * rows];
                 if (x == 0 || x == half) { A.y = 0; B.y = 0; }
                 Z0[x] = (x <= half) ? CI{A.x - B.y, A.y + B.x} : CI{A.x + B.y, B.x - A.y};
             }
@@ -392,36 +421,37 @@ __device__ void row_pass(const Params& P, const Tw& tw, int kin, int kout, const
                 Z0[x] = CO{Rout[(size_t)la * n1 + x], Rout[(size_t)lb * n1 + x]};
             const int res = fft_line_w<-1, TO>(Z0, Z1, logn1, tw_of<TO>(tw), tw.log, w.lane);
             const CO* Zr = res ? Z1 : Z0;
-            CO* da = dst + (size_t)(la / ru) * h1 * n0 + r0 + (la % ru);
-            CO* db = dst + (size_t)(lb / ru) * h1 * n0 + r0 + (lb % ru);
+            CO* da = dst + (size_t)(la / ru) * H + r0 + (la % ru);
+            CO* db = dst + (size_t)(lb / ru) * H + r0 + (lb % ru);
             const TO hf = (TO)0.5;
             for (int k = w.lane; k <= half; k += kWarp) {
                 const CO zk = Zr[k];
                 const CO zn = Zr[(n1 - k) & (n1 - 1)];
-                da[(size_t)k * n0] = CO{hf * (zk.x + zn.x), hf * (zk.y - zn.y)};
-                db[(size_t)k * n0] = CO{hf * (zk.y + zn.y), hf * (zn.x - zk.x)};
+                da[(size_t)k * rows] = CO{hf * (zk.x + zn.x), hf * (zk.y - zn.y)};
+                db[(size_t)k * rows] = CO{hf * (zk.y + zn.y), hf * (zn.x - zk.x)};
             }
         }
         warp_sync();
     }
 }
 
-// Column pass over half-spectrum columns k1 in [0, h1): one warp per column.
+// Column pass over the ncols contiguous lines of length n0: one warp per line.
 // fn(k1, k0, in, out); outputs may overwrite inputs of the same point.
 template <class T, class Fn>
 __device__ void col_pass(const Params& P, const Tw& tw, int kin, int kout, const cx<T>* src, cx<T>* dst,
                          char* smem, Fn&& fn) {
     using C = cx<T>;
-    const int n0 = P.n0, h1 = P.h1, logn0 = P.logn0;
+    const int n0 = P.n0, ncols = P.ncols, logn0 = P.logn0;
+    const long long H = P.H;
     const int pitch = pitch_of(n0);
     const int nb = (kin > kout ? kin : kout) + 1;
     const WarpCtx w = warp_ctx(P, smem);
-    const URange ur = units_of(tw, h1);
+    const URange ur = units_of(tw, ncols);
     for (int k1 = ur.b; k1 < ur.e; k1 += ur.s) {
         C* buf[kMaxK + 1];
         for (int i = 0; i < nb; i++) buf[i] = (C*)w.mem + (size_t)i * pitch;
         for (int f = 0; f < kin; f++) {
-            const C* s = src + (size_t)f * h1 * n0 + (size_t)k1 * n0;
+            const C* s = src + (size_t)f * H + (size_t)k1 * n0;
             for (int k0 = w.lane; k0 < n0; k0 += kWarp) buf[f][k0] = s[k0];
             const int res = fft_line_w<-1, T>(buf[f], buf[nb - 1], logn0, tw_of<T>(tw), tw.log, w.lane);
             if (res) {
@@ -440,7 +470,7 @@ __device__ void col_pass(const Params& P, const Tw& tw, int kin, int kout, const
         for (int g = 0; g < kout; g++) {
             const int res = fft_line_w<+1, T>(buf[g], buf[nb - 1], logn0, tw_of<T>(tw), tw.log, w.lane);
             const C* r = res ? buf[nb - 1] : buf[g];
-            C* d = dst + (size_t)g * h1 * n0 + (size_t)k1 * n0;
+            C* d = dst + (size_t)g * H + (size_t)k1 * n0;
             for (int k0 = w.lane; k0 < n0; k0 += kWarp) d[k0] = r[k0];
             warp_sync();
         }
@@ -475,18 +505,19 @@ __device__ void row_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
     constexpr int E = NF / kWarp, EH = (H1 + kWarp - 1) / kWarp;
     constexpr int GCH = E < 8 ? E : 8;
     constexpr int NPT = 2 * E, PCH = NPT < kChunk ? NPT : kChunk;
-    const int n0 = P.n0;
+    const int rows = P.rows;
+    const long long Hs = P.H;
     const WarpCtx w = warp_ctx(P, smem);
     CI* X0 = (CI*)w.mem;
     CI* X1 = X0 + (size_t)kin * PITCH;
     CO* Y0 = (CO*)(X1 + (size_t)kin * PITCH);
     CO* Y1 = Y0 + (size_t)kout * PITCH;
-    const TI iscale = (TI)(1.0 / ((double)n0 * (double)NF));
-    const URange ur = units_of(tw, n0 / 2);
+    const TI iscale = (TI)P.inv_npts;
+    const URange ur = units_of(tw, rows / 2);
     for (int u = ur.b; u < ur.e; u += ur.s) {
         const int r0 = 2 * u;
         for (int l = 0; l < kin; l++) {
-            const CI* s0 = src + (size_t)l * H1 * n0 + r0;
+            const CI* s0 = src + (size_t)l * Hs + r0;
 #pragma unroll
             for (int c = 0; c < E; c += GCH) {
                 CI a[GCH], b[GCH];
@@ -494,8 +525,8 @@ __device__ void row_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
                 for (int i = 0; i < GCH; i++) {
                     const int x = w.lane + kWarp * (c + i);
                     const int k = (x <= HALF) ? x : NF - x;
-                    a[i] = s0[(size_t)k * n0];
-                    b[i] = s0[(size_t)k * n0 + 1];
+                    a[i] = s0[(size_t)k * rows];
+                    b[i] = s0[(size_t)k * rows + 1];
                 }
 #pragma unroll
                 for (int i = 0; i < GCH; i++) {
@@ -547,7 +578,7 @@ __device__ void row_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
                 fft_lines_fixed<-1, TO, LOGN, kMaxK>(Y0, Y1, PITCH, kout, tw_of<TO>(tw), tw.log, w.lane) ? Y1 : Y0;
             const TO hf = (TO)0.5;
             for (int g = 0; g < kout; g++) {
-                CO* d0 = dst + (size_t)g * H1 * n0 + r0;
+                CO* d0 = dst + (size_t)g * Hs + r0;
                 const CO* zl = Yr + (size_t)g * PITCH;
 #pragma unroll
                 for (int i = 0; i < EH; i++) {
@@ -555,8 +586,8 @@ __device__ void row_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
                     if (k <= HALF) {
                         const CO zk = zl[k];
                         const CO zn = zl[(NF - k) & (NF - 1)];
-                        d0[(size_t)k * n0] = CO{hf * (zk.x + zn.x), hf * (zk.y - zn.y)};
-                        d0[(size_t)k * n0 + 1] = CO{hf * (zk.y + zn.y), hf * (zn.x - zk.x)};
+                        d0[(size_t)k * rows] = CO{hf * (zk.x + zn.x), hf * (zk.y - zn.y)};
+                        d0[(size_t)k * rows + 1] = CO{hf * (zk.y + zn.y), hf * (zn.x - zk.x)};
                     }
                 }
             }
@@ -573,15 +604,16 @@ __device__ void col_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
     constexpr int LOGN = ilog2c(NF), PITCH = NF + 2, E = NF / kWarp;
     constexpr int GCH = E < 8 ? E : 8;
     constexpr int PCH = E < kChunk ? E : kChunk;
-    const int h1 = P.h1;
+    const int ncols = P.ncols;
+    const long long Hs = P.H;
     const int kl = kin > kout ? kin : kout;
     const WarpCtx w = warp_ctx(P, smem);
     C* B0 = (C*)w.mem;
     C* B1 = B0 + (size_t)kl * PITCH;
-    const URange ur = units_of(tw, h1);
+    const URange ur = units_of(tw, ncols);
     for (int k1 = ur.b; k1 < ur.e; k1 += ur.s) {
         for (int f = 0; f < kin; f++) {
-            const C* s = src + (size_t)f * h1 * NF + (size_t)k1 * NF;
+            const C* s = src + (size_t)f * Hs + (size_t)k1 * NF;
 #pragma unroll
             for (int c = 0; c < E; c += GCH) {
                 C v[GCH];
@@ -622,13 +654,84 @@ __device__ void col_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
             const int r = fft_lines_fixed<+1, T, LOGN, kMaxK>(Xo, scratch, PITCH, kout, tw_of<T>(tw), tw.log, w.lane);
             const C* Yr = r ? scratch : Xo;
             for (int g = 0; g < kout; g++) {
-                C* d = dst + (size_t)g * h1 * NF + (size_t)k1 * NF;
+                C* d = dst + (size_t)g * Hs + (size_t)k1 * NF;
 #pragma unroll
                 for (int i = 0; i < E; i++) d[w.lane + kWarp * i] = Yr[(size_t)g * PITCH + w.lane + kWarp * i];
             }
         }
         warp_sync();
     }
+}
+
+// ------------------------------------------------------- middle axis (3D)
+//
+// S = -1: forward along the middle axis, [f][k1][i0 nm + i1] -> [f][k1][km][i0];
+// S = +1: inverse, [f][k1][km][i0] -> [f][k1][i0 nm + i1] (no scaling: the
+// row passes apply 1/n_pts).  A unit is kMidG consecutive i0 of one k1 plane:
+// its kMidG lines are contiguous on the row side, and on the transposed side
+// every km holds kMidG neighbouring values.
+constexpr int kMidG = 2;
+
+__host__ __device__ __forceinline__ size_t mid_warp_smem(int nm, int sz) {
+    return (size_t)2 * kMidG * pitch_of(nm) * 2 * sz;
+}
+__host__ __device__ __forceinline__ int mid_units(const Params& P) { return P.h1 * (P.n0 / kMidG); }
+
+template <class T, int S>
+__device__ void mid_pass(const Params& P, const Tw& tw, int k, const cx<T>* src, cx<T>* dst, char* smem) {
+    using C = cx<T>;
+    const int nm = P.nm, logm = P.logm, n0 = P.n0, rows = P.rows, gpp = P.n0 / kMidG;
+    const long long H = P.H;
+    const int pitch = pitch_of(nm);
+    const WarpCtx w = warp_ctx(P, smem);
+    C* B0 = (C*)w.mem;
+    C* B1 = B0 + (size_t)kMidG * pitch;
+    const URange ur = units_of(tw, P.h1 * gpp);
+    for (int u = ur.b; u < ur.e; u += ur.s) {
+        const int k1 = u / gpp, i0 = (u - k1 * gpp) * kMidG;
+        for (int f = 0; f < k; f++) {
+            const C* sf = src + (size_t)f * H;
+            C* df = dst + (size_t)f * H;
+            const size_t rowbase = (size_t)k1 * rows + (size_t)i0 * nm;    // [k1][i0][i1]
+            const size_t colbase = (size_t)k1 * nm * n0 + (size_t)i0;      // [k1][km][i0]
+            for (int j = w.lane; j < kMidG * nm; j += kWarp) {
+                if (S < 0) {
+                    const int g = j >> logm, i1 = j & (nm - 1);
+                    B0[g * pitch + i1] = sf[rowbase + j];
+                } else {
+                    const int km = j / kMidG, g = j - km * kMidG;
+                    B0[g * pitch + km] = sf[colbase + (size_t)km * n0 + g];
+                }
+            }
+            int r = 0;
+            for (int g = 0; g < kMidG; g++)
+                r = fft_line_w<S, T>(B0 + g * pitch, B1 + g * pitch, logm, tw_of<T>(tw), tw.log, w.lane);
+            const C* Br = r ? B1 : B0;
+            for (int j = w.lane; j < kMidG * nm; j += kWarp) {
+                if (S < 0) {
+                    const int km = j / kMidG, g = j - km * kMidG;
+                    df[colbase + (size_t)km * n0 + g] = Br[g * pitch + km];
+                } else {
+                    const int g = j >> logm, i1 = j & (nm - 1);
+                    df[rowbase + j] = Br[g * pitch + i1];
+                }
+            }
+            warp_sync();
+        }
+    }
+}
+
+// Column passes read the last row pass's output and write the next row pass's
+// input: in 2D NB -> DB directly; in 3D the middle passes sit between, so the
+// column passes read X (forward middle output) and write NB (inverse middle
+// input), and the inverse middle pass writes DB.
+__device__ __forceinline__ const double2* csrc64(const Params& P) { return P.nm > 1 ? P.X64 : P.NB64; }
+__device__ __forceinline__ double2* cdst64(const Params& P) { return P.nm > 1 ? P.NB64 : P.DB64; }
+template <class T> __device__ __forceinline__ const cx<T>* csrcT(const Params& P) {
+    return (const cx<T>*)(P.nm > 1 ? P.X : P.NB);
+}
+template <class T> __device__ __forceinline__ cx<T>* cdstT(const Params& P) {
+    return (cx<T>*)(P.nm > 1 ? P.NB : P.DB);
 }
 
 // dispatch: NF = 0 runs the runtime-length passes
@@ -842,7 +945,7 @@ __device__ void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem)
     const double iM = 1.0 / P.M;
     const double e4 = P.eps * P.eps * P.eps * P.eps;
     if (P.model == M_PFC) {
-        colp<double, NF>(P, tw, kb, 1, P.NB64, P.DB64, smem, [&](int, int) { return Nil{}; },
+        colp<double, NF>(P, tw, kb, 1, csrc64(P), cdst64(P), smem, [&](int, int) { return Nil{}; },
                          [&](int k1, int k0, const Nil&, const double2* in, double2* out) {
                              const double kap = kappa_at(P, k1, k0);
                              const double2 v = in[0], g = in[1], nl = in[2];
@@ -861,7 +964,7 @@ __device__ void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem)
                              out[0] = d;
                          });
     } else {
-        colp<double, NF>(P, tw, kb, 1, P.NB64, P.DB64, smem, [&](int, int) { return Nil{}; },
+        colp<double, NF>(P, tw, kb, 1, csrc64(P), cdst64(P), smem, [&](int, int) { return Nil{}; },
                          [&](int k1, int k0, const Nil&, const double2* in, double2* out) {
                              const double kap = kappa_at(P, k1, k0);
                              const double2 v = in[0], g = in[1];
@@ -903,13 +1006,13 @@ __device__ void phase_E(const Params& P, const Ctl& c, const Tw& tw, char* smem)
     const Beta B = betas(P, k, c.step);
     const double e2 = P.eps * P.eps;
     const double l1 = lam_at(P, 1);
-    colp<double, NF>(P, tw, 2, 2, P.NB64, P.DB64, smem,
+    colp<double, NF>(P, tw, 2, 2, csrc64(P), cdst64(P), smem,
                      [&](int k1, int k0) { return P.CL64[(long long)k1 * P.n0 + k0]; },
                      [&](int k1, int k0, const double2& lin, const double2* in, double2* out) {
                          const double kap = kappa_at(P, k1, k0);
                          const long long idx = (long long)k1 * P.n0 + k0;
                          P.NR64[idx] = in[0];
-                         P.NR64[idx + (long long)P.h1 * P.n0] = in[1];
+                         P.NR64[idx + P.H] = in[1];
                          double2 G{0.0, 0.0};
                          if (kap != 0.0) {
                              G.x = lin.x + e2 * kap * in[0].x + in[1].x;
@@ -944,7 +1047,7 @@ __device__ void phase_CN(const Params& P, const Ctl& c, const Tw& tw, char* smem
     const bool pfc = P.model == M_PFC;
     struct St { double2 v, n, w; };
     colp<T, NF>(
-        P, tw, kin, 1, (const C*)P.NB, (C*)P.DB, smem,
+        P, tw, kin, 1, csrcT<T>(P), cdstT<T>(P), smem,
         [&](int k1, int k0) {
             const long long idx = (long long)k1 * P.n0 + k0;
             return St{P.VR64[idx], pfc ? P.NR64[idx] : double2{0.0, 0.0}, P.WR64[idx]};
@@ -1022,10 +1125,10 @@ __device__ void phase_EN(const Params& P, const Ctl& c, const Tw& tw, char* smem
     const Beta B = betas(P, k, c.step);
     const double e2 = P.eps * P.eps;
     const double l1 = lam_at(P, 1);
-    const long long H = (long long)P.h1 * P.n0;
+    const long long H = P.H;
     struct St { double2 lin, f1, pp; };
     colp<T, NF>(
-        P, tw, 2, 2, (const C*)P.NB, (C*)P.DB, smem,
+        P, tw, 2, 2, csrcT<T>(P), cdstT<T>(P), smem,
         [&](int k1, int k0) {
             const long long idx = (long long)k1 * P.n0 + k0;
             return St{P.CL64[idx], P.NR64[idx], P.NR64[idx + H]};
@@ -1127,7 +1230,7 @@ __device__ void phase_CI(const Params& P, const Ctl& c, const Tw& tw, char* smem
     const T aim = (T)(k.Ai / P.M), c0 = (T)(1.0 - P.eps), e2 = (T)(P.eps * P.eps), e4 = e2 * e2;
     struct St { C sc, sp, g0; };
     colp<T, NF>(
-        P, tw, K, K, (const C*)P.NB, (C*)P.DB, smem,
+        P, tw, K, K, csrcT<T>(P), cdstT<T>(P), smem,
         [&](int k1, int k0) {
             const long long idx = (long long)k1 * P.n0 + k0;
             return St{scur[idx], sprev[idx], C0[idx]};
@@ -1217,15 +1320,15 @@ __device__ void phase_fwd_r(const Params& P, const Tw& tw, char* smem) {
 }
 template <int NF>
 __device__ void phase_fwd_c(const Params& P, const Tw& tw, char* smem) {
-    colp<double, NF>(P, tw, 1, 0, P.NB64, (double2*)nullptr, smem, [&](int, int) { return Nil{}; },
+    colp<double, NF>(P, tw, 1, 0, csrc64(P), (double2*)nullptr, smem, [&](int, int) { return Nil{}; },
                      [&](int k1, int k0, const Nil&, const double2* in, double2*) {
-                         P.out_spec[(long long)k0 * P.h1 + k1] = in[0];
+                         P.out_spec[api_spec_index(P, k1, k0)] = in[0];
                      });
 }
 template <int NF>
 __device__ void phase_inv_c(const Params& P, const Tw& tw, char* smem) {
-    colp<double, NF>(P, tw, 0, 1, (const double2*)nullptr, P.DB64, smem,
-                     [&](int k1, int k0) { return P.in_spec[(long long)k0 * P.h1 + k1]; },
+    colp<double, NF>(P, tw, 0, 1, (const double2*)nullptr, cdst64(P), smem,
+                     [&](int k1, int k0) { return P.in_spec[api_spec_index(P, k1, k0)]; },
                      [&](int, int, const double2& v, const double2*, double2* out) { out[0] = v; });
 }
 template <int NF>
@@ -1259,10 +1362,11 @@ __device__ void phase_en_c(const Params& P, const Tw& tw, char* smem, double* re
     double acc = 0.0;
     const bool pfc = P.model == M_PFC;
     const int half = P.n1 >> 1;
-    colp<double, NF>(P, tw, 1, pfc ? 0 : 1, P.NB64, P.DB64, smem, [&](int, int) { return Nil{}; },
+    colp<double, NF>(P, tw, 1, pfc ? 0 : 1, csrc64(P), cdst64(P), smem, [&](int, int) { return Nil{}; },
                      [&](int k1, int k0, const Nil&, const double2* in, double2* out) {
                          const double kap = kappa_at(P, k1, k0);
-                         const double w = (k1 == 0 || k1 == half) ? 1.0 : 2.0;
+                         const int kl = kl_of(P, k1);
+                         const double w = (kl == 0 || kl == half) ? 1.0 : 2.0;
                          const double a2 = in[0].x * in[0].x + in[0].y * in[0].y;
                          if (pfc) {
                              acc += w * (-kap + 0.5 * kap * kap) * a2;
@@ -1349,18 +1453,18 @@ template <int NF>
 __device__ void phase_im_c0(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     const StepK& k = step_coeffs(P, c.step);
     if (P.model == M_PFC) {
-        colp<double, NF>(P, tw, 3, 1, P.NB64, P.DB64, smem, [&](int, int) { return Nil{}; },
+        colp<double, NF>(P, tw, 3, 1, csrc64(P), cdst64(P), smem, [&](int, int) { return Nil{}; },
                          [&](int k1, int k0, const Nil&, const double2* in, double2* out) {
                              const double kap = kappa_at(P, k1, k0);
                              out[0] = imex_solve(P, k, kap, in[0], in[1], in[2]);
                          });
     } else {
-        colp<double, NF>(P, tw, 3, 1, P.NB64, P.DB64, smem, [&](int, int) { return Nil{}; },
+        colp<double, NF>(P, tw, 3, 1, csrc64(P), cdst64(P), smem, [&](int, int) { return Nil{}; },
                          [&](int k1, int k0, const Nil&, const double2* in, double2* out) {
                              const double kap = kappa_at(P, k1, k0);
                              const long long idx = (long long)k1 * P.n0 + k0;
                              P.CL64[idx] = in[1];
-                             P.CL64[idx + (long long)P.h1 * P.n0] = in[2];
+                             P.CL64[idx + P.H] = in[2];
                              out[0] = double2{-kap * in[0].x, -kap * in[0].y};
                          });
     }
@@ -1383,10 +1487,10 @@ __device__ void phase_im_c1(const Params& P, const Ctl& c, const Tw& tw, char* s
     const StepK& k = step_coeffs(P, c.step);
     const double e2 = P.eps * P.eps;
     struct St { double2 un, um; };
-    colp<double, NF>(P, tw, 2, 1, P.NB64, P.DB64, smem,
+    colp<double, NF>(P, tw, 2, 1, csrc64(P), cdst64(P), smem,
                      [&](int k1, int k0) {
                          const long long idx = (long long)k1 * P.n0 + k0;
-                         return St{P.CL64[idx], P.CL64[idx + (long long)P.h1 * P.n0]};
+                         return St{P.CL64[idx], P.CL64[idx + P.H]};
                      },
                      [&](int k1, int k0, const St& s, const double2* in, double2* out) {
                          const double kap = kappa_at(P, k1, k0);
@@ -1434,6 +1538,7 @@ __host__ __device__ inline Ctl ctl_init(const Params& P) {
     c.ref_ok = P.ref_valid;
     c.exact_done = 0;
     c.ereb = 0;
+    c.after = PH_DONE; c.mk = 0; c.m64 = 1;
     c.inc = inc_eval(P, c.ref_ok, P.step0, 1);
     c.resid = 0.0; c.base_nrm = 0.0; c.best_nrm = 0.0; c.acc_resid = 0.0;
     switch (P.prog) {
@@ -1447,11 +1552,72 @@ __host__ __device__ inline Ctl ctl_init(const Params& P) {
     return c;
 }
 
+// phases by pass type, for the 3D middle passes and the batched schedule
+__host__ __device__ inline bool phase_is_col(int ph) {
+    return ph == PH_C || ph == PH_E || ph == PH_CI || ph == PH_IM_C0 || ph == PH_IM_C1 || ph == PH_FWD_C ||
+           ph == PH_INV_C || ph == PH_EN_C;
+}
+__host__ __device__ inline bool phase_is_mid(int ph) { return ph == PH_MF || ph == PH_MI; }
+// row passes that read a half spectrum written by the column pass before them
+__host__ __device__ inline bool row_reads_spectrum(int ph) {
+    return ph == PH_D || ph == PH_R1 || ph == PH_RI || ph == PH_INV_R || ph == PH_EN_R2 || ph == PH_IM_R1 ||
+           ph == PH_IM_R2;
+}
+
+// 3D: put a middle pass between a row pass and the column pass after it (MF)
+// and between a column pass and a row pass that reads its output (MI).  pph,
+// pinc, preb: the phase that just ran and its incremental / rebase flags,
+// which fix the number of spectral fields it wrote and their buffer set.
+__host__ __device__ inline void mid_insert(const Params& P, int pph, int pinc, int preb, Ctl& c) {
+    const int nx = c.ph;
+    const int K = k_iter(P.model), kb = k_base(P.model);
+    int k = 0, m64 = 1, ph = -1;
+    if (!phase_is_col(pph) && !phase_is_mid(pph) && phase_is_col(nx)) {
+        ph = PH_MF;
+        switch (pph) {
+            case PH_B: k = (pinc && preb) ? kb - 1 : kb; m64 = !pinc; break;
+            case PH_D: k = 2; m64 = !pinc; break;
+            case PH_R1:
+            case PH_RI: k = K; m64 = 0; break;
+            case PH_IM_R0: k = 3; break;
+            case PH_IM_R1: k = 2; break;
+            default: k = 1; break;  // FWD_R, EN_R
+        }
+    } else if (phase_is_col(pph) && row_reads_spectrum(nx)) {
+        ph = PH_MI;
+        switch (pph) {
+            case PH_C: k = 1; m64 = !pinc; break;
+            case PH_E: k = 2; m64 = !pinc; break;
+            case PH_CI: k = K; m64 = 0; break;
+            default: k = 1; break;  // INV_C, EN_C, IM_C0, IM_C1
+        }
+    }
+    if (ph < 0) return;
+    c.after = nx;
+    c.ph = ph;
+    c.mk = k;
+    c.m64 = m64;
+}
+
+template <class T>
+__device__ void ctl_step(const Params& P, Ctl& c);
+
 // Decide the next phase.  Runs identically in every thread of every CTA after a
 // grid barrier; only device-global values that were final before the barrier
 // are read.
 template <class T>
 __device__ void ctl_advance(const Params& P, Ctl& c) {
+    if (phase_is_mid(c.ph)) {
+        c.ph = c.after;
+        return;
+    }
+    const int pph = c.ph, pinc = c.inc, preb = c.reb;
+    ctl_step<T>(P, c);
+    if (P.nm > 1) mid_insert(P, pph, pinc, preb, c);
+}
+
+template <class T>
+__device__ void ctl_step(const Params& P, Ctl& c) {
     const bool t64 = sizeof(T) == 8;
     const int bank = c.step & 1;
     switch (c.ph) {
@@ -1488,7 +1654,12 @@ __device__ void ctl_advance(const Params& P, Ctl& c) {
             if (c.ph == PH_R1 || nrm < c.best_nrm) { c.best_nrm = nrm; c.best_ev = c.ev; }
             if (c.ph == PH_R1) c.base_nrm = nrm;
             const bool fp32_norm = P.precision == P_MIXED && !t64 && c.ph == PH_RI;
-            if (nrm <= P.tol && !fp32_norm) {
+            // Only an exact FP64 evaluation certifies a step.  An incremental
+            // base evaluation (T transforms of the shift from the reference
+            // point) errs by about 1e-7 of that shift, so when its norm reaches
+            // tol the base moves there and is evaluated exactly.
+            const bool inc_norm = c.ph == PH_R1 && c.inc;
+            if (nrm <= P.tol && !fp32_norm && !inc_norm) {
                 if (c.step + 1 < P.nsteps) {
                     // accepted inside the next step's phase B
                     c.acc = 1;
@@ -1508,12 +1679,15 @@ __device__ void ctl_advance(const Params& P, Ctl& c) {
             } else if (c.ev >= P.max_iter || c.ev + 1 >= P.nslots) {
                 c.fail = ST_ENOCONV;
                 c.ph = PH_FAIL;
-            } else if (fp32_norm && (nrm <= P.tol || nrm <= kRebaseRatio * c.base_nrm ||
-                                     c.ev - c.best_ev >= kStagnation)) {
+            } else if ((fp32_norm && (nrm <= P.tol || nrm <= kRebaseRatio * c.base_nrm ||
+                                      c.ev - c.best_ev >= kStagnation)) ||
+                       (inc_norm && nrm <= P.tol)) {
                 if (c.rech >= P.max_recheck) { c.fail = ST_ENOCONV; c.ph = PH_FAIL; break; }
                 c.rech++;
                 c.reb = 1;
-                c.inc = c.exact_done ? inc_eval(P, c.ref_ok, P.step0 + c.step, 0) : 0;
+                // a rebase that may accept is evaluated exactly; one that only
+                // moves the base past the FP32 floor may be incremental
+                c.inc = (nrm <= P.tol || !c.exact_done) ? 0 : inc_eval(P, c.ref_ok, P.step0 + c.step, 0);
                 c.ph = PH_B;
             } else {
                 c.ph = PH_CI;
@@ -1574,6 +1748,14 @@ __device__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* sm
         case PH_EN_C: phase_en_c<NF>(P, tw, smem, red); break;
         case PH_EN_R2: phase_en_r2<NF>(P, tw, smem, red); break;
         case PH_MASS: phase_mass(P, tw, red); break;
+        case PH_MF:
+            if (c.m64) mid_pass<double, -1>(P, tw, c.mk, P.NB64, P.X64, smem);
+            else mid_pass<T, -1>(P, tw, c.mk, (const cx<T>*)P.NB, (cx<T>*)P.X, smem);
+            break;
+        case PH_MI:
+            if (c.m64) mid_pass<double, +1>(P, tw, c.mk, P.NB64, P.DB64, smem);
+            else mid_pass<T, +1>(P, tw, c.mk, (const cx<T>*)P.NB, (cx<T>*)P.DB, smem);
+            break;
         case PH_IM_R0: phase_im_r0<NF>(P, c, tw, smem); break;
         case PH_IM_C0: phase_im_c0<NF>(P, c, tw, smem); break;
         case PH_IM_R1: phase_im_r1<NF>(P, tw, smem); break;
@@ -1584,10 +1766,11 @@ __device__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* sm
 }
 
 // shared memory per warp needed by any phase (bytes, 16-byte multiple);
-// nf = 0: runtime-length passes, else the fixed-length ones
-inline size_t warp_smem_bytes(int n0, int n1, int model, int tsize, int nf) {
+// nf = 0: runtime-length passes, else the fixed-length ones; nm: middle axis
+inline size_t warp_smem_bytes(int n0, int n1, int model, int tsize, int nf, int nm = 1) {
     size_t m = 0;
     auto upd = [&](size_t v) { if (v > m) m = v; };
+    if (nm > 1) upd(mid_warp_smem(nm, 16));  // middle passes (3D), FP64 worst case
     const int ki = k_iter(model);
     if (nf == 0) {
         upd(row_warp_smem(n1, 0, 8, 3, 8));            // B (PFC: 3 fields) / IMEX R0
@@ -1639,12 +1822,14 @@ struct BatchParams {
     const float2* tw32;
 };
 
-// phases whose units are half-spectrum columns; all others use row pairs
-__host__ __device__ inline bool phase_is_col(int ph) {
-    return ph == PH_C || ph == PH_E || ph == PH_CI || ph == PH_IM_C0 || ph == PH_IM_C1;
+// work units of a phase and the points one unit touches: column lines, middle
+// groups, or row pairs (also for the pointwise phases)
+__host__ __device__ inline int phase_units(const Params& P, int ph) {
+    return phase_is_col(ph) ? P.ncols : phase_is_mid(ph) ? mid_units(P) : P.rows / 2;
 }
-__host__ __device__ inline int phase_units(const Params& P, int ph) { return phase_is_col(ph) ? P.h1 : P.n0 / 2; }
-__host__ __device__ inline int unit_cost(const Params& P, int ph) { return phase_is_col(ph) ? P.n0 : 2 * P.n1; }
+__host__ __device__ inline int unit_cost(const Params& P, int ph) {
+    return phase_is_col(ph) ? P.n0 : phase_is_mid(ph) ? kMidG * P.nm : 2 * P.n1;
+}
 
 // the fixed line lengths compiled into the batched kernel (others: runtime length)
 __host__ __device__ inline int batch_nf(int n0, int n1) {

@@ -88,7 +88,14 @@ FCH256 = Workload("fch2d_256_bdf2_fp32mixed", "fch", (256, 256), (FOURPI, FOURPI
                   eta1=0.1, eta2=0.1, tau=0.0, scheme="bdf2", precision="fp32_mixed", dt=1e-3,
                   steps=1000, tol=1e-8, mean=-0.3, amp=0.05)
 
-WORKLOADS = {w.name: w for w in (PFC64, FCH256)}
+# PFC 3D 256^3 on [0, 64 pi]^3, eps = 0.3, u0 = -0.25 + 0.1 U(-1,1), BDF2,
+# dt = 0.5, 200 steps, FP32 iterations with FP64 norms, tol 1e-8; two seeds
+# advanced together as one batch.
+PFC3D256 = Workload("pfc3d_256_bdf2_fp32mixed", "pfc", (256, 256, 256), (64 * math.pi,) * 3, eps=0.3,
+                    scheme="bdf2", precision="fp32_mixed", dt=0.5, steps=200, tol=1e-8, mean=-0.25,
+                    amp=0.1, seeds=(1, 2))
+
+WORKLOADS = {w.name: w for w in (PFC64, FCH256, PFC3D256)}
 
 
 @dataclass

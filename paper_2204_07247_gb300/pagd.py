@@ -33,7 +33,8 @@ EXPORTS = ("pagd_default_opts", "pfc_init", "fch_init", "pagd_workspace_size", "
            "pagd_batch_last_error", "pagd_batch_destroy")
 # phase identifiers of the persistent kernel's control machine (for traces)
 PHASES = ("B", "C", "D", "E", "R1", "CI", "RI", "ACCEPT", "FAIL", "FWD_R", "FWD_C", "INV_C", "INV_R",
-          "EN_R", "EN_C", "EN_R2", "MASS", "IM_R0", "IM_C0", "IM_R1", "IM_C1", "IM_R2", "START")
+          "EN_R", "EN_C", "EN_R2", "MASS", "IM_R0", "IM_C0", "IM_R1", "IM_C1", "IM_R2", "MF", "MI",
+          "START")
 
 
 class PagdError(RuntimeError):
