@@ -821,6 +821,10 @@ static pagd_status bfail(pagd_batch* b, pagd_status st, const char* msg) {
 static size_t batch_off_params() { return (sizeof(Scal) + 255) & ~(size_t)255; }
 
 #ifdef PAGD_EMU
+constexpr int kEmuBatchWarps = 3;  // warps per emulated CTA in batched launches
+#endif
+
+#ifdef PAGD_EMU
 template <class T> static void batch_exec_host(const Params& P, const Ctl& c, const Tw& t, char* wsm, double* red) {
     switch (batch_nf(P.n0, P.n1)) {
         case 128: exec_phase<T, 128>(P, c, t, wsm, red); break;
@@ -829,13 +833,15 @@ template <class T> static void batch_exec_host(const Params& P, const Ctl& c, co
         default: exec_phase<T, 0>(P, c, t, wsm, red); break;
     }
 }
-// the batched kernel's schedule, one CTA (of one thread) after the other
+// the batched kernel's schedule, one CTA after the other and within a CTA one
+// warp (of one thread) after the other, kEmuBatchWarps warps per CTA so that
+// warps which own nothing of an instance their CTA works on are exercised
 template <class T> static pagd_status batch_launch(pagd_batch* b, const BatchParams& B) {
     std::vector<char> sm(b->smem + 64);
     char* base = (char*)(((uintptr_t)sm.data() + 15) & ~(uintptr_t)15);
     double red[32];
     gridDim.x = (unsigned)b->grid;
-    blockDim.x = 1;
+    blockDim.x = kEmuBatchWarps;
     threadIdx.x = 0;
     const int ntw = 1 << B.logtw;
     double2* t64 = (double2*)base;
@@ -848,7 +854,8 @@ template <class T> static pagd_status batch_launch(pagd_batch* b, const BatchPar
     std::vector<Ctl> ctl(B.count);
     std::vector<long long> G(B.count + 1);
     for (int i = 0; i < B.count; i++) ctl[i] = ctl_init(B.PI[i]);
-    const long long nw = b->grid;
+    const int wpb = kEmuBatchWarps;
+    const long long nw = (long long)b->grid * wpb;
     for (;;) {
         G[0] = 0;
         for (int i = 0; i < B.count; i++)
@@ -859,14 +866,19 @@ template <class T> static pagd_status batch_launch(pagd_batch* b, const BatchPar
         if (total == 0) break;
         for (int blk = 0; blk < b->grid; blk++) {
             blockIdx.x = (unsigned)blk;
-            const long long clo = cost_start(blk, total, nw), chi = cost_start(blk + 1, total, nw);
+            const long long clo = cost_start((long long)blk * wpb, total, nw);
+            const long long chi = cost_start((long long)(blk + 1) * wpb, total, nw);
             for (int i = 0; i < B.count; i++) {
                 if (G[i + 1] <= clo || G[i] >= chi || G[i + 1] == G[i]) continue;
                 const Params& P = B.PI[i];
-                Tw t{t64, t32, B.logtw, 0, 0, 0, 0};
-                batch_split(t, blk, nw, total, G[i], G[i + 1] - G[i], phase_units(P, ctl[i].ph),
-                            unit_cost(P, ctl[i].ph));
-                batch_exec_host<T>(P, ctl[i], t, wsm, red);
+                for (int wi = 0; wi < wpb; wi++) {
+                    threadIdx.x = (unsigned)wi;
+                    Tw t{t64, t32, B.logtw, 0, 0, 0, 0};
+                    batch_split(t, (long long)blk * wpb + wi, nw, total, G[i], G[i + 1] - G[i],
+                                phase_units(P, ctl[i].ph), unit_cost(P, ctl[i].ph));
+                    batch_exec_host<T>(P, ctl[i], t, wsm, red);
+                }
+                threadIdx.x = 0;
             }
         }
         for (int i = 0; i < B.count; i++)
@@ -913,7 +925,7 @@ pagd_status pagd_batch_create(pagd_batch** out, pagd_solver* const* members, int
                                                                 batch_nf(s->n[0], s->n[last]), nm));
     }
 #ifdef PAGD_EMU
-    const int wpb = 1;
+    const int wpb = kEmuBatchWarps;
 #else
     const int wpb = kThreads / 32;
 #endif

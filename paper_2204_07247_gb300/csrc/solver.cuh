@@ -293,6 +293,17 @@ __device__ __forceinline__ double Fwell(double z, double tau) {
 
 __device__ __forceinline__ double nanmax(double a, double b) { return (b > a || b != b) ? b : a; }
 
+// The thread that publishes a block reduction.  The emulation runs the warps
+// of a CTA one after another, each reduction returning that warp's own
+// partial, so there every warp publishes its partial.
+__device__ __forceinline__ bool red_leader() {
+#ifdef PAGD_EMU
+    return true;
+#else
+    return threadIdx.x == 0;
+#endif
+}
+
 // block-wide reductions; the result is valid in thread 0.  All threads call.
 __device__ __forceinline__ double block_max(double v, double* red) {
 #ifdef PAGD_EMU
@@ -897,15 +908,15 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
         });
     if (!reb) {
         s0 = block_sum(s0, red);
-        if (threadIdx.x == 0) atomicAdd(&P.sc->beta_sum[bank][0], s0);
+        if (red_leader()) atomicAdd(&P.sc->beta_sum[bank][0], s0);
         if (!pfc) {
             s2 = block_sum(s2, red);
-            if (threadIdx.x == 0) atomicAdd(&P.sc->beta_sum[bank][1], s2);
+            if (red_leader()) atomicAdd(&P.sc->beta_sum[bank][1], s2);
         }
     }
     if (acc) {
         dmass = block_sum(dmass, red);
-        if (threadIdx.x == 0) atomicAdd(&P.mass[1], dmass);
+        if (red_leader()) atomicAdd(&P.mass[1], dmass);
     }
 }
 
@@ -1205,9 +1216,9 @@ __device__ void phase_R(const Params& P, const Ctl& c, const Tw& tw, char* smem,
             }
         });
     const double amx = block_max((double)amax, red);
-    if (threadIdx.x == 0) atomicMax(&P.norms[(size_t)bank * P.nslots + c.ev], dbl_bits(amx));
+    if (red_leader()) atomicMax(&P.norms[(size_t)bank * P.nslots + c.ev], dbl_bits(amx));
     asum = block_sum(asum, red);
-    if (threadIdx.x == 0) atomicAdd(&P.sums[(size_t)bank * P.nslots + c.ev], asum);
+    if (red_leader()) atomicAdd(&P.sums[(size_t)bank * P.nslots + c.ev], asum);
 }
 
 // Iteration column pass: ybar_hat, spectral residual (Eq. obj:G' with the
@@ -1291,7 +1302,7 @@ __device__ void phase_accept(const Params& P, const Ctl& c, const Tw& tw, double
         if (P.out_real) P.out_real[p] = x;
     }
     dmass = block_sum(dmass, red);
-    if (threadIdx.x == 0) atomicAdd(&P.mass[1], dmass);
+    if (red_leader()) atomicAdd(&P.mass[1], dmass);
     if (leader(tw)) {
         P.stats[c.step].iters = c.ev;
         P.stats[c.step].status = ST_OK;
@@ -1354,7 +1365,7 @@ __device__ void phase_en_r(const Params& P, const Tw& tw, char* smem, double* re
                              });
     if (pfc) {
         acc = block_sum(acc, red);
-        if (threadIdx.x == 0) atomicAdd(&P.sc->red[0], acc);
+        if (red_leader()) atomicAdd(&P.sc->red[0], acc);
     }
 }
 template <int NF>
@@ -1376,7 +1387,7 @@ __device__ void phase_en_c(const Params& P, const Tw& tw, char* smem, double* re
                          }
                      });
     acc = block_sum(acc, red);
-    if (threadIdx.x == 0) atomicAdd(&P.sc->red[1], acc);
+    if (red_leader()) atomicAdd(&P.sc->red[1], acc);
 }
 template <int NF>
 __device__ void phase_en_r2(const Params& P, const Tw& tw, char* smem, double* red) {
@@ -1389,7 +1400,7 @@ __device__ void phase_en_r2(const Params& P, const Tw& tw, char* smem, double* r
                                  acc += 0.5 * w * w - P.eta2 * Fwell(u, P.tau);
                              });
     acc = block_sum(acc, red);
-    if (threadIdx.x == 0) atomicAdd(&P.sc->red[0], acc);
+    if (red_leader()) atomicAdd(&P.sc->red[0], acc);
 }
 inline __device__ void phase_mass(const Params& P, const Tw& tw, double* red) {
     double acc = 0.0;
@@ -1397,7 +1408,7 @@ inline __device__ void phase_mass(const Params& P, const Tw& tw, double* red) {
     const long long gs = thread_count(tw);
     for (long long p = gt; p < P.npts; p += gs) acc += P.in_real[p];
     acc = block_sum(acc, red);
-    if (threadIdx.x == 0) atomicAdd(&P.sc->red[0], acc);
+    if (red_leader()) atomicAdd(&P.sc->red[0], acc);
 }
 
 // ------------------------------------------------------ linear IMEX step
@@ -1845,13 +1856,19 @@ __host__ __device__ inline long long cost_start(long long w, long long total, lo
     return (total * w) / nw;
 }
 
+constexpr int kIdleRank = 1 << 28;  // rank * 32 exceeds any point count (< 2^32)
+
 // Tw of warp gw for instance i whose work is [g, g + cost) on the cost axis.
 __host__ __device__ inline void batch_split(Tw& t, long long gw, long long nw, long long total, long long g,
                                             long long cost, int units, int q) {
     const long long wa = cost_owner(g, total, nw), wb = cost_owner(g + cost - 1, total, nw);
     if (gw < wa || gw > wb) {
-        t.wr = 1;
-        t.wn = 0;  // thread_rank >= thread_count: no point work
+        // a warp of a CTA that works on the instance but owns none of it: it
+        // joins the CTA's barriers and reductions only.  Its thread rank is
+        // past every point and slot index and its stride is nonzero, so every
+        // strided loop is empty; it is not the leader; its unit range is empty.
+        t.wr = kIdleRank;
+        t.wn = 1;
         t.ulo = 0;
         t.uhi = 0;
         return;
