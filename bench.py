@@ -19,6 +19,7 @@ path); value = all ranks' steps / max-over-ranks time.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -34,6 +35,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 from paper_2204_07247_gb300 import inputs as I  # noqa: E402
+from paper_2204_07247_gb300 import replicas as R  # noqa: E402
 
 METRIC = "time steps/s at residual<=1e-8"
 UNIT = "steps/s"
@@ -112,6 +114,81 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# algorithmic HBM bytes per grid point per PAGD residual evaluation of the
+# iteration passes as laid out here (PFC, FP32-mixed): row pass 24.1 B (read the
+# direction's half spectrum, delta_i, delta_{i-1}, the FP32 base; write delta,
+# the nonlinear term's half spectrum) + column pass 24.2 B (read it, the two
+# spectral states and C0; write a state and the direction's half spectrum); 3D
+# adds the middle passes (read + write one half spectrum each way, 16.1 B)
+ITER_BYTES_2D_PFC = 48.3
+ITER_BYTES_3D_PFC = 64.4
+
+
+def flush_l2(torch):
+    buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    buf.fill_(1.0)  # larger than the 129 MB L2
+    del buf
+
+
+def bench_batch(torch, pagd, bw, steps, warm, plain_steps, bytes_per_eval, peak, rank=0, world=1, dist=None):
+    """One batched launch per chunk over all members of bw (the batched form),
+    and each member alone through the single-instance kernel (the plain form).
+    With N ranks each advances a disjoint shard of the members (strong scaling)."""
+    members = R.shard(bw.members, rank, world)
+    if not members:  # more ranks than members: this rank only joins the collectives
+        R.max_over_ranks(0.0, dist, "cuda")
+        R.sum_over_ranks(0.0, dist, "cuda")
+        R.max_over_ranks(0.0, dist, "cuda")
+        return None
+    sol = []
+    for w in members:
+        S = pagd.solver_for(w)
+        S.set_state(torch.from_numpy(w.u0(w.seeds[0])).cuda())
+        sol.append(S)
+    B = pagd.Batch(sol)
+    B.run(bw.dt, warm, bw.tol)
+    flush_l2(torch)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    its, res, status = B.run(bw.dt, steps, bw.tol)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = R.max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    npts = np.array([int(np.prod(w.n)) for w in members], dtype=np.float64)
+    evals = its.sum(axis=1).astype(np.float64)
+    nbytes = R.sum_over_ranks(float((evals * npts).sum()) * bytes_per_eval, dist, "cuda")
+    achieved = nbytes / (ms / 1000.0) / 1e9 / world  # per GPU
+    # plain form: the same members one at a time, a bounded number of steps each
+    plain_ms = 0.0
+    for w in members:
+        S = pagd.solver_for(w)
+        S.set_state(torch.from_numpy(w.u0(w.seeds[0])).cuda())
+        S.run(w.dt, warm, w.tol)
+        torch.cuda.synchronize()
+        e0.record()
+        S.run(w.dt, plain_steps, w.tol)
+        e1.record()
+        torch.cuda.synchronize()
+        plain_ms += e0.elapsed_time(e1)
+    plain_ms = R.max_over_ranks(plain_ms, dist, "cuda")
+    m = len(bw.members)
+    return {
+        "workload": bw.name, "members": m, "steps": steps, "ms": ms,
+        "member_steps_per_s": m * steps / (ms / 1000.0), "batch_steps_per_s": steps / (ms / 1000.0),
+        "iters_per_step": float(its.mean()), "max_iters": int(its.max()), "max_resid": float(res.max()),
+        "all_ok": bool(np.all(status == 0)), "gpu_launches": math.ceil(steps / 4096),
+        "scaling": "strong" if world > 1 else "weak",
+        "plain_member_steps_per_s": m * plain_steps / (plain_ms / 1000.0),
+        "plain_sample": f"each member alone, {plain_steps} steps after {warm} warm-up steps",
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "pagd_batch_kernel<float>",
+                     "bytes_model": f"{bytes_per_eval} B per point per residual evaluation of the "
+                                    f"iteration passes x sum over members of points x evaluations "
+                                    f"({nbytes / 1e9:.1f} GB); base evaluations not counted"},
+    }
+
+
 def oracle_steps_per_s(w, budget_s=15.0, max_steps=20):
     """The FP64 CPU oracle as it stands on a bounded sample of the workload."""
     from oracle import oracle as O
@@ -161,6 +238,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=I.FCH256.name, choices=sorted(I.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and 3D lines")
     args = ap.parse_args()
     w = I.WORKLOADS[args.workload]
 
@@ -241,12 +319,24 @@ def main():
     torch.cuda.synchronize()
     imex_sps = K / (e0.elapsed_time(e1) / 1000.0)
 
+    # the batched form (PFC, 96 members of 128^2 / 256^2 / 512^2) and the 3D
+    # workload (PFC 256^3, two seeds in one batch), each timed on its own
+    peak, peak_kind = measured_peaks()
+    extra = {}
+    if not args.no_forms:
+        extra["batched"] = bench_batch(torch, pagd, I.PFC_BATCH96, I.PFC_BATCH96.steps, W, 20,
+                                       ITER_BYTES_2D_PFC, peak, rank, world, dist)
+        w3 = I.PFC3D256
+        bw3 = I.BatchWorkload(w3.name + "_x2", [w3, dataclasses.replace(w3, seeds=(w3.seeds[1],))],
+                              w3.dt, w3.steps, w3.tol)
+        extra["pfc3d"] = bench_batch(torch, pagd, bw3, w3.steps, W, 5, ITER_BYTES_3D_PFC, peak, rank,
+                                     world, dist)
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return 0
 
-    peak, peak_kind = measured_peaks()
     bpp = BYTES_PER_POINT_EVAL[(w.model, w.precision)]
     launches = math.ceil(K / 4096)
     achieved = bpp * n_pts * evals / launches / ((ms / 1000.0) / launches) / 1e9
@@ -278,6 +368,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": launches,
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

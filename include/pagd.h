@@ -163,7 +163,9 @@ pagd_status pagd_step_static(pagd_solver* s, const double* un_dev, const double*
  * phase[i] and t_us[i] (microseconds since the launch started; record 0 is the
  * start marker), at most cap records, and the number recorded to *count.
  * Phase identifiers are those of the kernel's control machine (see
- * paper_2204_07247_gb300/pagd.py PHASES). */
+ * paper_2204_07247_gb300/pagd.py PHASES).  With tracing enabled on the first
+ * member of a batch, pagd_batch_run records its global phases in that member
+ * instead: phase[i] is then a bit mask (bit p set: some member ran phase p). */
 pagd_status pagd_set_trace(pagd_solver* s, int enable);
 pagd_status pagd_get_trace(pagd_solver* s, int* phase, double* t_us, int cap, int* count);
 

@@ -53,16 +53,27 @@ __global__ void __launch_bounds__(kThreads, 1) pagd_batch_kernel(BatchParams B) 
     const long long nw = (long long)gridDim.x * wpb;
     const long long gw = (long long)blockIdx.x * wpb + threadIdx.x / kWarp;
     unsigned gen = 0;
+    __shared__ unsigned s_mask;
+    int ntr = 0;
+    const bool tr = B.trace && blockIdx.x == 0 && threadIdx.x == 0;
+    if (tr) {
+        B.trace[0] = 1ull << PH_DONE;  // start marker
+        B.trace[1] = gtimer();
+        ntr = 1;
+    }
     for (;;) {
         __syncthreads();
         // cost prefix over the instances' current phases (warp 0, 32 at a time)
         if (threadIdx.x < 32) {
             long long base = 0;
+            unsigned mask = 0;
             for (int i0 = 0; i0 < B.count; i0 += 32) {
                 const int i = i0 + (int)threadIdx.x;
                 long long v = 0;
-                if (i < B.count && ctl[i].ph != PH_DONE)
+                if (i < B.count && ctl[i].ph != PH_DONE) {
                     v = (long long)phase_units(B.PI[i], ctl[i].ph) * unit_cost(B.PI[i], ctl[i].ph);
+                    mask |= 1u << ctl[i].ph;
+                }
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     const long long u = __shfl_up_sync(0xffffffffu, v, o);
@@ -71,7 +82,11 @@ __global__ void __launch_bounds__(kThreads, 1) pagd_batch_kernel(BatchParams B) 
                 if (i < B.count) G[i + 1] = base + v;
                 base += __shfl_sync(0xffffffffu, v, 31);
             }
-            if (threadIdx.x == 0) G[0] = 0;
+            mask = __reduce_or_sync(0xffffffffu, mask);
+            if (threadIdx.x == 0) {
+                G[0] = 0;
+                s_mask = mask;
+            }
         }
         __syncthreads();
         const long long total = G[B.count];
@@ -94,9 +109,15 @@ __global__ void __launch_bounds__(kThreads, 1) pagd_batch_kernel(BatchParams B) 
             batch_exec<T>(P, ctl[i], t, wsm, red);
         }
         if (!grid_barrier(B.sc, gen)) break;
+        if (tr && ntr < B.trace_cap) {
+            B.trace[2 * ntr] = s_mask;
+            B.trace[2 * ntr + 1] = gtimer();
+            ntr++;
+        }
         for (int i = threadIdx.x; i < B.count; i += blockDim.x)
             if (ctl[i].ph != PH_DONE) ctl_advance<T>(B.PI[i], ctl[i]);
     }
+    if (tr) *B.ntrace = ntr;
 }
 
 template <class T>

@@ -982,6 +982,10 @@ static pagd_status batch_chunk(pagd_batch* b, double dt, int nsteps, double tol,
     B.sc = bsc;
     B.tw64 = PI[0].tw64;
     B.tw32 = PI[0].tw32;
+    // tracing on the first member records the launch's global phases there
+    B.trace = s0->trace ? (unsigned long long*)(s0->ws + s0->off[O_TRACE]) : nullptr;
+    B.trace_cap = kTraceCap;
+    B.ntrace = &PI[0].sc->ntrace;
     st = (b->tsize == 8) ? batch_launch<double>(b, B) : batch_launch<float>(b, B);
     if (st != PAGD_OK) return st;
     Scal bs;

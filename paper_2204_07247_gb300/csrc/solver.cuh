@@ -1829,6 +1829,11 @@ struct BatchParams {
     Params* PI;  // device array of count instance parameter blocks
     int count, logtw;
     Scal* sc;    // barrier state of the launch
+    // nullable: one (mask of the phases run, globaltimer) record per global
+    // phase, the count in *ntrace
+    unsigned long long* trace;
+    int trace_cap;
+    int* ntrace;
     const double2* tw64;
     const float2* tw32;
 };

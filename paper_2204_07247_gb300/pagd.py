@@ -283,13 +283,16 @@ class Solver:
     def set_trace(self, enable=True):
         self._check(self.lib.pagd_set_trace(self._h, 1 if enable else 0), "set_trace")
 
-    def get_trace(self, cap=8192):
-        """(phase names, end times in us) of the last launch's phases."""
+    def get_trace(self, cap=8192, raw=False):
+        """(phase names, end times in us) of the last launch's phases; raw:
+        the identifiers as recorded (bit masks for a batch's global phases)."""
         ph = (ctypes.c_int * cap)()
         t = (ctypes.c_double * cap)()
         cnt = ctypes.c_int()
         self._check(self.lib.pagd_get_trace(self._h, ph, t, cap, ctypes.byref(cnt)), "get_trace")
         n = min(cnt.value, cap)
+        if raw:
+            return [ph[i] & 0xFFFFFFFF for i in range(n)], np.array(t[:n])
         return [PHASES[ph[i]] for i in range(n)], np.array(t[:n])
 
     def close(self):
