@@ -62,7 +62,7 @@ struct pagd_solver {
 
 enum {
     O_SC, O_NORMS, O_SUMS, O_STATS, O_TW64, O_TW32, O_U0, O_U1, O_VB, O_G64, O_VBT, O_LBT, O_DD0,
-    O_DD1, O_SS0, O_SS1, O_C0, O_NB, O_DB, O_CL64, O_NB64, O_DB64, O_MASS, O_TRACE, O_VR64, O_NR64, O_WR64, O_LB64, O_YB, O_X, O_X64, O_END
+    O_DD1, O_SS0, O_SS1, O_C0, O_NB, O_DB, O_CL64, O_NB64, O_DB64, O_MASS, O_TRACE, O_VR64, O_NR64, O_WR64, O_LB64, O_YB, O_X, O_X64, O_GH64, O_END
 };
 
 static pagd_status fail(pagd_solver* s, pagd_status st, const char* msg) {
@@ -116,6 +116,7 @@ static void plan_layout(pagd_solver* s) {
     sz[O_YB] = (size_t)T * N;
     sz[O_X] = s->dim == 3 ? (size_t)2 * T * H * 3 : 0;
     sz[O_X64] = s->dim == 3 ? sizeof(double2) * H * 3 : 0;
+    sz[O_GH64] = sizeof(double2) * H;
     size_t o = 0;
     for (int i = 0; i < O_END; i++) {
         s->off[i] = o;
@@ -195,6 +196,7 @@ static Params params_for(const pagd_solver* s, char* w) {
     P.VR64 = (double2*)(w + s->off[O_VR64]);
     P.NR64 = (double2*)(w + s->off[O_NR64]);
     P.WR64 = (double2*)(w + s->off[O_WR64]);
+    P.GH64 = (double2*)(w + s->off[O_GH64]);
     P.LB64 = (double*)(w + s->off[O_LB64]);
     P.YB = w + s->off[O_YB];
     P.X = s->dim == 3 ? (void*)(w + s->off[O_X]) : nullptr;

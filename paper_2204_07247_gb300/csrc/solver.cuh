@@ -120,6 +120,7 @@ struct Params {
     double2* VR64;
     double2* NR64;
     double2* WR64;  // FP64 spectrum of A_i v + g at the reference
+    double2* GH64;  // FP64 spectrum of the step's history term g (fixed within a step)
     double* LB64;
     void* YB;
     int ref_valid, refresh;
@@ -142,6 +143,7 @@ struct Params {
 struct Ctl {
     int ph, step, it, ev, lastev, cur, rech, fail, best_ev;
     int after, mk, m64;  // 3D middle pass: the phase after it, its fields, FP64 buffers
+    int gok;             // GH64 holds this step's g_hat (an exact evaluation made it)
     int acc, acc_cur, acc_it, acc_lastev, acc_ev, reb, ereb, inc, ref_ok, exact_done;
     double resid, base_nrm, best_nrm, acc_resid;
 };
@@ -359,6 +361,10 @@ __host__ __device__ __forceinline__ size_t row_warp_smem(int n1, int kin, int sz
 __host__ __device__ __forceinline__ size_t col_warp_smem(int n0, int k, int sz) {
     return (size_t)(k + 1) * pitch_of(n0) * 2 * sz;
 }
+// inputs in szi, outputs in szo < szi (separate buffers)
+__host__ __device__ __forceinline__ size_t col_warp_smem_mixed(int n0, int kin, int szi, int kout, int szo) {
+    return (size_t)(kin + 1) * pitch_of(n0) * 2 * szi + (size_t)(kout + 1) * pitch_of(n0) * 2 * szo;
+}
 
 struct WarpCtx {
     int lane;
@@ -447,41 +453,51 @@ __device__ void row_pass(const Params& P, const Tw& tw, int kin, int kout, const
 }
 
 // Column pass over the ncols contiguous lines of length n0: one warp per line.
-// fn(k1, k0, in, out); outputs may overwrite inputs of the same point.
-template <class T, class Fn>
-__device__ void col_pass(const Params& P, const Tw& tw, int kin, int kout, const cx<T>* src, cx<T>* dst,
+// fn(k1, k0, in, out); outputs may overwrite inputs of the same point.  The
+// forward transforms run in TI, the inverse ones in TO (TO narrower than TI:
+// outputs whose size is a small fraction of the inputs', e.g. a direction
+// computed from FP64 spectra, go back to physical space in FP32).
+template <class TI, class TO, class Fn>
+__device__ void col_pass(const Params& P, const Tw& tw, int kin, int kout, const cx<TI>* src, cx<TO>* dst,
                          char* smem, Fn&& fn) {
-    using C = cx<T>;
+    using CI = cx<TI>;
+    using CO = cx<TO>;
+    constexpr bool same = sizeof(TI) == sizeof(TO);
     const int n0 = P.n0, ncols = P.ncols, logn0 = P.logn0;
     const long long H = P.H;
     const int pitch = pitch_of(n0);
-    const int nb = (kin > kout ? kin : kout) + 1;
+    const int nbi = same ? (kin > kout ? kin : kout) + 1 : kin + 1;
     const WarpCtx w = warp_ctx(P, smem);
     const URange ur = units_of(tw, ncols);
     for (int k1 = ur.b; k1 < ur.e; k1 += ur.s) {
-        C* buf[kMaxK + 1];
-        for (int i = 0; i < nb; i++) buf[i] = (C*)w.mem + (size_t)i * pitch;
+        CI* buf[kMaxK + 1];
+        CO* obuf[kMaxK + 1];
+        for (int i = 0; i < nbi; i++) buf[i] = (CI*)w.mem + (size_t)i * pitch;
         for (int f = 0; f < kin; f++) {
-            const C* s = src + (size_t)f * H + (size_t)k1 * n0;
+            const CI* s = src + (size_t)f * H + (size_t)k1 * n0;
             for (int k0 = w.lane; k0 < n0; k0 += kWarp) buf[f][k0] = s[k0];
-            const int res = fft_line_w<-1, T>(buf[f], buf[nb - 1], logn0, tw_of<T>(tw), tw.log, w.lane);
+            const int res = fft_line_w<-1, TI>(buf[f], buf[nbi - 1], logn0, tw_of<TI>(tw), tw.log, w.lane);
             if (res) {
-                C* t = buf[f];
-                buf[f] = buf[nb - 1];
-                buf[nb - 1] = t;
+                CI* t = buf[f];
+                buf[f] = buf[nbi - 1];
+                buf[nbi - 1] = t;
             }
         }
+        // outputs: in place of the inputs (same precision) or after them
+        for (int i = 0; i <= kout; i++)
+            obuf[i] = same ? (CO*)(i < kout ? buf[i] : buf[nbi - 1])
+                           : (CO*)((CI*)w.mem + (size_t)nbi * pitch) + (size_t)i * pitch;
         for (int k0 = w.lane; k0 < n0; k0 += kWarp) {
-            C in[kMaxK];
-            C out[kMaxK];
+            CI in[kMaxK];
+            CO out[kMaxK];
             for (int f = 0; f < kin; f++) in[f] = buf[f][k0];
             fn(k1, k0, in, out);
-            for (int g = 0; g < kout; g++) buf[g][k0] = out[g];
+            for (int g = 0; g < kout; g++) obuf[g][k0] = out[g];
         }
         for (int g = 0; g < kout; g++) {
-            const int res = fft_line_w<+1, T>(buf[g], buf[nb - 1], logn0, tw_of<T>(tw), tw.log, w.lane);
-            const C* r = res ? buf[nb - 1] : buf[g];
-            C* d = dst + (size_t)g * H + (size_t)k1 * n0;
+            const int res = fft_line_w<+1, TO>(obuf[g], obuf[kout], logn0, tw_of<TO>(tw), tw.log, w.lane);
+            const CO* r = res ? obuf[kout] : obuf[g];
+            CO* d = dst + (size_t)g * H + (size_t)k1 * n0;
             for (int k0 = w.lane; k0 < n0; k0 += kWarp) d[k0] = r[k0];
             warp_sync();
         }
@@ -607,10 +623,11 @@ __device__ void row_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
     }
 }
 
-template <class T, int NF, class Ld, class Ap>
-__device__ void col_pass_fixed(const Params& P, const Tw& tw, int kin, int kout, const cx<T>* src, cx<T>* dst,
-                               char* smem, Ld&& ld, Ap&& ap) {
-    using C = cx<T>;
+template <class TI, class TO, int NF, class Ld, class Ap>
+__device__ void col_pass_fixed(const Params& P, const Tw& tw, int kin, int kout, const cx<TI>* src,
+                               cx<TO>* dst, char* smem, Ld&& ld, Ap&& ap) {
+    using C = cx<TI>;
+    using CO = cx<TO>;
     using S = decltype(ld(0, 0));
     constexpr int LOGN = ilog2c(NF), PITCH = NF + 2, E = NF / kWarp;
     constexpr int GCH = E < 8 ? E : 8;
@@ -635,12 +652,15 @@ __device__ void col_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
             }
         }
         const C* Xr = B0;
-        C* Xo = B1;
+        C* Xi = B1;
         if (kin > 0) {
-            const int r = fft_lines_fixed<-1, T, LOGN, kMaxK>(B0, B1, PITCH, kin, tw_of<T>(tw), tw.log, w.lane);
+            const int r = fft_lines_fixed<-1, TI, LOGN, kMaxK>(B0, B1, PITCH, kin, tw_of<TI>(tw), tw.log, w.lane);
             Xr = r ? B1 : B0;
-            Xo = r ? B0 : B1;
+            Xi = r ? B0 : B1;
         }
+        // outputs (TO, PITCH apart) in the buffer the inputs do not occupy;
+        // kl lines of TI hold kout lines of TO
+        CO* Xo = (CO*)Xi;
 #pragma unroll 1
         for (int c0 = 0; c0 < E; c0 += PCH) {
             S st[PCH];
@@ -650,7 +670,7 @@ __device__ void col_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
             for (int q = 0; q < PCH; q++) {
                 const int k0 = w.lane + kWarp * (c0 + q);
                 C in[kMaxK];
-                C out[kMaxK];
+                CO out[kMaxK];
 #pragma unroll
                 for (int f = 0; f < kMaxK; f++)
                     if (f < kin) in[f] = Xr[(size_t)f * PITCH + k0];
@@ -661,11 +681,12 @@ __device__ void col_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
             }
         }
         if (kout > 0) {
-            C* scratch = (C*)Xr;
-            const int r = fft_lines_fixed<+1, T, LOGN, kMaxK>(Xo, scratch, PITCH, kout, tw_of<T>(tw), tw.log, w.lane);
-            const C* Yr = r ? scratch : Xo;
+            CO* scratch = (CO*)Xr;
+            const int r =
+                fft_lines_fixed<+1, TO, LOGN, kMaxK>(Xo, scratch, PITCH, kout, tw_of<TO>(tw), tw.log, w.lane);
+            const CO* Yr = r ? scratch : Xo;
             for (int g = 0; g < kout; g++) {
-                C* d = dst + (size_t)g * Hs + (size_t)k1 * NF;
+                CO* d = dst + (size_t)g * Hs + (size_t)k1 * NF;
 #pragma unroll
                 for (int i = 0; i < E; i++) d[w.lane + kWarp * i] = Yr[(size_t)g * PITCH + w.lane + kWarp * i];
             }
@@ -760,17 +781,22 @@ __device__ __forceinline__ void rowp(const Params& P, const Tw& tw, int kin, int
     }
 }
 
-template <class T, int NF, class Ld, class Ap>
-__device__ __forceinline__ void colp(const Params& P, const Tw& tw, int kin, int kout, const cx<T>* src,
-                                     cx<T>* dst, char* smem, Ld&& ld, Ap&& ap) {
+template <class TI, class TO, int NF, class Ld, class Ap>
+__device__ __forceinline__ void colp2(const Params& P, const Tw& tw, int kin, int kout, const cx<TI>* src,
+                                      cx<TO>* dst, char* smem, Ld&& ld, Ap&& ap) {
     if constexpr (NF == 0) {
-        col_pass<T>(P, tw, kin, kout, src, dst, smem, [&](int k1, int k0, const cx<T>* in, cx<T>* out) {
+        col_pass<TI, TO>(P, tw, kin, kout, src, dst, smem, [&](int k1, int k0, const cx<TI>* in, cx<TO>* out) {
             const auto s = ld(k1, k0);
             ap(k1, k0, s, in, out);
         });
     } else {
-        col_pass_fixed<T, NF>(P, tw, kin, kout, src, dst, smem, ld, ap);
+        col_pass_fixed<TI, TO, NF>(P, tw, kin, kout, src, dst, smem, ld, ap);
     }
+}
+template <class T, int NF, class Ld, class Ap>
+__device__ __forceinline__ void colp(const Params& P, const Tw& tw, int kin, int kout, const cx<T>* src,
+                                     cx<T>* dst, char* smem, Ld&& ld, Ap&& ap) {
+    colp2<T, T, NF>(P, tw, kin, kout, src, dst, smem, ld, ap);
 }
 
 struct Nil {};
@@ -844,7 +870,9 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
     T* yb = (T*)P.YB;
     cx<TO>* dst = INC ? (cx<TO>*)P.NB : (cx<TO>*)P.NB64;
     const double Ai = k.Ai;
-    const int kout = (INC && reb) ? kb - 1 : kb;
+    // an exact re-evaluation within a step reuses the step's g_hat (GH64)
+    const bool gcached = !INC && reb && c.gok;
+    const int kout = ((INC && reb) || gcached) ? kb - 1 : kb;
     rowp<double, TO, NF>(
         P, tw, 0, kout, (const double2*)nullptr, dst, smem,
         [&](long long p, int, int) {
@@ -902,8 +930,8 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
                 }
             } else {
                 out[0] = vb;
-                out[1] = g;
-                if (pfc) out[2] = vb * vb * vb;
+                if (!gcached) out[1] = g;
+                if (pfc) out[gcached ? 1 : 2] = vb * vb * vb;
             }
         });
     if (!reb) {
@@ -955,11 +983,18 @@ __device__ void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem)
     const int kb = k_base(P.model);
     const double iM = 1.0 / P.M;
     const double e4 = P.eps * P.eps * P.eps * P.eps;
+    const bool gcached = c.ereb && c.gok;  // g_hat from GH64, not among the inputs
+    const int kin = gcached ? kb - 1 : kb;
+    auto ldg_hat = [&](int k1, int k0) {
+        return gcached ? P.GH64[(long long)k1 * P.n0 + k0] : double2{0.0, 0.0};
+    };
     if (P.model == M_PFC) {
-        colp<double, NF>(P, tw, kb, 1, csrc64(P), cdst64(P), smem, [&](int, int) { return Nil{}; },
-                         [&](int k1, int k0, const Nil&, const double2* in, double2* out) {
+        // the direction is small: its inverse transforms run in T
+        colp2<double, T, NF>(P, tw, kin, 1, csrc64(P), cdstT<T>(P), smem, ldg_hat,
+                         [&](int k1, int k0, const double2& gh, const double2* in, cx<T>* out) {
                              const double kap = kappa_at(P, k1, k0);
-                             const double2 v = in[0], g = in[1], nl = in[2];
+                             const double2 v = in[0], g = gcached ? gh : in[1], nl = in[gcached ? 1 : 2];
+                             if (!gcached) P.GH64[(long long)k1 * P.n0 + k0] = g;
                              P.VR64[(long long)k1 * P.n0 + k0] = v;
                              P.NR64[(long long)k1 * P.n0 + k0] = nl;
                              P.WR64[(long long)k1 * P.n0 + k0] = double2{k.Ai * v.x + g.x, k.Ai * v.y + g.y};
@@ -972,13 +1007,14 @@ __device__ void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem)
                              }
                              double2 d;
                              base_direction<T>(P, k, B, k1, k0, kap, G, d);
-                             out[0] = d;
+                             out[0] = cx<T>{(T)d.x, (T)d.y};
                          });
     } else {
-        colp<double, NF>(P, tw, kb, 1, csrc64(P), cdst64(P), smem, [&](int, int) { return Nil{}; },
-                         [&](int k1, int k0, const Nil&, const double2* in, double2* out) {
+        colp<double, NF>(P, tw, kin, 1, csrc64(P), cdst64(P), smem, ldg_hat,
+                         [&](int k1, int k0, const double2& gh, const double2* in, double2* out) {
                              const double kap = kappa_at(P, k1, k0);
-                             const double2 v = in[0], g = in[1];
+                             const double2 v = in[0], g = gcached ? gh : in[1];
+                             if (!gcached) P.GH64[(long long)k1 * P.n0 + k0] = g;
                              P.VR64[(long long)k1 * P.n0 + k0] = v;
                              P.WR64[(long long)k1 * P.n0 + k0] = double2{k.Ai * v.x + g.x, k.Ai * v.y + g.y};
                              double2 G{0.0, 0.0};
@@ -1017,9 +1053,10 @@ __device__ void phase_E(const Params& P, const Ctl& c, const Tw& tw, char* smem)
     const Beta B = betas(P, k, c.step);
     const double e2 = P.eps * P.eps;
     const double l1 = lam_at(P, 1);
-    colp<double, NF>(P, tw, 2, 2, csrc64(P), cdst64(P), smem,
+    // the direction (and Lap of the first correction) are small: inverse in T
+    colp2<double, T, NF>(P, tw, 2, 2, csrc64(P), cdstT<T>(P), smem,
                      [&](int k1, int k0) { return P.CL64[(long long)k1 * P.n0 + k0]; },
-                     [&](int k1, int k0, const double2& lin, const double2* in, double2* out) {
+                     [&](int k1, int k0, const double2& lin, const double2* in, cx<T>* out) {
                          const double kap = kappa_at(P, k1, k0);
                          const long long idx = (long long)k1 * P.n0 + k0;
                          P.NR64[idx] = in[0];
@@ -1031,9 +1068,9 @@ __device__ void phase_E(const Params& P, const Ctl& c, const Tw& tw, char* smem)
                          }
                          double2 d;
                          base_direction<T>(P, k, B, k1, k0, kap, G, d);
-                         out[0] = d;
+                         out[0] = cx<T>{(T)d.x, (T)d.y};
                          const double f = -kap * (1.0 + l1) * k.ts;
-                         out[1] = double2{f * d.x, f * d.y};
+                         out[1] = cx<T>{(T)(f * d.x), (T)(f * d.y)};
                      });
 }
 
@@ -1550,6 +1587,7 @@ __host__ __device__ inline Ctl ctl_init(const Params& P) {
     c.exact_done = 0;
     c.ereb = 0;
     c.after = PH_DONE; c.mk = 0; c.m64 = 1;
+    c.gok = 0;
     c.inc = inc_eval(P, c.ref_ok, P.step0, 1);
     c.resid = 0.0; c.base_nrm = 0.0; c.best_nrm = 0.0; c.acc_resid = 0.0;
     switch (P.prog) {
@@ -1579,14 +1617,14 @@ __host__ __device__ inline bool row_reads_spectrum(int ph) {
 // and between a column pass and a row pass that reads its output (MI).  pph,
 // pinc, preb: the phase that just ran and its incremental / rebase flags,
 // which fix the number of spectral fields it wrote and their buffer set.
-__host__ __device__ inline void mid_insert(const Params& P, int pph, int pinc, int preb, Ctl& c) {
+__host__ __device__ inline void mid_insert(const Params& P, int pph, int pinc, int preb, int pgok, Ctl& c) {
     const int nx = c.ph;
     const int K = k_iter(P.model), kb = k_base(P.model);
     int k = 0, m64 = 1, ph = -1;
     if (!phase_is_col(pph) && !phase_is_mid(pph) && phase_is_col(nx)) {
         ph = PH_MF;
         switch (pph) {
-            case PH_B: k = (pinc && preb) ? kb - 1 : kb; m64 = !pinc; break;
+            case PH_B: k = (preb && (pinc || pgok)) ? kb - 1 : kb; m64 = !pinc; break;
             case PH_D: k = 2; m64 = !pinc; break;
             case PH_R1:
             case PH_RI: k = K; m64 = 0; break;
@@ -1597,8 +1635,8 @@ __host__ __device__ inline void mid_insert(const Params& P, int pph, int pinc, i
     } else if (phase_is_col(pph) && row_reads_spectrum(nx)) {
         ph = PH_MI;
         switch (pph) {
-            case PH_C: k = 1; m64 = !pinc; break;
-            case PH_E: k = 2; m64 = !pinc; break;
+            case PH_C: k = 1; m64 = (P.model == M_FCH) && !pinc; break;  // PFC: direction in T
+            case PH_E: k = 2; m64 = 0; break;
             case PH_CI: k = K; m64 = 0; break;
             default: k = 1; break;  // INV_C, EN_C, IM_C0, IM_C1
         }
@@ -1622,9 +1660,9 @@ __device__ void ctl_advance(const Params& P, Ctl& c) {
         c.ph = c.after;
         return;
     }
-    const int pph = c.ph, pinc = c.inc, preb = c.reb;
+    const int pph = c.ph, pinc = c.inc, preb = c.reb, pgok = c.gok;
     ctl_step<T>(P, c);
-    if (P.nm > 1) mid_insert(P, pph, pinc, preb, c);
+    if (P.nm > 1) mid_insert(P, pph, pinc, preb, pgok, c);
 }
 
 template <class T>
@@ -1640,6 +1678,7 @@ __device__ void ctl_step(const Params& P, Ctl& c) {
             c.ph = PH_C;
             break;
         case PH_C:
+            if (!c.inc) c.gok = 1;  // GH64 now holds this step's g_hat
             if (P.model == M_FCH) { c.ph = PH_D; break; }
             [[fallthrough]];
         case PH_E:
@@ -1682,6 +1721,7 @@ __device__ void ctl_step(const Params& P, Ctl& c) {
                     c.step++;
                     c.cur ^= 1;
                     c.exact_done = 0;
+                    c.gok = 0;
                     c.inc = t64 ? 0 : inc_eval(P, c.ref_ok, P.step0 + c.step, 1);
                     c.ph = PH_B;
                 } else {
@@ -1743,10 +1783,7 @@ __device__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* sm
             if (c.inc) phase_EN<T, NF>(P, c, tw, smem);
             else phase_E<T, NF>(P, c, tw, smem);
             break;
-        case PH_R1:
-            if (c.inc) phase_R<T, T, NF>(P, c, tw, smem, red, (const cx<T>*)P.DB);
-            else phase_R<double, T, NF>(P, c, tw, smem, red, P.DB64);
-            break;
+        case PH_R1: phase_R<T, T, NF>(P, c, tw, smem, red, (const cx<T>*)P.DB); break;
         case PH_RI: phase_R<T, T, NF>(P, c, tw, smem, red, (const cx<T>*)P.DB); break;
         case PH_CI: phase_CI<T, NF>(P, c, tw, smem); break;
         case PH_ACCEPT: phase_accept<T>(P, c, tw, red); break;
@@ -1792,6 +1829,8 @@ inline size_t warp_smem_bytes(int n0, int n1, int model, int tsize, int nf, int 
         upd(col_warp_smem(n0, 3, 8));                  // C / IMEX C0
         upd(col_warp_smem(n0, 2, 8));                  // E
         upd(col_warp_smem(n0, ki, tsize));             // CI
+        upd(col_warp_smem_mixed(n0, 3, 8, 1, tsize));  // exact C (PFC): FP64 in, direction out
+        upd(col_warp_smem_mixed(n0, 2, 8, 2, tsize));  // exact E (FCH)
     } else {
         const size_t p = (size_t)(nf + 2);
         auto rowf = [&](int kin, int szin, int kout, int szout) {
