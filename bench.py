@@ -189,6 +189,64 @@ def bench_batch(torch, pagd, bw, steps, warm, plain_steps, bytes_per_eval, peak,
     }
 
 
+def timed_run(torch, S, dt, steps, tol):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    its, res = S.run(dt, steps, tol)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), its
+
+
+def bench_pgd_vs_pagd(torch, pagd, w, steps):
+    """Table 2 analogue on the workload: the same kernels with sweeping friction
+    (PAGD, Algorithm 2) and with lambda = 0 (PGD, Algorithm 1), from the same
+    state after the same warm-up; transform pairs per step = evaluations x real
+    fields per pass (PFC 1, FCH 2)."""
+    pairs = 1 if w.model == "pfc" else 2
+    out = {"workload": w.name, "steps": steps}
+    for name, accel in (("pagd", 1), ("pgd", 0)):
+        S = pagd.solver_for(w, accel=accel, max_iter=5000)
+        S.set_state(torch.from_numpy(w.u0(1)).cuda())
+        S.run(w.dt, 3, w.tol)
+        ms, its = timed_run(torch, S, w.dt, steps, w.tol)
+        out[name] = {"steps_per_s": steps / (ms / 1000.0), "iters_per_step": float(np.mean(its)),
+                     "fft_pairs_per_step": pairs * float(np.mean(its))}
+    out["iteration_ratio_pgd_over_pagd"] = out["pgd"]["iters_per_step"] / out["pagd"]["iters_per_step"]
+    return out
+
+
+def bench_cost_to_accuracy(torch, pagd, w, T_end, dts, ref_refine=8):
+    """Table 4 analogue: fully implicit (PAGD) and linear IMEX schemes at equal
+    final time T_end, error in the relative L2 norm against a reference run of
+    the implicit scheme at dt_min / ref_refine, and the device time of each run."""
+    def run(scheme, dt, precision):
+        S = pagd.solver_for(w, scheme=scheme, precision=precision)
+        S.set_state(torch.from_numpy(w.u0(1)).cuda())
+        n = int(round(T_end / dt))
+        out = torch.empty(w.n, dtype=torch.float64, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        S.run(dt, n, w.tol if scheme in ("bdf2", "mp") else 0.0, out)
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    imp, imex = w.scheme, {"bdf2": "lbdf2", "mp": "lmp"}[w.scheme]
+    ref, _ = run(imp, min(dts) / ref_refine, "fp64")
+    rn = float(torch.linalg.norm(ref))
+    rows = []
+    for dt in dts:
+        for scheme, prec in ((imp, w.precision), (imex, "fp64")):
+            u, ms = run(scheme, dt, prec)
+            rows.append({"scheme": scheme, "precision": prec, "dt": dt, "ms": ms,
+                         "rel_l2_error": float(torch.linalg.norm(u - ref)) / rn})
+    return {"workload": w.name, "T": T_end, "reference": f"{imp} fp64 at dt {min(dts) / ref_refine:g}",
+            "runs": rows}
+
+
 def oracle_steps_per_s(w, budget_s=15.0, max_steps=20):
     """The FP64 CPU oracle as it stands on a bounded sample of the workload."""
     from oracle import oracle as O
@@ -239,6 +297,7 @@ def main():
     ap.add_argument("--workload", default=I.FCH256.name, choices=sorted(I.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and 3D lines")
+    ap.add_argument("--no-studies", action="store_true", help="skip the PGD and cost-to-accuracy studies")
     args = ap.parse_args()
     w = I.WORKLOADS[args.workload]
 
@@ -323,6 +382,10 @@ def main():
     # workload (PFC 256^3, two seeds in one batch), each timed on its own
     peak, peak_kind = measured_peaks()
     extra = {}
+    if not args.no_studies and rank == 0:
+        extra["pgd_vs_pagd"] = bench_pgd_vs_pagd(torch, pagd, w, 100)
+        extra["cost_to_accuracy"] = bench_cost_to_accuracy(torch, pagd, w, 0.064,
+                                                           [4e-3, 2e-3, 1e-3, 5e-4])
     if not args.no_forms:
         extra["batched"] = bench_batch(torch, pagd, I.PFC_BATCH96, I.PFC_BATCH96.steps, W, 20,
                                        ITER_BYTES_2D_PFC, peak, rank, world, dist)
