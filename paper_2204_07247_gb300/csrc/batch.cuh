@@ -34,7 +34,7 @@ __device__ void batch_exec(const Params& P, const Ctl& c, const Tw& t, char* wsm
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads, 1) pagd_batch_kernel(BatchParams B) {
+__global__ void __launch_bounds__(kMaxThreads, 1) pagd_batch_kernel(BatchParams B) {
     extern __shared__ __align__(16) char smem[];
     __shared__ double red[32];
     const int ntw = 1 << B.logtw;
@@ -121,12 +121,13 @@ __global__ void __launch_bounds__(kThreads, 1) pagd_batch_kernel(BatchParams B) 
 }
 
 template <class T>
-cudaError_t pagd_batch_launch(const BatchParams& B, int grid, size_t smem, void* stream, int* grid_used) {
+cudaError_t pagd_batch_launch(const BatchParams& B, int grid, int threads, size_t smem, void* stream,
+                              int* grid_used) {
     void (*kern)(BatchParams) = pagd_batch_kernel<T>;
     cudaError_t e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int dev = 0, sms = 1;
@@ -139,11 +140,11 @@ cudaError_t pagd_batch_launch(const BatchParams& B, int grid, size_t smem, void*
     if (grid_used) *grid_used = grid;
     BatchParams Bc = B;
     void* args[] = {(void*)&Bc};
-    return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kThreads), args, smem,
+    return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(threads), args, smem,
                                        (cudaStream_t)stream);
 }
 
 }  // namespace pagd
 
 #define PAGD_INSTANTIATE_BATCH(T) \
-    template cudaError_t pagd::pagd_batch_launch<T>(const pagd::BatchParams&, int, size_t, void*, int*);
+    template cudaError_t pagd::pagd_batch_launch<T>(const pagd::BatchParams&, int, int, size_t, void*, int*);

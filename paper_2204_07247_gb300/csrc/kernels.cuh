@@ -60,7 +60,7 @@ static __device__ bool grid_barrier(Scal* sc, unsigned& gen) {
 }
 
 template <class T, int NF>
-__global__ void __launch_bounds__(kThreads, 1) pagd_kernel(Params P) {
+__global__ void __launch_bounds__(kMaxThreads, 1) pagd_kernel(Params P) {
     extern __shared__ __align__(16) char smem[];
     __shared__ double red[32];
     // twiddles exp(-2 pi i m / 2^logtw) staged from the global table
@@ -102,12 +102,12 @@ __global__ void __launch_bounds__(kThreads, 1) pagd_kernel(Params P) {
 // Launch pagd_kernel<T, NF> cooperatively: the grid is capped at the number of
 // co-resident CTAs so that the device-wide barrier is safe.
 template <class T, int NF>
-cudaError_t pagd_launch(const Params& P, int grid, size_t smem, void* stream, int* grid_used) {
+cudaError_t pagd_launch(const Params& P, int grid, int threads, size_t smem, void* stream, int* grid_used) {
     void (*kern)(Params) = pagd_kernel<T, NF>;
     cudaError_t e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int dev = 0, sms = 1;
@@ -120,12 +120,12 @@ cudaError_t pagd_launch(const Params& P, int grid, size_t smem, void* stream, in
     if (grid_used) *grid_used = grid;
     Params Pc = P;
     void* args[] = {(void*)&Pc};
-    return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kThreads), args, smem,
+    return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(threads), args, smem,
                                        (cudaStream_t)stream);
 }
 
 }  // namespace pagd
 
 #define PAGD_INSTANTIATE(NF)                                                                             \
-    template cudaError_t pagd::pagd_launch<float, NF>(const pagd::Params&, int, size_t, void*, int*);   \
-    template cudaError_t pagd::pagd_launch<double, NF>(const pagd::Params&, int, size_t, void*, int*);
+    template cudaError_t pagd::pagd_launch<float, NF>(const pagd::Params&, int, int, size_t, void*, int*);   \
+    template cudaError_t pagd::pagd_launch<double, NF>(const pagd::Params&, int, int, size_t, void*, int*);

@@ -21,9 +21,10 @@ using namespace pagd;
 #ifndef PAGD_EMU
 namespace pagd {
 template <class T, int NF>
-cudaError_t pagd_launch(const Params& P, int grid, size_t smem, void* stream, int* grid_used);
+cudaError_t pagd_launch(const Params& P, int grid, int threads, size_t smem, void* stream, int* grid_used);
 template <class T>
-cudaError_t pagd_batch_launch(const BatchParams& B, int grid, size_t smem, void* stream, int* grid_used);
+cudaError_t pagd_batch_launch(const BatchParams& B, int grid, int threads, size_t smem, void* stream,
+                              int* grid_used);
 }
 #else
 thread_local EmuDim3 threadIdx{0, 0, 0}, blockIdx{0, 0, 0}, blockDim{1, 1, 1}, gridDim{1, 1, 1};
@@ -52,7 +53,7 @@ struct pagd_solver {
     size_t ws_bytes;
     char* ws;
     // launch plan
-    int grid, logtw;
+    int grid, logtw, threads;
     size_t smem, warp_bytes;
     // state
     int have_state, step, cur, trace, ref_valid;
@@ -287,11 +288,11 @@ template <class T> static pagd_status launch(pagd_solver* s, const Params& P) {
     cudaError_t e;
     int used = 0;
     switch (fixed_len(P.n0, P.n1)) {
-        case 64: e = pagd_launch<T, 64>(P, s->grid, s->smem, s->stream, &used); break;
-        case 128: e = pagd_launch<T, 128>(P, s->grid, s->smem, s->stream, &used); break;
-        case 256: e = pagd_launch<T, 256>(P, s->grid, s->smem, s->stream, &used); break;
-        case 512: e = pagd_launch<T, 512>(P, s->grid, s->smem, s->stream, &used); break;
-        default: e = pagd_launch<T, 0>(P, s->grid, s->smem, s->stream, &used); break;
+        case 64: e = pagd_launch<T, 64>(P, s->grid, s->threads, s->smem, s->stream, &used); break;
+        case 128: e = pagd_launch<T, 128>(P, s->grid, s->threads, s->smem, s->stream, &used); break;
+        case 256: e = pagd_launch<T, 256>(P, s->grid, s->threads, s->smem, s->stream, &used); break;
+        case 512: e = pagd_launch<T, 512>(P, s->grid, s->threads, s->smem, s->stream, &used); break;
+        default: e = pagd_launch<T, 0>(P, s->grid, s->threads, s->smem, s->stream, &used); break;
     }
     if (e != cudaSuccess) return cuda_fail(s, e, "cooperative launch of pagd_kernel");
     return PAGD_OK;
@@ -306,16 +307,23 @@ static pagd_status run_program(pagd_solver* s, Params& P) {
     return st;
 }
 
-// One warp per row unit / column; kThreads / 32 warps per CTA (one in the
-// emulation).  The grid covers the larger of the row and column unit counts
-// and is capped at the co-resident CTA count when launched.
+// One warp per row unit / column / middle unit.  A CTA has as many warps (at
+// most 8) as their shared-memory slices allow (one in the emulation).  The
+// grid covers the largest unit count and is capped at the co-resident CTA
+// count when launched.
 static void make_plan(pagd_solver* s) {
+    const int last = s->dim - 1, nm = s->dim == 3 ? s->n[1] : 1;
+    s->logtw = 0;
+    for (int d = 0; d < s->dim; d++) s->logtw = std::max(s->logtw, ilog2(s->n[d]));
+    s->warp_bytes = warp_smem_bytes(s->n[0], s->n[last], s->model, s->tsize, fixed_len(s->n[0], s->n[last]), nm);
 #ifdef PAGD_EMU
     const int wpb = 1;
 #else
-    const int wpb = kThreads / 32;
+    const size_t room = kMaxSmem - tw_smem_bytes(s->logtw);
+    int wpb = (int)std::min<size_t>((size_t)(kMaxThreads / 32), room / s->warp_bytes);
+    if (wpb < 1) wpb = 1;
 #endif
-    const int last = s->dim - 1, nm = s->dim == 3 ? s->n[1] : 1;
+    s->threads = wpb * 32;
     const long long rows = rows_of(s);
     long long units = rows / 2;
     if ((long long)s->h1 * nm > units) units = (long long)s->h1 * nm;
@@ -326,9 +334,6 @@ static void make_plan(pagd_solver* s) {
         s->grid = (int)(g < 65536 ? g : 65536);  // capped at the co-resident CTAs when launched
     }
     if (s->grid < 1) s->grid = 1;
-    s->logtw = 0;
-    for (int d = 0; d < s->dim; d++) s->logtw = std::max(s->logtw, ilog2(s->n[d]));
-    s->warp_bytes = warp_smem_bytes(s->n[0], s->n[last], s->model, s->tsize, fixed_len(s->n[0], s->n[last]), nm);
     s->smem = tw_smem_bytes(s->logtw) + (size_t)wpb * s->warp_bytes;
 }
 
@@ -808,7 +813,7 @@ pagd_status pagd_get_trace(pagd_solver* s, int* phase, double* t_us, int cap, in
 
 struct pagd_batch {
     std::vector<pagd_solver*> m;
-    int tsize, logtw, grid;
+    int tsize, logtw, grid, threads;
     size_t warp_bytes, smem, ws_bytes;
     char* ws;
     void* stream;
@@ -891,7 +896,7 @@ template <class T> static pagd_status batch_launch(pagd_batch* b, const BatchPar
 #else
 template <class T> static pagd_status batch_launch(pagd_batch* b, const BatchParams& B) {
     int used = 0;
-    cudaError_t e = pagd_batch_launch<T>(B, b->grid, b->smem, b->stream, &used);
+    cudaError_t e = pagd_batch_launch<T>(B, b->grid, b->threads, b->smem, b->stream, &used);
     if (e != cudaSuccess) {
         char buf[256];
         std::snprintf(buf, sizeof(buf), "cooperative launch of pagd_batch_kernel: %s", cudaGetErrorString(e));
@@ -929,8 +934,11 @@ pagd_status pagd_batch_create(pagd_batch** out, pagd_solver* const* members, int
 #ifdef PAGD_EMU
     const int wpb = kEmuBatchWarps;
 #else
-    const int wpb = kThreads / 32;
+    const size_t fixed = tw_smem_bytes(b->logtw) + batch_ctl_bytes(count);
+    int wpb = fixed < kMaxSmem ? (int)std::min<size_t>((size_t)(kMaxThreads / 32), (kMaxSmem - fixed) / b->warp_bytes) : 0;
+    if (wpb < 1) wpb = 1;
 #endif
+    b->threads = wpb * 32;
     b->smem = tw_smem_bytes(b->logtw) + batch_ctl_bytes(count) + (size_t)wpb * b->warp_bytes;
     if (b->smem > kMaxSmem) {
         delete b;

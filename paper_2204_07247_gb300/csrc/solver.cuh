@@ -64,7 +64,10 @@ struct StepStat {
 };
 
 constexpr int kMaxK = 3;        // fields per pass
-constexpr int kThreads = 128;   // CTA size of the persistent kernel (4 warps)
+// CTA size of the persistent kernels: up to 8 warps (255 registers each fill
+// the register file); the launch picks as many as the warps' shared memory
+// slices allow
+constexpr int kMaxThreads = 256;
 
 // scheme coefficients of one step (see compute_step_coeffs)
 struct StepK {
