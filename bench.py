@@ -288,6 +288,59 @@ def run_reference(args, w, rank):
     return 0
 
 
+FORMS = ("single", "batched", "pfc3d")
+
+
+def form_solvers(torch, pagd, form, w):
+    """Solvers (state set) and a runner for one form: the single-instance
+    workload w, the 96-member batch, or the two-seed 3D batch."""
+    if form == "single":
+        S = pagd.solver_for(w)
+        S.set_state(torch.from_numpy(w.u0(1)).cuda())
+        return [S], (lambda k: S.run(w.dt, k, w.tol)), w.dt
+    if form == "batched":
+        members = I.PFC_BATCH96.members
+    else:
+        members = [I.PFC3D256, dataclasses.replace(I.PFC3D256, seeds=(I.PFC3D256.seeds[1],))]
+    sol = []
+    for m in members:
+        S = pagd.solver_for(m)
+        S.set_state(torch.from_numpy(m.u0(m.seeds[0])).cuda())
+        sol.append(S)
+    B = pagd.Batch(sol)
+    m0 = members[0]
+    return sol, (lambda k: B.run(m0.dt, k, m0.tol)), m0.dt
+
+
+def profile_form(torch, pagd, form, w, steps, warm, trace):
+    """One warm-up launch, then one launch of `steps` steps (the launch an ncu
+    capture with -s 1 -c 1 takes); with trace, print its phase breakdown."""
+    import collections
+    sol, run, _ = form_solvers(torch, pagd, form, w)
+    run(warm)
+    if trace:
+        sol[0].set_trace(True)
+    out = run(steps)
+    torch.cuda.synchronize()
+    if not trace:
+        print("ok", flush=True)
+        return 0
+    batch = form != "single"
+    masks, t = sol[0].get_trace(raw=True)
+    its = out[0]
+    agg = collections.defaultdict(lambda: [0, 0.0])
+    for m, d in zip(masks[1:], np.diff(t)):
+        name = ("+".join(pagd.PHASES[p] for p in range(32) if m >> p & 1) if batch else pagd.PHASES[m])
+        agg[name][0] += 1
+        agg[name][1] += d
+    tot = t[-1]
+    print(f"{form}: {steps} steps, {tot / steps:.1f} us/step, {(len(t) - 1) / steps:.1f} phases/step, "
+          f"{float(np.mean(its)):.2f} evaluations/step")
+    for k, (n, sec) in sorted(agg.items(), key=lambda x: -x[1][1]):
+        print(f"  {k:24s} per step {n / steps:6.2f}  mean {sec / n:9.2f} us  share {100 * sec / tot:5.1f}%")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -298,6 +351,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and 3D lines")
     ap.add_argument("--no-studies", action="store_true", help="skip the PGD and cost-to-accuracy studies")
+    ap.add_argument("--profile", choices=FORMS, help="one warm-up launch and one launch of --steps steps of "
+                    "a form, then exit (the launch for ncu -s 1 -c 1)")
+    ap.add_argument("--trace", choices=FORMS, help="print the phase trace of --steps steps of a form")
     args = ap.parse_args()
     w = I.WORKLOADS[args.workload]
 
@@ -319,6 +375,8 @@ def main():
 
     W = max(3, args.warmup)
     K = max(1, args.steps)
+    if args.profile or args.trace:
+        return profile_form(torch, pagd, args.profile or args.trace, w, K, W, bool(args.trace))
     S = pagd.solver_for(w)
     u0 = torch.from_numpy(w.u0(1 + rank)).cuda()
     S.set_state(u0)

@@ -11,8 +11,9 @@
 // instance i covers [G_i, G_i + units_i * q_i), q_i the points a unit touches
 // (2 n1 for a row unit of two rows, n0 for a column), and warp w of the grid
 // takes the slice [C_w, C_{w+1}), C_w = floor(total * w / NW), so every warp
-// gets about the same number of points whatever the mix of sizes.  Warps of one
-// CTA are adjacent on the axis, so a CTA works on few instances per phase.
+// gets about the same number of points whatever the mix of sizes.  Each warp
+// runs the members on its own slice; reductions are per warp (lane 0 publishes
+// with an atomic), so warps never wait for each other inside a global phase.
 #pragma once
 #include "kernels.cuh"
 
@@ -91,10 +92,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pagd_batch_kernel(BatchParams 
         __syncthreads();
         const long long total = G[B.count];
         if (total == 0) break;
-        // instances on this CTA's slice [C_{wpb b}, C_{wpb (b+1)})
-        const long long clo = cost_start((long long)blockIdx.x * wpb, total, nw);
-        const long long chi = cost_start((long long)(blockIdx.x + 1) * wpb, total, nw);
-        int lo = 0, hi = B.count;  // first instance with G[i+1] > clo
+        // the members on this warp's slice [C_gw, C_{gw+1}) of the cost axis; the
+        // warps of a CTA need not agree (phases hold no CTA-wide barrier)
+        const long long clo = cost_start(gw, total, nw), chi = cost_start(gw + 1, total, nw);
+        int lo = 0, hi = B.count;  // first member with G[i+1] > clo
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             if (G[mid + 1] > clo) hi = mid;

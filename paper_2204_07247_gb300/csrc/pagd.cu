@@ -841,8 +841,7 @@ template <class T> static void batch_exec_host(const Params& P, const Ctl& c, co
     }
 }
 // the batched kernel's schedule, one CTA after the other and within a CTA one
-// warp (of one thread) after the other, kEmuBatchWarps warps per CTA so that
-// warps which own nothing of an instance their CTA works on are exercised
+// warp (of one thread) after the other, kEmuBatchWarps warps per CTA
 template <class T> static pagd_status batch_launch(pagd_batch* b, const BatchParams& B) {
     std::vector<char> sm(b->smem + 64);
     char* base = (char*)(((uintptr_t)sm.data() + 15) & ~(uintptr_t)15);
@@ -873,20 +872,20 @@ template <class T> static pagd_status batch_launch(pagd_batch* b, const BatchPar
         if (total == 0) break;
         for (int blk = 0; blk < b->grid; blk++) {
             blockIdx.x = (unsigned)blk;
-            const long long clo = cost_start((long long)blk * wpb, total, nw);
-            const long long chi = cost_start((long long)(blk + 1) * wpb, total, nw);
-            for (int i = 0; i < B.count; i++) {
-                if (G[i + 1] <= clo || G[i] >= chi || G[i + 1] == G[i]) continue;
-                const Params& P = B.PI[i];
-                for (int wi = 0; wi < wpb; wi++) {
-                    threadIdx.x = (unsigned)wi;
+            for (int wi = 0; wi < wpb; wi++) {
+                threadIdx.x = (unsigned)wi;
+                const long long gw = (long long)blk * wpb + wi;
+                const long long clo = cost_start(gw, total, nw), chi = cost_start(gw + 1, total, nw);
+                for (int i = 0; i < B.count; i++) {
+                    if (G[i + 1] <= clo || G[i] >= chi || G[i + 1] == G[i]) continue;
+                    const Params& P = B.PI[i];
                     Tw t{t64, t32, B.logtw, 0, 0, 0, 0};
-                    batch_split(t, (long long)blk * wpb + wi, nw, total, G[i], G[i + 1] - G[i],
-                                phase_units(P, ctl[i].ph), unit_cost(P, ctl[i].ph));
+                    batch_split(t, gw, nw, total, G[i], G[i + 1] - G[i], phase_units(P, ctl[i].ph),
+                                unit_cost(P, ctl[i].ph));
                     batch_exec_host<T>(P, ctl[i], t, wsm, red);
                 }
-                threadIdx.x = 0;
             }
+            threadIdx.x = 0;
         }
         for (int i = 0; i < B.count; i++)
             if (ctl[i].ph != PH_DONE) ctl_advance<T>(B.PI[i], ctl[i]);

@@ -298,52 +298,16 @@ __device__ __forceinline__ double Fwell(double z, double tau) {
 
 __device__ __forceinline__ double nanmax(double a, double b) { return (b > a || b != b) ? b : a; }
 
-// The thread that publishes a block reduction.  The emulation runs the warps
-// of a CTA one after another, each reduction returning that warp's own
-// partial, so there every warp publishes its partial.
-__device__ __forceinline__ bool red_leader() {
-#ifdef PAGD_EMU
-    return true;
-#else
-    return threadIdx.x == 0;
-#endif
-}
-
-// block-wide reductions; the result is valid in thread 0.  All threads call.
-__device__ __forceinline__ double block_max(double v, double* red) {
-#ifdef PAGD_EMU
-    (void)red;
-    return v;
-#else
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    v = warp_max(v);
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        v = (lane < nw) ? red[lane] : 0.0;
-        v = warp_max(v);
-    }
-    return v;
-#endif
-}
-
-__device__ __forceinline__ double block_sum(double v, double* red) {
-#ifdef PAGD_EMU
-    (void)red;
-    return v;
-#else
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+// Grid-wide reductions: every warp reduces its lanes with shuffles and lane 0
+// publishes the partial with an atomic, so no CTA-wide barrier is needed
+// inside a phase (warps of a CTA never wait for each other's units).
+__device__ __forceinline__ void publish_sum(double* a, double v) {
     v = warp_sum(v);
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        v = (lane < nw) ? red[lane] : 0.0;
-        v = warp_sum(v);
-    }
-    return v;
-#endif
+    if ((threadIdx.x % kWarp) == 0) atomicAdd(a, v);
+}
+__device__ __forceinline__ void publish_max(unsigned long long* a, double v) {
+    v = warp_max(v);
+    if ((threadIdx.x % kWarp) == 0) atomicMax(a, dbl_bits(v));
 }
 
 // ---------------------------------------------------------- pass templates
@@ -938,16 +902,13 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
             }
         });
     if (!reb) {
-        s0 = block_sum(s0, red);
-        if (red_leader()) atomicAdd(&P.sc->beta_sum[bank][0], s0);
+        publish_sum(&P.sc->beta_sum[bank][0], s0);
         if (!pfc) {
-            s2 = block_sum(s2, red);
-            if (red_leader()) atomicAdd(&P.sc->beta_sum[bank][1], s2);
+            publish_sum(&P.sc->beta_sum[bank][1], s2);
         }
     }
     if (acc) {
-        dmass = block_sum(dmass, red);
-        if (red_leader()) atomicAdd(&P.mass[1], dmass);
+        publish_sum(&P.mass[1], dmass);
     }
 }
 
@@ -1255,10 +1216,8 @@ __device__ void phase_R(const Params& P, const Ctl& c, const Tw& tw, char* smem,
                 out[1] = -e2 * (df2 * s.lb + (f2n - eta1) * ly) + df2 * f1n + (f2b - eta2) * df1;
             }
         });
-    const double amx = block_max((double)amax, red);
-    if (red_leader()) atomicMax(&P.norms[(size_t)bank * P.nslots + c.ev], dbl_bits(amx));
-    asum = block_sum(asum, red);
-    if (red_leader()) atomicAdd(&P.sums[(size_t)bank * P.nslots + c.ev], asum);
+    publish_max(&P.norms[(size_t)bank * P.nslots + c.ev], (double)amax);
+    publish_sum(&P.sums[(size_t)bank * P.nslots + c.ev], asum);
 }
 
 // Iteration column pass: ybar_hat, spectral residual (Eq. obj:G' with the
@@ -1341,8 +1300,7 @@ __device__ void phase_accept(const Params& P, const Ctl& c, const Tw& tw, double
         dmass += x - a;
         if (P.out_real) P.out_real[p] = x;
     }
-    dmass = block_sum(dmass, red);
-    if (red_leader()) atomicAdd(&P.mass[1], dmass);
+    publish_sum(&P.mass[1], dmass);
     if (leader(tw)) {
         P.stats[c.step].iters = c.ev;
         P.stats[c.step].status = ST_OK;
@@ -1404,8 +1362,7 @@ __device__ void phase_en_r(const Params& P, const Tw& tw, char* smem, double* re
                                  if (pfc) acc += 0.25 * u * u * u * u + 0.5 * (1.0 - P.eps) * u * u;
                              });
     if (pfc) {
-        acc = block_sum(acc, red);
-        if (red_leader()) atomicAdd(&P.sc->red[0], acc);
+        publish_sum(&P.sc->red[0], acc);
     }
 }
 template <int NF>
@@ -1426,8 +1383,7 @@ __device__ void phase_en_c(const Params& P, const Tw& tw, char* smem, double* re
                              out[0] = double2{-kap * in[0].x, -kap * in[0].y};
                          }
                      });
-    acc = block_sum(acc, red);
-    if (red_leader()) atomicAdd(&P.sc->red[1], acc);
+    publish_sum(&P.sc->red[1], acc);
 }
 template <int NF>
 __device__ void phase_en_r2(const Params& P, const Tw& tw, char* smem, double* red) {
@@ -1439,16 +1395,14 @@ __device__ void phase_en_r2(const Params& P, const Tw& tw, char* smem, double* r
                                  const double w = e2 * in[0] - dF1(u, P.tau);
                                  acc += 0.5 * w * w - P.eta2 * Fwell(u, P.tau);
                              });
-    acc = block_sum(acc, red);
-    if (red_leader()) atomicAdd(&P.sc->red[0], acc);
+    publish_sum(&P.sc->red[0], acc);
 }
 inline __device__ void phase_mass(const Params& P, const Tw& tw, double* red) {
     double acc = 0.0;
     const long long gt = thread_rank(tw);
     const long long gs = thread_count(tw);
     for (long long p = gt; p < P.npts; p += gs) acc += P.in_real[p];
-    acc = block_sum(acc, red);
-    if (red_leader()) atomicAdd(&P.sc->red[0], acc);
+    publish_sum(&P.sc->red[0], acc);
 }
 
 // ------------------------------------------------------ linear IMEX step
