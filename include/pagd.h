@@ -106,6 +106,18 @@ pagd_status pagd_set_state(pagd_solver* s, const double* u0_dev);
 pagd_status pagd_step(pagd_solver* s, double* u_dev, double dt, double tol, int* iters_out,
                       double* resid_out);
 
+/* One implicit step (as pagd_step) started from a caller's initial iterate,
+ * e.g. a learned predictor of u^{n+1}.  The guess (device, n_pts doubles) is
+ * first moved to the mass of u^n (the discrete solution keeps it and every
+ * PAGD update has zero mean).  Then the first direction d_0 of Algorithm 2 is
+ * evaluated at the moved guess and at the extrapolated guess of Sec. 3.4.2,
+ * with the averaged Newton constants of each, and PAGD continues from the one
+ * with the smaller ||d_0||_inf; both evaluations count in iters_out.
+ * used_guess_out (nullable): 1 if the caller's guess was kept.  Implicit
+ * schemes only (PAGD_EINVAL for LBDF2 / LMP).  Synchronises the stream. */
+pagd_status pagd_step_with_guess(pagd_solver* s, double* u_dev, const double* guess_dev, double dt, double tol,
+                                 int* iters_out, double* resid_out, int* used_guess_out);
+
 /* Advance nsteps steps of size dt in one device launch per chunk of at most
  * 4096 steps.  u_dev (nullable) receives the final field.  iters_out and
  * resid_out (nullable, host arrays of nsteps) receive per-step values.

@@ -492,7 +492,7 @@ static Params run_params(const pagd_solver* s, double* u_out, double dt, int nst
 // per-step results, the solver's step count and history slot.  bar_error: the
 // launch's device barrier gave up.
 static pagd_status run_finish(pagd_solver* s, const Params& P, double dt, int nsteps, int* iters, double* resid,
-                              bool bar_error) {
+                              bool bar_error, int* used_guess = nullptr) {
     const bool imex = s->scheme == PAGD_LBDF2 || s->scheme == PAGD_LMP;
     Scal sc;
     pagd_status st = dcopy(s, &sc, P.sc, sizeof(Scal));
@@ -510,6 +510,7 @@ static pagd_status run_finish(pagd_solver* s, const Params& P, double dt, int ns
     for (int i = 0; i < nrec && i < nsteps; i++) {
         if (iters) iters[i] = stats[i].iters;
         if (resid) resid[i] = stats[i].resid;
+        if (used_guess) used_guess[i] = stats[i].used_guess;
     }
     if (ndone > 0) {
         s->step += ndone;
@@ -554,6 +555,21 @@ pagd_status pagd_run(pagd_solver* s, double* u_dev, double dt, int nsteps, doubl
         done += c;
     }
     return PAGD_OK;
+}
+
+pagd_status pagd_step_with_guess(pagd_solver* s, double* u_dev, const double* guess_dev, double dt, double tol,
+                                 int* iters_out, double* resid_out, int* used_guess_out) {
+    if (!s) return PAGD_EINVAL;
+    if (!u_dev || !guess_dev) return fail(s, PAGD_EINVAL, "null output or guess");
+    if (!s->ws || !s->have_state) return fail(s, PAGD_ESTATE, "workspace and state must be set first");
+    if (s->scheme == PAGD_LBDF2 || s->scheme == PAGD_LMP)
+        return fail(s, PAGD_EINVAL, "an initial iterate applies to the implicit schemes only");
+    if (!(dt > 0.0) || !std::isfinite(dt) || !(tol >= 0.0)) return fail(s, PAGD_EINVAL, "bad dt / tol");
+    Params P = run_params(s, u_dev, dt, 1, tol);
+    P.guess = guess_dev;
+    pagd_status st = run_program(s, P);
+    if (st != PAGD_OK) return st;
+    return run_finish(s, P, dt, 1, iters_out, resid_out, false, used_guess_out);
 }
 
 pagd_status pagd_step(pagd_solver* s, double* u_dev, double dt, double tol, int* iters_out, double* resid_out) {

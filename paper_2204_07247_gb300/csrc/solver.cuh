@@ -45,7 +45,7 @@ enum Phase {
     PH_B, PH_C, PH_D, PH_E, PH_R1, PH_CI, PH_RI, PH_ACCEPT, PH_FAIL,
     PH_FWD_R, PH_FWD_C, PH_INV_C, PH_INV_R, PH_EN_R, PH_EN_C, PH_EN_R2, PH_MASS,
     PH_IM_R0, PH_IM_C0, PH_IM_R1, PH_IM_C1, PH_IM_R2,
-    PH_MF, PH_MI,
+    PH_MF, PH_MI, PH_GS,
     PH_DONE
 };
 
@@ -54,13 +54,16 @@ struct Scal {
     unsigned long long bar_count;  // grid barrier arrivals (monotonic)
     int bar_error, flags;
     int status, steps_done, fail_step, ntrace;
-    double beta_sum[2][2];  // [step parity][field]
+    // averaged-Newton grid sums [bank][field]: banks 0 / 1 by step parity, 2 / 3
+    // for the evaluations at a caller's initial guess (probe, re-run)
+    double beta_sum[4][2];
     double red[4];
 };
 
 struct StepStat {
     int iters, status;
     double resid;
+    int used_guess, pad;
 };
 
 constexpr int kMaxK = 3;        // fields per pass
@@ -136,6 +139,8 @@ struct Params {
     unsigned long long* norms;
     double* sums;
     StepStat* stats;
+    // caller's initial iterate for the first step of the run (nullable)
+    const double* guess;
     // program input / output
     const double* in_real;
     double* out_real;
@@ -147,6 +152,11 @@ struct Ctl {
     int ph, step, it, ev, lastev, cur, rech, fail, best_ev;
     int after, mk, m64;  // 3D middle pass: the phase after it, its fields, FP64 buffers
     int gok;             // GH64 holds this step's g_hat (an exact evaluation made it)
+    int bsel;            // bank of the averaged-Newton sums of the current evaluation
+    int gmode;           // caller's guess: 0 none, 1 probing it, 2 probing the extrapolation,
+                         // 3 iterating from it, 4 iterating from the extrapolation
+    double gnorm;        // ||d_0||_inf at the caller's guess
+    int acc_used;        // the step pending acceptance started from the caller's guess
     int acc, acc_cur, acc_it, acc_lastev, acc_ev, reb, ereb, inc, ref_ok, exact_done;
     double resid, base_nrm, best_nrm, acc_resid;
 };
@@ -234,10 +244,9 @@ struct Beta {
 
 // Averaged Newton constants (Sec. 3.4.1) from the grid sums over the argument
 // of the initial guess of this step.
-__device__ __forceinline__ Beta betas(const Params& P, const StepK& k, int step) {
+__device__ __forceinline__ Beta betas(const Params& P, const StepK& k, int bank) {
     Beta B;
     const double inv = P.inv_npts;
-    const int bank = step & 1;
     B.m2 = k.m2;
     const double s0 = ldcg(&P.sc->beta_sum[bank][0]) * inv;
     if (P.model == M_PFC) {
@@ -822,6 +831,7 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
         P.stats[c.step - 1].iters = c.acc_ev;
         P.stats[c.step - 1].status = ST_OK;
         P.stats[c.step - 1].resid = c.acc_resid;
+        P.stats[c.step - 1].used_guess = c.acc_used;
         P.sc->steps_done = c.step;
     }
     double s0 = 0.0, s2 = 0.0;
@@ -839,6 +849,8 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
     const double Ai = k.Ai;
     // an exact re-evaluation within a step reuses the step's g_hat (GH64)
     const bool gcached = !INC && reb && c.gok;
+    const bool use_guess = !reb && (c.gmode == 1 || c.gmode == 3);
+    const double gshift = use_guess ? ldcg(&P.sc->red[2]) * P.inv_npts : 0.0;
     const int kout = ((INC && reb) || gcached) ? kb - 1 : kb;
     rowp<double, TO, NF>(
         P, tw, 0, kout, (const double2*)nullptr, dst, smem,
@@ -865,7 +877,9 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
                     U0[p] = a;
                     dmass += a - s.b;
                 }
-                const double x0 = a + k.rho * (a - b);
+                // initial iterate (Sec. 3.4.2): extrapolation, or the caller's
+                // guess moved to the mass of u^n
+                const double x0 = use_guess ? P.guess[p] + gshift : a + k.rho * (a - b);
                 vb = k.thv * x0 + (1.0 - k.thv) * a;
                 g = k.b * a + k.c * b - k.gun * a;
                 P.G64[p] = g;
@@ -902,9 +916,9 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
             }
         });
     if (!reb) {
-        publish_sum(&P.sc->beta_sum[bank][0], s0);
+        publish_sum(&P.sc->beta_sum[c.bsel][0], s0);
         if (!pfc) {
-            publish_sum(&P.sc->beta_sum[bank][1], s2);
+            publish_sum(&P.sc->beta_sum[c.bsel][1], s2);
         }
     }
     if (acc) {
@@ -943,7 +957,7 @@ __device__ void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem)
         P.mass[1] = 0.0;
     }
     const StepK& k = step_coeffs(P, c.step);
-    const Beta B = betas(P, k, c.step);
+    const Beta B = betas(P, k, c.bsel);
     const int kb = k_base(P.model);
     const double iM = 1.0 / P.M;
     const double e4 = P.eps * P.eps * P.eps * P.eps;
@@ -1014,7 +1028,7 @@ __device__ void phase_D(const Params& P, const Tw& tw, char* smem) {
 template <class T, int NF>
 __device__ void phase_E(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     const StepK& k = step_coeffs(P, c.step);
-    const Beta B = betas(P, k, c.step);
+    const Beta B = betas(P, k, c.bsel);
     const double e2 = P.eps * P.eps;
     const double l1 = lam_at(P, 1);
     // the direction (and Lap of the first correction) are small: inverse in T
@@ -1049,7 +1063,7 @@ __device__ void phase_CN(const Params& P, const Ctl& c, const Tw& tw, char* smem
         P.mass[1] = 0.0;
     }
     const StepK& k = step_coeffs(P, c.step);
-    const Beta B = betas(P, k, c.step);
+    const Beta B = betas(P, k, c.bsel);
     const bool reb = c.ereb != 0;
     const int kb = k_base(P.model);
     const int kin = reb ? kb - 1 : kb;
@@ -1134,7 +1148,7 @@ template <class T, int NF>
 __device__ void phase_EN(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     using C = cx<T>;
     const StepK& k = step_coeffs(P, c.step);
-    const Beta B = betas(P, k, c.step);
+    const Beta B = betas(P, k, c.bsel);
     const double e2 = P.eps * P.eps;
     const double l1 = lam_at(P, 1);
     const long long H = P.H;
@@ -1227,7 +1241,7 @@ template <class T, int NF>
 __device__ void phase_CI(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     using C = cx<T>;
     const StepK& k = step_coeffs(P, c.step);
-    const Beta B = betas(P, k, c.step);
+    const Beta B = betas(P, k, c.bsel);
     const int it = c.it;
     const T l = (T)lam_at(P, it), ln = (T)lam_at(P, it + 1), ts = (T)k.ts;
     const C* scur = (const C*)P.SS[it & 1];
@@ -1305,6 +1319,7 @@ __device__ void phase_accept(const Params& P, const Ctl& c, const Tw& tw, double
         P.stats[c.step].iters = c.ev;
         P.stats[c.step].status = ST_OK;
         P.stats[c.step].resid = c.resid;
+        P.stats[c.step].used_guess = c.gmode == 1 || c.gmode == 3;
         P.sc->steps_done = c.step + 1;
     }
 }
@@ -1397,6 +1412,18 @@ __device__ void phase_en_r2(const Params& P, const Tw& tw, char* smem, double* r
                              });
     publish_sum(&P.sc->red[0], acc);
 }
+// Mass shift of the caller's initial guess: the discrete solution keeps the
+// mass of u^n and every PAGD update has zero mean, so the initial iterate is
+// the guess moved to that mass; red[2] = sum(u^n - guess).
+inline __device__ void phase_gs(const Params& P, const Ctl& c, const Tw& tw) {
+    double acc = 0.0;
+    const double* un = P.U[c.cur];
+    const long long gt = thread_rank(tw);
+    const long long gs = thread_count(tw);
+    for (long long p = gt; p < P.npts; p += gs) acc += un[p] - P.guess[p];
+    publish_sum(&P.sc->red[2], acc);
+}
+
 inline __device__ void phase_mass(const Params& P, const Tw& tw, double* red) {
     double acc = 0.0;
     const long long gt = thread_rank(tw);
@@ -1545,10 +1572,21 @@ __host__ __device__ inline Ctl ctl_init(const Params& P) {
     c.ereb = 0;
     c.after = PH_DONE; c.mk = 0; c.m64 = 1;
     c.gok = 0;
+    c.bsel = 0;  // bank of the launch's first step (c.step & 1)
+    c.gmode = 0;
+    c.gnorm = 0.0;
+    c.acc_used = 0;
     c.inc = inc_eval(P, c.ref_ok, P.step0, 1);
     c.resid = 0.0; c.base_nrm = 0.0; c.best_nrm = 0.0; c.acc_resid = 0.0;
     switch (P.prog) {
-        case PROG_RUN: c.ph = (P.nsteps > 0) ? PH_B : PH_DONE; break;
+        case PROG_RUN:
+            c.ph = (P.nsteps > 0) ? PH_B : PH_DONE;
+            if (P.nsteps > 0 && P.guess) {
+                c.ph = PH_GS;  // the guess's mass shift first
+                c.gmode = 1;
+                c.bsel = 2;
+            }
+            break;
         case PROG_IMEX: c.ph = (P.nsteps > 0) ? PH_IM_R0 : PH_DONE; break;
         case PROG_FFT_FWD: c.ph = PH_FWD_R; break;
         case PROG_FFT_INV: c.ph = PH_INV_C; break;
@@ -1627,8 +1665,11 @@ __device__ void ctl_step(const Params& P, Ctl& c) {
     const bool t64 = sizeof(T) == 8;
     const int bank = c.step & 1;
     switch (c.ph) {
+        case PH_GS: c.ph = PH_B; break;
         case PH_B:
-            if (!c.reb) { c.ev = 0; c.rech = 0; }
+            // a new step restarts the counts, except the repeated new-step
+            // evaluations of the guess probe (they count in the step's cost)
+            if (!c.reb && c.gmode != 2 && c.gmode != 3) { c.ev = 0; c.rech = 0; }
             c.ereb = c.reb;  // the evaluation started by B is a rebase (kept through C..E)
             c.acc = 0;
             c.reb = 0;
@@ -1641,7 +1682,7 @@ __device__ void ctl_step(const Params& P, Ctl& c) {
         case PH_E:
             c.ref_ok = 1;
             if (!c.inc) c.exact_done = 1;
-            if (!(fabs(ldcg(&P.sc->beta_sum[bank][0])) + fabs(ldcg(&P.sc->beta_sum[bank][1])) <= 1.0e300)) {
+            if (!(fabs(ldcg(&P.sc->beta_sum[c.bsel][0])) + fabs(ldcg(&P.sc->beta_sum[c.bsel][1])) <= 1.0e300)) {
                 c.fail = ST_ENAN;  // non-finite initial guess
                 c.ph = PH_FAIL;
                 break;
@@ -1675,10 +1716,13 @@ __device__ void ctl_step(const Params& P, Ctl& c) {
                     c.acc_lastev = c.lastev;
                     c.acc_ev = c.ev;
                     c.acc_resid = nrm;
+                    c.acc_used = c.gmode == 1 || c.gmode == 3;
                     c.step++;
                     c.cur ^= 1;
                     c.exact_done = 0;
                     c.gok = 0;
+                    c.gmode = 0;
+                    c.bsel = c.step & 1;
                     c.inc = t64 ? 0 : inc_eval(P, c.ref_ok, P.step0 + c.step, 1);
                     c.ph = PH_B;
                 } else {
@@ -1687,6 +1731,19 @@ __device__ void ctl_step(const Params& P, Ctl& c) {
             } else if (c.ev >= P.max_iter || c.ev + 1 >= P.nslots) {
                 c.fail = ST_ENOCONV;
                 c.ph = PH_FAIL;
+            } else if (c.ph == PH_R1 && c.gmode == 1) {
+                // first direction at the caller's guess; now the same at the
+                // extrapolated guess, and the smaller of the two is kept
+                c.gnorm = nrm;
+                c.gmode = 2;
+                c.bsel = bank;
+                c.inc = t64 ? 0 : inc_eval(P, c.ref_ok, P.step0 + c.step, 1);
+                c.ph = PH_B;
+            } else if (c.ph == PH_R1 && c.gmode == 2 && nrm > c.gnorm) {
+                c.gmode = 3;  // back to the caller's guess
+                c.bsel = 3;
+                c.inc = t64 ? 0 : inc_eval(P, c.ref_ok, P.step0 + c.step, 1);
+                c.ph = PH_B;
             } else if ((fp32_norm && (nrm <= P.tol || nrm <= kRebaseRatio * c.base_nrm ||
                                       c.ev - c.best_ev >= kStagnation)) ||
                        (inc_norm && nrm <= P.tol)) {
@@ -1753,6 +1810,7 @@ __device__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* sm
         case PH_EN_C: phase_en_c<NF>(P, tw, smem, red); break;
         case PH_EN_R2: phase_en_r2<NF>(P, tw, smem, red); break;
         case PH_MASS: phase_mass(P, tw, red); break;
+        case PH_GS: phase_gs(P, c, tw); break;
         case PH_MF:
             if (c.m64) mid_pass<double, -1>(P, tw, c.mk, P.NB64, P.X64, smem);
             else mid_pass<T, -1>(P, tw, c.mk, (const cx<T>*)P.NB, (cx<T>*)P.X, smem);

@@ -26,7 +26,7 @@ STATUS = {0: "PAGD_OK", 1: "PAGD_EINVAL", 2: "PAGD_ENOMEM", 3: "PAGD_ECUDA", 4: 
 SCHEMES = {"bdf2": BDF2, "mp": MP, "lbdf2": LBDF2, "lmp": LMP}
 PRECISIONS = {"fp64": FP64, "fp32_mixed": FP32_MIXED}
 EXPORTS = ("pagd_default_opts", "pfc_init", "fch_init", "pagd_workspace_size", "pagd_set_workspace",
-           "pagd_set_state", "pagd_step", "pagd_run", "pagd_run_host", "pagd_energy", "pagd_mass",
+           "pagd_set_state", "pagd_step", "pagd_step_with_guess", "pagd_run", "pagd_run_host", "pagd_energy", "pagd_mass",
            "pagd_fft_r2c", "pagd_fft_c2r", "pagd_get_state", "pagd_step_static", "pagd_set_trace",
            "pagd_get_trace", "pagd_last_error", "pagd_destroy", "pagd_batch_create",
            "pagd_batch_workspace_size", "pagd_batch_set_workspace", "pagd_batch_run",
@@ -61,6 +61,7 @@ def _declare(lib):
         "pagd_set_workspace": [P, P, ctypes.c_size_t],
         "pagd_set_state": [P, P],
         "pagd_step": [P, P, d, d, IP, D],
+        "pagd_step_with_guess": [P, P, P, d, d, IP, D, IP],
         "pagd_run": [P, P, d, i, d, IP, D],
         "pagd_run_host": [P, P, P, d, i, d, IP, D],
         "pagd_energy": [P, P, D],
@@ -225,6 +226,18 @@ class Solver:
         self._check(self.lib.pagd_step(self._h, self._ptr(u_out), dt, tol, ctypes.byref(it),
                                        ctypes.byref(r)), "step")
         return it.value, r.value
+
+    def step_with_guess(self, u_out, guess, dt, tol):
+        """One implicit step from the caller's initial iterate `guess` (kept only
+        if its first PAGD direction is smaller than the extrapolation's);
+        returns (evaluations, accepted residual, guess used)."""
+        it = ctypes.c_int()
+        r = ctypes.c_double()
+        used = ctypes.c_int()
+        self._check(self.lib.pagd_step_with_guess(self._h, self._ptr(u_out), self._ptr(guess), dt, tol,
+                                                  ctypes.byref(it), ctypes.byref(r), ctypes.byref(used)),
+                    "step_with_guess")
+        return it.value, r.value, bool(used.value)
 
     def run(self, dt, nsteps, tol, u_out=None):
         iters = (ctypes.c_int * max(nsteps, 1))()
