@@ -444,6 +444,11 @@ def main():
         extra["pgd_vs_pagd"] = bench_pgd_vs_pagd(torch, pagd, w, 100)
         extra["cost_to_accuracy"] = bench_cost_to_accuracy(torch, pagd, w, 0.064,
                                                            [4e-3, 2e-3, 1e-3, 5e-4])
+    if not args.no_forms and rank == 0:
+        # learned initial iterate (FCH 512^2): train on solver trajectories, then
+        # PAGD from the network's proposal vs from the extrapolation
+        from paper_2204_07247_gb300 import learned
+        extra["learned"] = learned.run_study(torch, I.FCH512, list(range(1000, 1008)), [0, 1], 64, 16, 300)
     if not args.no_forms:
         extra["batched"] = bench_batch(torch, pagd, I.PFC_BATCH96, I.PFC_BATCH96.steps, W, 20,
                                        ITER_BYTES_2D_PFC, peak, rank, world, dist)

@@ -19,9 +19,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpagd.so")
 EMU = os.path.join(BUILD, "libpagd_emu.so")
 # host code, one kernel translation unit per fixed line length (0: runtime length)
-# and the batched kernel per iteration precision
+# the batched kernel per iteration precision, and the learned-guess network
 SOURCES = ["pagd.cu", "pagd_k0.cu", "pagd_k64.cu", "pagd_k128.cu", "pagd_k256.cu", "pagd_k512.cu",
-           "pagd_batch_f32.cu", "pagd_batch_f64.cu"]
+           "pagd_batch_f32.cu", "pagd_batch_f64.cu", "sno.cu"]
 HEADERS = ["compat.cuh", "fft.cuh", "solver.cuh", "kernels.cuh", "batch.cuh"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
@@ -29,6 +29,7 @@ GENCODE = "arch=compute_103a,code=sm_103a"
 def _deps():
     files = [os.path.join(CSRC, f) for f in SOURCES + HEADERS]
     files.append(os.path.join(os.path.dirname(HERE), "include", "pagd.h"))
+    files.append(os.path.join(os.path.dirname(HERE), "include", "pagd_sno.h"))
     return files
 
 

@@ -95,7 +95,13 @@ PFC3D256 = Workload("pfc3d_256_bdf2_fp32mixed", "pfc", (256, 256, 256), (64 * ma
                     scheme="bdf2", precision="fp32_mixed", dt=0.5, steps=200, tol=1e-8, mean=-0.25,
                     amp=0.1, seeds=(1, 2))
 
-WORKLOADS = {w.name: w for w in (PFC64, FCH256, PFC3D256)}
+# FCH 2D 512x512 on [0, 4 pi]^2, parameters as the 256^2 workload (the
+# learned-initial-iterate workload).
+FCH512 = Workload("fch2d_512_bdf2_fp32mixed", "fch", (512, 512), (FOURPI, FOURPI), eps=0.1, eta1=0.1, eta2=0.1,
+                  tau=0.0, scheme="bdf2", precision="fp32_mixed", dt=1e-3, steps=2000, tol=1e-8, mean=-0.3,
+                  amp=0.05)
+
+WORKLOADS = {w.name: w for w in (PFC64, FCH256, PFC3D256, FCH512)}
 
 
 @dataclass

@@ -1,0 +1,115 @@
+"""The learned-guess form: trajectories from the solver, training of the
+spectral neural operator (sno.SNO, own CUDA forward / backward / Adam
+kernels), and its evaluation through pagd_step_with_guess against the plain
+extrapolated initial iterate.
+
+A training sample is a triple (u^{n-1}, u^n, u^{n+1}) of consecutive accepted
+states of one trajectory; the network learns u^{n+1} minus the extrapolation
+u^n + rho (u^n - u^{n-1}) (rho = 1 at a fixed dt).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import inputs as I
+from . import pagd
+from . import sno as SB
+
+
+def trajectories(torch, w, seeds, steps, skip=2):
+    """[len(seeds), steps + 2, n0, n1] accepted states (FP64, device), after
+    `skip` steps from u0 (the first steps of a noisy start are not typical)."""
+    out = torch.empty((len(seeds), steps + 2) + tuple(w.n), dtype=torch.float64, device="cuda")
+    for i, seed in enumerate(seeds):
+        S = pagd.solver_for(w)
+        S.set_state(torch.from_numpy(w.u0(seed)).cuda())
+        if skip:
+            S.run(w.dt, skip, w.tol)
+        for k in range(steps + 2):
+            if k:
+                S.run(w.dt, 1, w.tol, out[i, k])
+            else:
+                out[i, 0].copy_(S.get_state()[0])
+    return out
+
+
+def scales(torch, traj):
+    """Input and output scales from the data: 1 / rms(u^n - u^{n-1}) and
+    rms(u^{n+1} - extrapolation)."""
+    d1 = traj[:, 1:] - traj[:, :-1]
+    r = traj[:, 2:] - (2 * traj[:, 1:-1] - traj[:, :-2])
+    return 1.0 / float(torch.sqrt((d1 ** 2).mean())), float(torch.sqrt((r ** 2).mean()))
+
+
+def train(torch, net, traj, iters, batch, lr, s_in, s_out, seed=0):
+    """Adam on random minibatches of triples; returns the loss history."""
+    rng = np.random.default_rng(seed)
+    nt, nk = traj.shape[0], traj.shape[1] - 2
+    hist = []
+    for it in range(iters):
+        pick = rng.integers(0, nt * nk, size=batch)
+        ti, ki = pick // nk, pick % nk
+        unm1 = traj[ti, ki].contiguous()
+        un = traj[ti, ki + 1].contiguous()
+        tgt = traj[ti, ki + 2].contiguous()
+        loss, _ = net.loss_grad(un, unm1, tgt, 1.0, s_in, s_out)
+        net.adam(lr)
+        hist.append(loss)
+    return hist
+
+
+def evaluate(torch, w, net, seeds, steps, s_in, s_out, skip=2):
+    """PAGD evaluations per step and device time per step, from the
+    extrapolated initial iterate (plain) and from the network's proposal
+    (learned, through pagd_step_with_guess; inference included)."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = {"plain": {"evals": [], "ms": 0.0}, "learned": {"evals": [], "ms": 0.0, "used": 0}}
+    for seed in seeds:
+        for form in ("plain", "learned"):
+            S = pagd.solver_for(w)
+            S.set_state(torch.from_numpy(w.u0(seed)).cuda())
+            S.run(w.dt, skip + 1, w.tol)
+            out = torch.empty(w.n, dtype=torch.float64, device="cuda")
+            un, unm1, _ = S.get_state()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(steps):
+                if form == "plain":
+                    its, _ = S.run(w.dt, 1, w.tol, out)
+                    res[form]["evals"].append(int(its[0]))
+                else:
+                    un, unm1, _ = S.get_state()
+                    g = net.predict(un, unm1, 1.0, s_in, s_out)
+                    its, _, used = S.step_with_guess(out, g, w.dt, w.tol)
+                    res[form]["evals"].append(int(its))
+                    res[form]["used"] += int(used)
+            e1.record()
+            torch.cuda.synchronize()
+            res[form]["ms"] += e0.elapsed_time(e1)
+    n = len(seeds) * steps
+    for form in res:
+        r = res[form]
+        r["evals_per_step"] = float(np.mean(r["evals"]))
+        r["steps_per_s"] = n / (r["ms"] / 1000.0)
+        del r["evals"]
+    return res
+
+
+def run_study(torch, w, train_seeds, test_seeds, steps_train, steps_test, iters, batch=4, lr=1e-3,
+              channels=16, layers=4, modes=(16, 16)):
+    """Collect, train, evaluate; a dict for the benchmark line."""
+    traj = trajectories(torch, w, train_seeds, steps_train)
+    s_in, s_out = scales(torch, traj)
+    net = SB.SNO(w.n, channels=channels, layers=layers, modes=modes, batch=batch, seed=1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    hist = train(torch, net, traj, iters, batch, lr, s_in, s_out)
+    e1.record()
+    torch.cuda.synchronize()
+    ev = evaluate(torch, w, net, test_seeds, steps_test, s_in, s_out)
+    del traj
+    return {"workload": w.name, "network": f"{layers} spectral layers, {channels} channels, "
+            f"{modes[0]}x{modes[1]} modes, GELU, FP32", "train": {"trajectories": len(train_seeds),
+            "steps": steps_train, "iters": iters, "batch": batch, "ms": e0.elapsed_time(e1),
+            "loss_first": hist[0], "loss_last": float(np.mean(hist[-10:]))},
+            "test": {"seeds": list(test_seeds), "steps": steps_test}, **ev}
