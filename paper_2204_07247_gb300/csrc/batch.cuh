@@ -42,11 +42,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pagd_batch_kernel(BatchParams 
     double2* t64 = (double2*)smem;
     float2* t32 = (float2*)(smem + (size_t)ntw * sizeof(double2));
     const int stride = kNMax >> B.logtw;
-    dcx* tdf = (dcx*)(smem + (size_t)ntw * (sizeof(double2) + sizeof(float2)));
     for (int m = threadIdx.x; m < ntw; m += blockDim.x) {
         t64[m] = B.tw64[m * stride];
         t32[m] = B.tw32[m * stride];
-        tdf[m] = B.twdf[m * stride];
     }
     Ctl* ctl = (Ctl*)(smem + tw_smem_bytes(B.logtw));
     long long* G = (long long*)(ctl + B.count);  // cost prefix, count + 1 entries
@@ -107,7 +105,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pagd_batch_kernel(BatchParams 
             const long long cost = G[i + 1] - G[i];
             if (cost == 0) continue;
             const Params& P = B.PI[i];
-            Tw t{t64, t32, tdf, B.logtw, 0, 0, 0, 0};
+            Tw t{t64, t32, B.logtw, 0, 0, 0, 0};
             batch_split(t, gw, nw, total, G[i], cost, phase_units(P, ctl[i].ph), unit_cost(P, ctl[i].ph));
             batch_exec<T>(P, ctl[i], t, wsm, red);
         }

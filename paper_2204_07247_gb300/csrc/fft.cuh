@@ -23,53 +23,9 @@ constexpr int kLogNMax = 10;
 constexpr int kNMax = 1 << kLogNMax;
 constexpr int kWarp = PAGD_WARP;
 
-// ---------------------------------------------------------------------------
-// Double-float ("FP32 pair") numbers: the value is hi + lo with |lo| at most
-// half an ulp of hi, about 48 significant bits.  Sums use the error-free
-// two-sum of Knuth and products the FMA-based two-product (Dekker's product
-// with a fused multiply-add), each followed by a renormalising fast two-sum, as
-// in the double-float arithmetic of Dekker (1971) and Hida, Li and Bailey (2001).
-// GB300 runs FP32 at about 60 times its FP64 rate, so transforms in this type
-// are FP64-grade (relative error ~1e-14) at a fraction of the FP64 cost.
-struct dfl {
-    float hi, lo;
-    __host__ __device__ constexpr dfl() : hi(0.f), lo(0.f) {}
-    __host__ __device__ constexpr dfl(float h, float l) : hi(h), lo(l) {}
-    __host__ __device__ constexpr dfl(int v) : hi((float)v), lo(0.f) {}
-    // exact split of a double's leading 48 bits (constants, pass boundaries)
-    __host__ __device__ constexpr dfl(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
-};
-__host__ __device__ __forceinline__ double to_double(dfl a) { return (double)a.hi + (double)a.lo; }
-__host__ __device__ __forceinline__ dfl df_two_sum(float a, float b) {
-    const float s = a + b;
-    const float bb = s - a;
-    return dfl(s, (a - (s - bb)) + (b - bb));
-}
-__host__ __device__ __forceinline__ dfl df_fast_two_sum(float a, float b) {  // |a| >= |b|
-    const float s = a + b;
-    return dfl(s, b - (s - a));
-}
-__host__ __device__ __forceinline__ dfl operator+(dfl a, dfl b) {
-    const dfl s = df_two_sum(a.hi, b.hi);
-    return df_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
-}
-__host__ __device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.hi, -a.lo); }
-__host__ __device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
-__host__ __device__ __forceinline__ dfl operator*(dfl a, dfl b) {
-    const float p = a.hi * b.hi;
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
-    return df_fast_two_sum(p, e);
-}
-struct dcx {
-    dfl x, y;
-};
-
 template <class T> struct V2;
 template <> struct V2<float> { using type = float2; };
 template <> struct V2<double> { using type = double2; };
-template <> struct V2<dfl> { using type = dcx; };
 template <class T> using cx = typename V2<T>::type;
 
 template <class C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }

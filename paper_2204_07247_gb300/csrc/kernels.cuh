@@ -68,15 +68,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pagd_kernel(Params P) {
     double2* t64 = (double2*)smem;
     float2* t32 = (float2*)(smem + (size_t)ntw * sizeof(double2));
     const int stride = kNMax >> P.logtw;
-    dcx* tdf = (dcx*)(smem + (size_t)ntw * (sizeof(double2) + sizeof(float2)));
     for (int m = threadIdx.x; m < ntw; m += blockDim.x) {
         t64[m] = P.tw64[m * stride];
         t32[m] = P.tw32[m * stride];
-        tdf[m] = P.twdf[m * stride];
     }
     __syncthreads();
     const int wpb = blockDim.x / kWarp;
-    const Tw tw{t64, t32, tdf, P.logtw, (int)(threadIdx.x / kWarp) * (int)gridDim.x + (int)blockIdx.x,
+    const Tw tw{t64, t32, P.logtw, (int)(threadIdx.x / kWarp) * (int)gridDim.x + (int)blockIdx.x,
                 (int)gridDim.x * wpb, 0, -1};
     char* wsm = smem + tw_smem_bytes(P.logtw);
     Ctl c = ctl_init(P);

@@ -49,7 +49,7 @@ struct pagd_solver {
     // layout
     long long npts;
     int h1, nslots, tsize;
-    size_t off[48];  // workspace offsets, indexed by the O_* enum
+    size_t off[32];
     size_t ws_bytes;
     char* ws;
     // launch plan
@@ -63,7 +63,7 @@ struct pagd_solver {
 
 enum {
     O_SC, O_NORMS, O_SUMS, O_STATS, O_TW64, O_TW32, O_U0, O_U1, O_VB, O_G64, O_VBT, O_LBT, O_DD0,
-    O_DD1, O_SS0, O_SS1, O_C0, O_NB, O_DB, O_CL64, O_NB64, O_DB64, O_MASS, O_TRACE, O_VR64, O_NR64, O_WR64, O_LB64, O_YB, O_X, O_X64, O_GH64, O_TWDF, O_END
+    O_DD1, O_SS0, O_SS1, O_C0, O_NB, O_DB, O_CL64, O_NB64, O_DB64, O_MASS, O_TRACE, O_VR64, O_NR64, O_WR64, O_LB64, O_YB, O_X, O_X64, O_GH64, O_END
 };
 
 static pagd_status fail(pagd_solver* s, pagd_status st, const char* msg) {
@@ -114,12 +114,10 @@ static void plan_layout(pagd_solver* s) {
     sz[O_NR64] = sizeof(double2) * H * 2;
     sz[O_WR64] = sizeof(double2) * H;
     sz[O_LB64] = sizeof(double) * N;
-    sz[O_YB] = sizeof(double) * N;
+    sz[O_YB] = (size_t)T * N;
     sz[O_X] = s->dim == 3 ? (size_t)2 * T * H * 3 : 0;
     sz[O_X64] = s->dim == 3 ? sizeof(double2) * H * 3 : 0;
     sz[O_GH64] = sizeof(double2) * H;
-    sz[O_TWDF] = sizeof(dcx) * kNMax;
-    static_assert(O_END <= (int)(sizeof(((pagd_solver*)nullptr)->off) / sizeof(size_t)), "offset table too small");
     size_t o = 0;
     for (int i = 0; i < O_END; i++) {
         s->off[i] = o;
@@ -177,7 +175,6 @@ static Params params_for(const pagd_solver* s, char* w) {
     P.stats = (StepStat*)(w + s->off[O_STATS]);
     P.tw64 = (const double2*)(w + s->off[O_TW64]);
     P.tw32 = (const float2*)(w + s->off[O_TW32]);
-    P.twdf = (const dcx*)(w + s->off[O_TWDF]);
     P.U[0] = (double*)(w + s->off[O_U0]);
     P.U[1] = (double*)(w + s->off[O_U1]);
     P.VB = (double*)(w + s->off[O_VB]);
@@ -239,13 +236,11 @@ template <class T> static pagd_status launch(pagd_solver* s, const Params& P) {
     const int ntw = 1 << P.logtw;
     double2* t64 = (double2*)base;
     float2* t32 = (float2*)(base + (size_t)ntw * sizeof(double2));
-    dcx* tdf = (dcx*)(base + (size_t)ntw * (sizeof(double2) + sizeof(float2)));
     for (int m = 0; m < ntw; m++) {
         t64[m] = P.tw64[m * (kNMax >> P.logtw)];
         t32[m] = P.tw32[m * (kNMax >> P.logtw)];
-        tdf[m] = P.twdf[m * (kNMax >> P.logtw)];
     }
-    Tw tw{t64, t32, tdf, P.logtw, 0, s->grid, 0, -1};
+    Tw tw{t64, t32, P.logtw, 0, s->grid, 0, -1};
     char* wsm = base + tw_smem_bytes(P.logtw);
     Ctl c = ctl_init(P);
     const int nf = fixed_len(P.n0, P.n1);
@@ -439,21 +434,15 @@ pagd_status pagd_set_workspace(pagd_solver* s, void* dev_ptr, size_t bytes) {
     // twiddles exp(-2 pi i m / kNMax) from the host libm in long double
     std::vector<double2> t64(kNMax);
     std::vector<float2> t32(kNMax);
-    std::vector<dcx> tdf(kNMax);
     for (int m = 0; m < kNMax; m++) {
         const long double ang = -2.0L * 3.141592653589793238462643383279502884L * (long double)m / (long double)kNMax;
         t64[m].x = (double)cosl(ang);
         t64[m].y = (double)sinl(ang);
         t32[m].x = (float)t64[m].x;
         t32[m].y = (float)t64[m].y;
-        // double-float twiddles split from the long double values
-        const long double c = cosl(ang), sn = sinl(ang);
-        tdf[m].x = dfl((float)c, (float)(c - (long double)(float)c));
-        tdf[m].y = dfl((float)sn, (float)(sn - (long double)(float)sn));
     }
     pagd_status st = dcopy(s, s->ws + s->off[O_TW64], t64.data(), sizeof(double2) * kNMax);
     if (st == PAGD_OK) st = dcopy(s, s->ws + s->off[O_TW32], t32.data(), sizeof(float2) * kNMax);
-    if (st == PAGD_OK) st = dcopy(s, s->ws + s->off[O_TWDF], tdf.data(), sizeof(dcx) * kNMax);
     if (st == PAGD_OK) st = dsync(s);
     return st;
 }
@@ -711,7 +700,6 @@ constexpr int kMaxDevices = 64;
 static void* g_static_ptr[kMaxDevices];
 static double2 g_static_tw64[kNMax];
 static float2 g_static_tw32[kNMax];
-static dcx g_static_twdf[kNMax];
 static bool g_static_tw_ready = false;
 
 // Device address of the static scratch for the current device.  In host code
@@ -765,16 +753,12 @@ pagd_status pagd_step_static(pagd_solver* s, const double* un_dev, const double*
             g_static_tw64[m].y = (double)sinl(ang);
             g_static_tw32[m].x = (float)g_static_tw64[m].x;
             g_static_tw32[m].y = (float)g_static_tw64[m].y;
-            const long double c = cosl(ang), sn = sinl(ang);
-            g_static_twdf[m].x = dfl((float)c, (float)(c - (long double)(float)c));
-            g_static_twdf[m].y = dfl((float)sn, (float)(sn - (long double)(float)sn));
         }
         g_static_tw_ready = true;
     }
     const size_t b = sizeof(double) * s->npts;
     st = dcopy(s, w + s->off[O_TW64], g_static_tw64, sizeof(g_static_tw64));
     if (st == PAGD_OK) st = dcopy(s, w + s->off[O_TW32], g_static_tw32, sizeof(g_static_tw32));
-    if (st == PAGD_OK) st = dcopy(s, w + s->off[O_TWDF], g_static_twdf, sizeof(g_static_twdf));
     if (st == PAGD_OK) st = dcopy(s, w + s->off[O_U0], un_dev, b);
     if (st == PAGD_OK) st = dcopy(s, w + s->off[O_U1], unm1_dev, b);
     if (st == PAGD_OK) st = dzero(s, w + s->off[O_MASS], 2 * sizeof(double));
@@ -884,11 +868,9 @@ template <class T> static pagd_status batch_launch(pagd_batch* b, const BatchPar
     const int ntw = 1 << B.logtw;
     double2* t64 = (double2*)base;
     float2* t32 = (float2*)(base + (size_t)ntw * sizeof(double2));
-    dcx* tdf = (dcx*)(base + (size_t)ntw * (sizeof(double2) + sizeof(float2)));
     for (int m = 0; m < ntw; m++) {
         t64[m] = B.tw64[m * (kNMax >> B.logtw)];
         t32[m] = B.tw32[m * (kNMax >> B.logtw)];
-        tdf[m] = B.twdf[m * (kNMax >> B.logtw)];
     }
     char* wsm = base + tw_smem_bytes(B.logtw) + batch_ctl_bytes(B.count);
     std::vector<Ctl> ctl(B.count);
@@ -913,7 +895,7 @@ template <class T> static pagd_status batch_launch(pagd_batch* b, const BatchPar
                 for (int i = 0; i < B.count; i++) {
                     if (G[i + 1] <= clo || G[i] >= chi || G[i + 1] == G[i]) continue;
                     const Params& P = B.PI[i];
-                    Tw t{t64, t32, tdf, B.logtw, 0, 0, 0, 0};
+                    Tw t{t64, t32, B.logtw, 0, 0, 0, 0};
                     batch_split(t, gw, nw, total, G[i], G[i + 1] - G[i], phase_units(P, ctl[i].ph),
                                 unit_cost(P, ctl[i].ph));
                     batch_exec_host<T>(P, ctl[i], t, wsm, red);
@@ -1025,7 +1007,6 @@ static pagd_status batch_chunk(pagd_batch* b, double dt, int nsteps, double tol,
     B.sc = bsc;
     B.tw64 = PI[0].tw64;
     B.tw32 = PI[0].tw32;
-    B.twdf = PI[0].twdf;
     // tracing on the first member records the launch's global phases there
     B.trace = s0->trace ? (unsigned long long*)(s0->ws + s0->off[O_TRACE]) : nullptr;
     B.trace_cap = kTraceCap;
