@@ -49,7 +49,7 @@ struct pagd_solver {
     // layout
     long long npts;
     int h1, nslots, tsize;
-    size_t off[32];
+    size_t off[48];  // workspace offsets, indexed by the O_* enum
     size_t ws_bytes;
     char* ws;
     // launch plan
@@ -118,6 +118,7 @@ static void plan_layout(pagd_solver* s) {
     sz[O_X] = s->dim == 3 ? (size_t)2 * T * H * 3 : 0;
     sz[O_X64] = s->dim == 3 ? sizeof(double2) * H * 3 : 0;
     sz[O_GH64] = sizeof(double2) * H;
+    static_assert(O_END <= (int)(sizeof(((pagd_solver*)nullptr)->off) / sizeof(size_t)), "offset table too small");
     size_t o = 0;
     for (int i = 0; i < O_END; i++) {
         s->off[i] = o;
