@@ -16,9 +16,11 @@ from . import pagd
 from . import sno as SB
 
 
-def trajectories(torch, w, seeds, steps, skip=2):
+def trajectories(torch, w, seeds, steps, skip=20):
     """[len(seeds), steps + 2, n0, n1] accepted states (FP64, device), after
-    `skip` steps from u0 (the first steps of a noisy start are not typical)."""
+    `skip` steps from u0: the first steps from white-noise data are dominated
+    by stiff, fast-decaying high modes that a network with few kept modes
+    cannot represent and that no later state resembles."""
     out = torch.empty((len(seeds), steps + 2) + tuple(w.n), dtype=torch.float64, device="cuda")
     for i, seed in enumerate(seeds):
         S = pagd.solver_for(w)
@@ -41,6 +43,17 @@ def scales(torch, traj):
     return 1.0 / float(torch.sqrt((d1 ** 2).mean())), float(torch.sqrt((r ** 2).mean()))
 
 
+def batch_loss(torch, net, traj, picks, s_in, s_out):
+    """Loss on fixed triples (index pairs (trajectory, k)), for validation."""
+    ti = [p[0] for p in picks]
+    ki = [p[1] for p in picks]
+    unm1 = traj[ti, ki].contiguous()
+    un = traj[ti, [k + 1 for k in ki]].contiguous()
+    tgt = traj[ti, [k + 2 for k in ki]].contiguous()
+    loss, _ = net.loss_grad(un, unm1, tgt, 1.0, s_in, s_out)
+    return loss
+
+
 def train(torch, net, traj, iters, batch, lr, s_in, s_out, seed=0):
     """Adam on random minibatches of triples; returns the loss history."""
     rng = np.random.default_rng(seed)
@@ -58,7 +71,7 @@ def train(torch, net, traj, iters, batch, lr, s_in, s_out, seed=0):
     return hist
 
 
-def evaluate(torch, w, net, seeds, steps, s_in, s_out, skip=2):
+def evaluate(torch, w, net, seeds, steps, s_in, s_out, skip=20):
     """PAGD evaluations per step and device time per step, from the
     extrapolated initial iterate (plain) and from the network's proposal
     (learned, through pagd_step_with_guess; inference included)."""
@@ -101,15 +114,19 @@ def run_study(torch, w, train_seeds, test_seeds, steps_train, steps_test, iters,
     traj = trajectories(torch, w, train_seeds, steps_train)
     s_in, s_out = scales(torch, traj)
     net = SB.SNO(w.n, channels=channels, layers=layers, modes=modes, batch=batch, seed=1)
+    val = [(i % traj.shape[0], (7 * i) % (traj.shape[1] - 2)) for i in range(batch)]
+    val_before = batch_loss(torch, net, traj, val, s_in, s_out)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     hist = train(torch, net, traj, iters, batch, lr, s_in, s_out)
     e1.record()
     torch.cuda.synchronize()
+    val_after = batch_loss(torch, net, traj, val, s_in, s_out)
     ev = evaluate(torch, w, net, test_seeds, steps_test, s_in, s_out)
     del traj
     return {"workload": w.name, "network": f"{layers} spectral layers, {channels} channels, "
             f"{modes[0]}x{modes[1]} modes, GELU, FP32", "train": {"trajectories": len(train_seeds),
             "steps": steps_train, "iters": iters, "batch": batch, "ms": e0.elapsed_time(e1),
-            "loss_first": hist[0], "loss_last": float(np.mean(hist[-10:]))},
+            "loss_first": hist[0], "loss_last": float(np.mean(hist[-10:])),
+            "fixed_batch_loss_before": val_before, "fixed_batch_loss_after": val_after},
             "test": {"seeds": list(test_seeds), "steps": steps_test}, **ev}
