@@ -282,3 +282,78 @@ def run(P: Problem, u0, dt: float, nsteps: int, tol: float, callback=None):
         if callback is not None:
             callback(n, un)
     return un, iters
+
+
+def rhs(P: Problem, v) -> np.ndarray:
+    """R(v) = M Lap (delta E / delta u)(v)."""
+    v = _r(v)
+    out = np.empty_like(v)
+    p = P.cparams()
+    lib().orc_rhs(ctypes.byref(p), _dp(v), _dp(out))
+    return out
+
+
+def am3_err(P: Problem, un, ut, Rt, Rn, Rnm1, dt, dt_prev):
+    un, ut, Rt, Rn, Rnm1 = (_r(a) for a in (un, ut, Rt, Rn, Rnm1))
+    uh = np.empty_like(un)
+    p = P.cparams()
+    f = lib().orc_am3_err
+    f.restype = ctypes.c_double
+    e = f(ctypes.byref(p), _dp(un), _dp(ut), _dp(Rt), _dp(Rn), _dp(Rnm1), ctypes.c_double(dt),
+          ctypes.c_double(dt_prev), _dp(uh))
+    return e, uh
+
+
+def midab2_err(P: Problem, un, unm1, unm2, ut, dt, dtn, dtnm1):
+    un, unm1, unm2, ut = (_r(a) for a in (un, unm1, unm2, ut))
+    uh = np.empty_like(un)
+    p = P.cparams()
+    f = lib().orc_midab2_err
+    f.restype = ctypes.c_double
+    e = f(ctypes.byref(p), _dp(un), _dp(unm1), _dp(unm2), _dp(ut), ctypes.c_double(dt), ctypes.c_double(dtn),
+          ctypes.c_double(dtnm1), _dp(uh))
+    return e, uh
+
+
+def run_adaptive(P: Problem, u0, T, dt_min, dt_max, step_tol, tol, max_steps=100000):
+    """Algorithm 3: tentative step, higher-order estimate (AM3, or midAB2 for
+    MP from the third step on), accept if ERR <= step_tol or dt <= dt_min,
+    next dt = clamp(0.9 (step_tol / ERR)^(1/3) dt, dt_min, dt_max).
+    Returns (u, times, dts, rejections, iterations per accepted step)."""
+    un = _r(u0).copy()
+    unm1 = un.copy()
+    unm2 = None
+    t, n, dtt = 0.0, 0, dt_min
+    dts, times, its = [], [0.0], []
+    dt_prev = dt_min
+    rej = 0
+    Rn = rhs(P, un)
+    Rnm1 = Rn.copy()
+    while t < T and n < max_steps:
+        if P.scheme in (BDF2, MP):
+            r = pagd_step(P, n, un, unm1, dtt, dt_prev, tol)
+            if r.status != OK:
+                raise RuntimeError(f"oracle step failed with status {r.status}")
+            ut, it = r.u, r.iters
+        else:
+            ut, it = imex_step(P, n, un, unm1, dtt, dt_prev), 0
+        Rt = rhs(P, ut)
+        if P.scheme == MP and n >= 2:
+            err, _ = midab2_err(P, un, unm1, unm2, ut, dtt, dts[-1], dts[-2])
+        else:
+            err, _ = am3_err(P, un, ut, Rt, Rn, Rnm1, dtt, dt_prev if n > 0 else dtt)
+        tmp = dtt
+        if err <= step_tol or dtt <= dt_min:
+            unm2, unm1, un = unm1, un, ut
+            Rnm1, Rn = Rn, Rt
+            dt_prev = dtt
+            dts.append(dtt)
+            t += dtt
+            times.append(t)
+            its.append(it)
+            n += 1
+        else:
+            rej += 1
+        dtt = max(dt_min, min(0.9 * (step_tol / max(err, 1e-300)) ** (1.0 / 3.0) * tmp, dt_max))
+    return un, np.array(times), np.array(dts), rej, its
+

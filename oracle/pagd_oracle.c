@@ -630,5 +630,65 @@ int orc_scheme_residual(const orc_params *p, int step, const double *un, const d
     return ORC_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* adaptive time stepping (Sec. 3.1.2, Algorithm 3)                          */
+/* ------------------------------------------------------------------------ */
+
+/* R(v) = M Lap_N (delta E / delta u)(v), the right-hand side of the gradient
+ * flow (Eqs. eqn:PFCsystem / eqn:FCHPDE) that the AM3 estimator samples. */
+int orc_rhs(const orc_params *p, const double *v, double *out) {
+    long N = npts(p);
+    double *mu = (double *)malloc(sizeof(double) * (size_t)N);
+    orc_mu(p, v, mu);
+    lap(p, mu, out);
+    for (long i = 0; i < N; i++) out[i] *= p->M;
+    free(mu);
+    return ORC_OK;
+}
+
+static double l2(const orc_params *p, const double *u) { return sqrt(ip(p, u, u)); }
+
+/* AM3 stepping: the explicit variant of the third-order Adams-Moulton formula
+ * with the tentative solution ut in place of the implicit value,
+ *   uh = un + dt/6 [ (3 + 2 rho)/(1 + rho) R(ut) + (3 + rho) R(un) - rho^2/(1 + rho) R(unm1) ],
+ * rho = dt / dt_prev; returns ERR = ||ut - uh|| / ||uh|| (discrete L2) and
+ * writes uh. */
+double orc_am3_err(const orc_params *p, const double *un, const double *ut, const double *Rt, const double *Rn,
+                   const double *Rnm1, double dt, double dt_prev, double *uh) {
+    long N = npts(p);
+    double rho = dt / dt_prev;
+    double ct = (3.0 + 2.0 * rho) / (1.0 + rho), cn = 3.0 + rho, cm = -rho * rho / (1.0 + rho);
+    double *d = (double *)malloc(sizeof(double) * (size_t)N);
+    for (long i = 0; i < N; i++) {
+        uh[i] = un[i] + dt / 6.0 * (ct * Rt[i] + cn * Rn[i] + cm * Rnm1[i]);
+        d[i] = ut[i] - uh[i];
+    }
+    double e = l2(p, d) / l2(p, uh);
+    free(d);
+    return e;
+}
+
+/* midAB2 stepping (used with MP): the quadratic extrapolation through
+ * (t_{n-2}, t_{n-1}, t_n) evaluated at t_n + dt,
+ *   uh = a un - b unm1 + c unm2 with the Lagrange weights of the paper,
+ * and ERR = ||ut - uh|| / ||uh|| / (1 - 1 / (24 R_n)),
+ * R_n = 1/24 + 1/8 (1 + dtn/dt)(1 + 2 dtn/dt + dtnm1/dt). */
+double orc_midab2_err(const orc_params *p, const double *un, const double *unm1, const double *unm2,
+                      const double *ut, double dt, double dtn, double dtnm1, double *uh) {
+    long N = npts(p);
+    double a = (dt + dtn) * (dt + dtn + dtnm1) / (dtn * (dtn + dtnm1));
+    double b = dt * (dt + dtn + dtnm1) / (dtn * dtnm1);
+    double c = dt * (dt + dtn) / (dtnm1 * (dtn + dtnm1));
+    double Rn = 1.0 / 24.0 + 0.125 * (1.0 + dtn / dt) * (1.0 + 2.0 * dtn / dt + dtnm1 / dt);
+    double *d = (double *)malloc(sizeof(double) * (size_t)N);
+    for (long i = 0; i < N; i++) {
+        uh[i] = a * un[i] - b * unm1[i] + c * unm2[i];
+        d[i] = ut[i] - uh[i];
+    }
+    double e = l2(p, d) / l2(p, uh) / (1.0 - 1.0 / (24.0 * Rn));
+    free(d);
+    return e;
+}
+
 /* Sizes of the structs for the ctypes side to check its layout against. */
 int orc_sizeof_params(void) { return (int)sizeof(orc_params); }
