@@ -135,6 +135,29 @@ pagd_status pagd_run_host(pagd_solver* s, const double* u0_host, double* u_host_
 pagd_status pagd_energy(pagd_solver* s, const double* u_dev, double* E);
 pagd_status pagd_mass(pagd_solver* s, const double* u_dev, double* m);
 
+/* R(v) = M Lap_N mu(v) (the right-hand side of the gradient flow, Sec. 2) of a
+ * device field v into r (device; may not alias v). */
+pagd_status pagd_rhs(pagd_solver* s, const double* v_dev, double* r_dev);
+
+/* Adaptive time stepping (Sec. 3.1.2, Algorithm 3) from the current state to
+ * time T (or max_steps accepted steps): each tentative step of size dt is
+ * taken by the solver's scheme, a higher-order value is formed (AM3: the
+ * explicit third-order Adams-Moulton variant with R at the tentative, current
+ * and previous solutions; for MP from the third step on, midAB2: the quadratic
+ * extrapolation through the last three solutions with its truncation factor),
+ * ERR = ||u_tentative - u_high|| / ||u_high|| (discrete L2); the step is
+ * accepted when ERR <= step_tol or dt <= dt_min, and the next tentative size
+ * is clamp(0.9 (step_tol / ERR)^(1/3) dt, dt_min, dt_max).  The first
+ * tentative size is dt_min.  A rejected step leaves no trace in the solver
+ * state.  scratch_dev: device, 6 n_pts doubles (caller-owned).  Outputs
+ * (nullable, host): t_out [max_steps + 1] accepted times (t_out[0] = 0),
+ * dt_out / iters_out [max_steps] accepted sizes and PAGD evaluations,
+ * nsteps_out, rejected_out; u_dev (device) the final field.  tol is the PAGD
+ * tolerance of each step (ignored by IMEX schemes). */
+pagd_status pagd_run_adaptive(pagd_solver* s, double T, double dt_min, double dt_max, double step_tol, double tol,
+                              int max_steps, double* scratch_dev, double* u_dev, double* t_out, double* dt_out,
+                              int* iters_out, int* nsteps_out, int* rejected_out);
+
 /* Unnormalised forward DFT of a real device field (Sec. 3.2): writes the half
  * spectrum n[0] x ... x (n[dim-1]/2 + 1) complex (interleaved re, im doubles),
  * row-major.  pagd_fft_c2r inverts it including the 1/n_pts factor. */

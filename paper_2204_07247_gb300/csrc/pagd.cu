@@ -652,6 +652,145 @@ pagd_status pagd_mass(pagd_solver* s, const double* u_dev, double* m) {
     return PAGD_OK;
 }
 
+pagd_status pagd_rhs(pagd_solver* s, const double* v_dev, double* r_dev) {
+    if (!s || !v_dev || !r_dev) return PAGD_EINVAL;
+    if (!s->ws) return fail(s, PAGD_ESTATE, "no workspace");
+    Params P = base_params(s);
+    P.prog = PROG_RHS;
+    P.in_real = v_dev;
+    P.out_real = r_dev;
+    pagd_status st = run_program(s, P);
+    if (st != PAGD_OK) return st;
+    Scal sc;
+    st = dcopy(s, &sc, P.sc, sizeof(Scal));
+    if (st == PAGD_OK) st = dsync(s);
+    if (st != PAGD_OK) return st;
+    if (sc.bar_error) return fail(s, PAGD_ETIMEOUT, "device barrier timed out");
+    return PAGD_OK;
+}
+
+// ERR of adaptive stepping: sqrt(sum (ut - uh)^2 / sum uh^2), uh = sum c_j in_j
+static pagd_status est_program(pagd_solver* s, const double* ut, const double* const in[4], const double c[4],
+                               double* err) {
+    Params P = base_params(s);
+    P.prog = PROG_EST;
+    P.in_real = ut;
+    for (int j = 0; j < 4; j++) {
+        P.est_in[j] = in[j];
+        P.est_c[j] = c[j];
+    }
+    pagd_status st = run_program(s, P);
+    if (st != PAGD_OK) return st;
+    Scal sc;
+    st = dcopy(s, &sc, P.sc, sizeof(Scal));
+    if (st == PAGD_OK) st = dsync(s);
+    if (st != PAGD_OK) return st;
+    if (sc.bar_error) return fail(s, PAGD_ETIMEOUT, "device barrier timed out");
+    *err = sc.red[1] > 0.0 ? std::sqrt(sc.red[0] / sc.red[1]) : 0.0;
+    return PAGD_OK;
+}
+
+pagd_status pagd_run_adaptive(pagd_solver* s, double T, double dt_min, double dt_max, double step_tol, double tol,
+                              int max_steps, double* scratch_dev, double* u_dev, double* t_out, double* dt_out,
+                              int* iters_out, int* nsteps_out, int* rejected_out) {
+    if (!s || !scratch_dev) return PAGD_EINVAL;
+    if (!s->ws || !s->have_state) return fail(s, PAGD_ESTATE, "workspace and state must be set first");
+    if (!(T > 0.0) || !(dt_min > 0.0) || !(dt_max >= dt_min) || !(step_tol > 0.0) || !(tol >= 0.0) ||
+        max_steps < 1 || !std::isfinite(T) || !std::isfinite(dt_max))
+        return fail(s, PAGD_EINVAL, "bad T / dt_min / dt_max / step_tol / tol / max_steps");
+    const size_t nb = sizeof(double) * (size_t)s->npts;
+    const long long N = s->npts;
+    // scratch: R(u^n), R(u^{n-1}), R(ut), ut, u^{n-2}, saved u^{n-1}
+    double* Rn = scratch_dev;
+    double* Rm = scratch_dev + N;
+    double* Rt = scratch_dev + 2 * N;
+    double* ut = scratch_dev + 3 * N;
+    double* um2 = scratch_dev + 4 * N;
+    double* save = scratch_dev + 5 * N;
+    const bool mp = s->scheme == PAGD_MP;
+    auto slot = [&](int c) { return (double*)(s->ws + (c ? s->off[O_U1] : s->off[O_U0])); };
+    double* mass = (double*)(s->ws + s->off[O_MASS]);
+    double mass_save[2];
+    pagd_status st = pagd_rhs(s, slot(s->cur), Rn);
+    if (st == PAGD_OK) st = dcopy(s, Rm, Rn, nb);
+    if (st != PAGD_OK) return st;
+    double t = 0.0, dtt = dt_min, dt_prev = s->step > 0 ? s->dt_prev : dt_min;
+    double dtn = 0.0, dtnm1 = 0.0;  // the last two accepted steps (midAB2)
+    int n = 0, rej = 0;
+    if (t_out) t_out[0] = 0.0;
+    while (t < T && n < max_steps) {
+        // tentative step from (u^n, u^{n-1}); its writes are undone on rejection
+        const int cur0 = s->cur, step0 = s->step, ref0 = s->ref_valid;
+        const double dtp0 = s->dt_prev;
+        st = dcopy(s, save, slot(cur0 ^ 1), nb);
+        if (st == PAGD_OK) st = dcopy(s, mass_save, mass, sizeof(mass_save));
+        if (st == PAGD_OK) st = dsync(s);
+        if (st != PAGD_OK) return st;
+        s->dt_prev = dt_prev;
+        int it = 0;
+        double res = 0.0;
+        st = run_chunk(s, ut, dtt, 1, tol, &it, &res);
+        if (st != PAGD_OK) return st;
+        st = pagd_rhs(s, ut, Rt);
+        if (st != PAGD_OK) return st;
+        double err = 0.0;
+        if (mp && n >= 2) {
+            const double a = (dtt + dtn) * (dtt + dtn + dtnm1) / (dtn * (dtn + dtnm1));
+            const double b = dtt * (dtt + dtn + dtnm1) / (dtn * dtnm1);
+            const double c = dtt * (dtt + dtn) / (dtnm1 * (dtn + dtnm1));
+            const double* in[4] = {slot(cur0), save, um2, nullptr};
+            const double cf[4] = {a, -b, c, 0.0};
+            st = est_program(s, ut, in, cf, &err);
+            const double Rn_ = 1.0 / 24.0 + 0.125 * (1.0 + dtn / dtt) * (1.0 + 2.0 * dtn / dtt + dtnm1 / dtt);
+            err /= (1.0 - 1.0 / (24.0 * Rn_));
+        } else {
+            const double rho = dtt / (n > 0 ? dt_prev : dtt);
+            const double* in[4] = {slot(cur0), Rt, Rn, Rm};
+            const double cf[4] = {1.0, dtt / 6.0 * (3.0 + 2.0 * rho) / (1.0 + rho), dtt / 6.0 * (3.0 + rho),
+                                  -dtt / 6.0 * rho * rho / (1.0 + rho)};
+            st = est_program(s, ut, in, cf, &err);
+        }
+        if (st != PAGD_OK) return st;
+        const double tmp = dtt;
+        if (err <= step_tol || dtt <= dt_min) {
+            // accept: the solver already holds u^{n+1} = ut and u^n
+            st = dcopy(s, um2, save, nb);
+            if (st == PAGD_OK) st = dcopy(s, Rm, Rn, nb);
+            if (st == PAGD_OK) st = dcopy(s, Rn, Rt, nb);
+            if (st != PAGD_OK) return st;
+            dtnm1 = dtn;
+            dtn = dtt;
+            dt_prev = dtt;
+            t += dtt;
+            if (t_out) t_out[n + 1] = t;
+            if (dt_out) dt_out[n] = dtt;
+            if (iters_out) iters_out[n] = it;
+            n++;
+        } else {
+            // reject: put back u^{n-1}, the mass accumulators and the counters
+            st = dcopy(s, slot(cur0 ^ 1), save, nb);
+            if (st == PAGD_OK) st = dcopy(s, mass, mass_save, sizeof(mass_save));
+            if (st == PAGD_OK) st = dsync(s);
+            if (st != PAGD_OK) return st;
+            s->cur = cur0;
+            s->step = step0;
+            s->dt_prev = dtp0;
+            s->ref_valid = 0;  // the reference spectra moved with the rejected step
+            (void)ref0;
+            rej++;
+        }
+        dtt = 0.9 * std::cbrt(step_tol / (err > 1e-300 ? err : 1e-300)) * tmp;
+        dtt = std::max(dt_min, std::min(dtt, dt_max));
+    }
+    if (nsteps_out) *nsteps_out = n;
+    if (rejected_out) *rejected_out = rej;
+    if (u_dev) {
+        st = dcopy(s, u_dev, slot(s->cur), nb);
+        if (st == PAGD_OK) st = dsync(s);
+    }
+    return st;
+}
+
 pagd_status pagd_fft_r2c(pagd_solver* s, const double* u_dev, double* spec_dev) {
     if (!s || !u_dev || !spec_dev) return PAGD_EINVAL;
     if (!s->ws) return fail(s, PAGD_ESTATE, "no workspace");

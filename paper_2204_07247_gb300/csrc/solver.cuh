@@ -36,7 +36,7 @@ enum { M_PFC = 0, M_FCH = 1 };
 enum { S_BDF2 = 0, S_MP = 1, S_LBDF2 = 2, S_LMP = 3 };
 enum { P_FP64 = 0, P_MIXED = 1 };
 enum { PROG_RUN = 0, PROG_FFT_FWD = 1, PROG_FFT_INV = 2, PROG_ENERGY = 3, PROG_MASS = 4,
-       PROG_IMEX = 5 };
+       PROG_IMEX = 5, PROG_RHS = 6, PROG_EST = 7 };
 enum { ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ECUDA = 3, ST_ENOCONV = 4, ST_EPRECOND = 5,
        ST_ENAN = 6, ST_ESTATE = 7, ST_ETIMEOUT = 8 };
 enum { FLAG_PRECOND = 1 };
@@ -46,6 +46,7 @@ enum Phase {
     PH_FWD_R, PH_FWD_C, PH_INV_C, PH_INV_R, PH_EN_R, PH_EN_C, PH_EN_R2, PH_MASS,
     PH_IM_R0, PH_IM_C0, PH_IM_R1, PH_IM_C1, PH_IM_R2,
     PH_MF, PH_MI, PH_GS,
+    PH_RH_R0, PH_RH_C0, PH_RH_R1, PH_RH_C1, PH_RH_R2, PH_EST,
     PH_DONE
 };
 
@@ -141,6 +142,9 @@ struct Params {
     StepStat* stats;
     // caller's initial iterate for the first step of the run (nullable)
     const double* guess;
+    // error-estimate program: uh = sum_j est_c[j] est_in[j] (nullable terms)
+    const double* est_in[4];
+    double est_c[4];
     // program input / output
     const double* in_real;
     double* out_real;
@@ -1432,6 +1436,81 @@ inline __device__ void phase_mass(const Params& P, const Tw& tw, double* red) {
     publish_sum(&P.sc->red[0], acc);
 }
 
+// ------------------------------------------- right-hand side and estimate
+//
+// R(v) = M Lap mu(v) (the gradient flow of Sec. 2, sampled by the AM3
+// estimator of Sec. 3.1.2), in FP64: PFC mu_hat = N_hat + (1 - eps - 2 kappa +
+// kappa^2) v_hat with N = v^3; FCH mu_hat = eps^4 kappa^2 v_hat +
+// eps^2 kappa F'_hat + P_hat, P = -eps^2 (F'' - eta1) Lap v + (F'' - eta2) F'.
+template <int NF>
+__device__ void phase_rh_r0(const Params& P, const Tw& tw, char* smem) {
+    const bool pfc = P.model == M_PFC;
+    rowp<double, double, NF>(P, tw, 0, pfc ? 2 : 1, (const double2*)nullptr, P.NB64, smem,
+                             [&](long long p, int, int) { return P.in_real[p]; },
+                             [&](long long, int, int, const double& v, const double*, double* out) {
+                                 out[0] = v;
+                                 if (pfc) out[1] = v * v * v;
+                             });
+}
+template <int NF>
+__device__ void phase_rh_c0(const Params& P, const Tw& tw, char* smem) {
+    const bool pfc = P.model == M_PFC;
+    colp<double, NF>(P, tw, pfc ? 2 : 1, 1, csrc64(P), cdst64(P), smem, [&](int, int) { return Nil{}; },
+                     [&](int k1, int k0, const Nil&, const double2* in, double2* out) {
+                         const double kap = kappa_at(P, k1, k0);
+                         if (pfc) {
+                             const double Lh = 1.0 - P.eps - 2.0 * kap + kap * kap;
+                             const double f = -P.M * kap;
+                             out[0] = double2{f * (in[1].x + Lh * in[0].x), f * (in[1].y + Lh * in[0].y)};
+                         } else {
+                             P.CL64[(long long)k1 * P.n0 + k0] = in[0];
+                             out[0] = double2{-kap * in[0].x, -kap * in[0].y};
+                         }
+                     });
+}
+template <int NF>
+__device__ void phase_rh_r1(const Params& P, const Tw& tw, char* smem) {
+    const double e2 = P.eps * P.eps;
+    rowp<double, double, NF>(P, tw, 1, 2, P.DB64, P.NB64, smem,
+                             [&](long long p, int, int) { return P.in_real[p]; },
+                             [&](long long, int, int, const double& v, const double* in, double* out) {
+                                 const double f1 = dF1(v, P.tau), f2 = dF2(v, P.tau);
+                                 out[0] = f1;
+                                 out[1] = -e2 * (f2 - P.eta1) * in[0] + (f2 - P.eta2) * f1;
+                             });
+}
+template <int NF>
+__device__ void phase_rh_c1(const Params& P, const Tw& tw, char* smem) {
+    const double e2 = P.eps * P.eps, e4 = e2 * e2;
+    colp<double, NF>(P, tw, 2, 1, csrc64(P), cdst64(P), smem,
+                     [&](int k1, int k0) { return P.CL64[(long long)k1 * P.n0 + k0]; },
+                     [&](int k1, int k0, const double2& v, const double2* in, double2* out) {
+                         const double kap = kappa_at(P, k1, k0);
+                         const double f = -P.M * kap;
+                         const double mr = e4 * kap * kap * v.x + e2 * kap * in[0].x + in[1].x;
+                         const double mi = e4 * kap * kap * v.y + e2 * kap * in[0].y + in[1].y;
+                         out[0] = double2{f * mr, f * mi};
+                     });
+}
+// Error estimate of adaptive stepping: uh = sum_j c_j in_j (the AM3 or midAB2
+// higher-order value), red[0] = sum (ut - uh)^2, red[1] = sum uh^2 (the cell
+// volume cancels in their ratio); ut = in_real.
+inline __device__ void phase_est(const Params& P, const Tw& tw) {
+    double e = 0.0, h = 0.0;
+    const long long gt = thread_rank(tw);
+    const long long gs = thread_count(tw);
+    for (long long p = gt; p < P.npts; p += gs) {
+        double uh = 0.0;
+        for (int j = 0; j < 4; j++)
+            if (P.est_in[j]) uh += P.est_c[j] * P.est_in[j][p];
+        const double d = P.in_real[p] - uh;
+        e += d * d;
+        h += uh * uh;
+    }
+    publish_sum(&P.sc->red[0], e);
+    publish_sum(&P.sc->red[1], h);
+}
+
 // ------------------------------------------------------ linear IMEX step
 //
 // Eq. eqn:FCH-semidis-simplicit with the splits of Sec. 3.1.1, solved per
@@ -1591,6 +1670,8 @@ __host__ __device__ inline Ctl ctl_init(const Params& P) {
         case PROG_FFT_FWD: c.ph = PH_FWD_R; break;
         case PROG_FFT_INV: c.ph = PH_INV_C; break;
         case PROG_ENERGY: c.ph = PH_EN_R; break;
+        case PROG_RHS: c.ph = PH_RH_R0; break;
+        case PROG_EST: c.ph = PH_EST; break;
         default: c.ph = PH_MASS; break;
     }
     return c;
@@ -1599,13 +1680,13 @@ __host__ __device__ inline Ctl ctl_init(const Params& P) {
 // phases by pass type, for the 3D middle passes and the batched schedule
 __host__ __device__ inline bool phase_is_col(int ph) {
     return ph == PH_C || ph == PH_E || ph == PH_CI || ph == PH_IM_C0 || ph == PH_IM_C1 || ph == PH_FWD_C ||
-           ph == PH_INV_C || ph == PH_EN_C;
+           ph == PH_INV_C || ph == PH_EN_C || ph == PH_RH_C0 || ph == PH_RH_C1;
 }
 __host__ __device__ inline bool phase_is_mid(int ph) { return ph == PH_MF || ph == PH_MI; }
 // row passes that read a half spectrum written by the column pass before them
 __host__ __device__ inline bool row_reads_spectrum(int ph) {
     return ph == PH_D || ph == PH_R1 || ph == PH_RI || ph == PH_INV_R || ph == PH_EN_R2 || ph == PH_IM_R1 ||
-           ph == PH_IM_R2;
+           ph == PH_IM_R2 || ph == PH_RH_R1 || ph == PH_RH_R2;
 }
 
 // 3D: put a middle pass between a row pass and the column pass after it (MF)
@@ -1625,6 +1706,8 @@ __host__ __device__ inline void mid_insert(const Params& P, int pph, int pinc, i
             case PH_RI: k = K; m64 = 0; break;
             case PH_IM_R0: k = 3; break;
             case PH_IM_R1: k = 2; break;
+            case PH_RH_R0: k = (P.model == M_PFC) ? 2 : 1; break;
+            case PH_RH_R1: k = 2; break;
             default: k = 1; break;  // FWD_R, EN_R
         }
     } else if (phase_is_col(pph) && row_reads_spectrum(nx)) {
@@ -1774,6 +1857,10 @@ __device__ void ctl_step(const Params& P, Ctl& c) {
         case PH_INV_C: c.ph = PH_INV_R; break;
         case PH_EN_R: c.ph = PH_EN_C; break;
         case PH_EN_C: c.ph = (P.model == M_PFC) ? PH_DONE : PH_EN_R2; break;
+        case PH_RH_R0: c.ph = PH_RH_C0; break;
+        case PH_RH_C0: c.ph = (P.model == M_PFC) ? PH_RH_R2 : PH_RH_R1; break;
+        case PH_RH_R1: c.ph = PH_RH_C1; break;
+        case PH_RH_C1: c.ph = PH_RH_R2; break;
         default: c.ph = PH_DONE; break;
     }
 }
@@ -1811,6 +1898,12 @@ __device__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* sm
         case PH_EN_R2: phase_en_r2<NF>(P, tw, smem, red); break;
         case PH_MASS: phase_mass(P, tw, red); break;
         case PH_GS: phase_gs(P, c, tw); break;
+        case PH_RH_R0: phase_rh_r0<NF>(P, tw, smem); break;
+        case PH_RH_C0: phase_rh_c0<NF>(P, tw, smem); break;
+        case PH_RH_R1: phase_rh_r1<NF>(P, tw, smem); break;
+        case PH_RH_C1: phase_rh_c1<NF>(P, tw, smem); break;
+        case PH_RH_R2: phase_inv_r<NF>(P, tw, smem); break;
+        case PH_EST: phase_est(P, tw); break;
         case PH_MF:
             if (c.m64) mid_pass<double, -1>(P, tw, c.mk, P.NB64, P.X64, smem);
             else mid_pass<T, -1>(P, tw, c.mk, (const cx<T>*)P.NB, (cx<T>*)P.X, smem);

@@ -27,7 +27,7 @@ SCHEMES = {"bdf2": BDF2, "mp": MP, "lbdf2": LBDF2, "lmp": LMP}
 PRECISIONS = {"fp64": FP64, "fp32_mixed": FP32_MIXED}
 EXPORTS = ("pagd_default_opts", "pfc_init", "fch_init", "pagd_workspace_size", "pagd_set_workspace",
            "pagd_set_state", "pagd_step", "pagd_step_with_guess", "pagd_run", "pagd_run_host", "pagd_energy", "pagd_mass",
-           "pagd_fft_r2c", "pagd_fft_c2r", "pagd_get_state", "pagd_step_static", "pagd_set_trace",
+           "pagd_rhs", "pagd_run_adaptive", "pagd_fft_r2c", "pagd_fft_c2r", "pagd_get_state", "pagd_step_static", "pagd_set_trace",
            "pagd_get_trace", "pagd_last_error", "pagd_destroy", "pagd_batch_create",
            "pagd_batch_workspace_size", "pagd_batch_set_workspace", "pagd_batch_run",
            "pagd_batch_last_error", "pagd_batch_destroy")
@@ -66,6 +66,8 @@ def _declare(lib):
         "pagd_run_host": [P, P, P, d, i, d, IP, D],
         "pagd_energy": [P, P, D],
         "pagd_mass": [P, P, D],
+        "pagd_rhs": [P, P, P],
+        "pagd_run_adaptive": [P, d, d, d, d, d, i, P, P, D, D, IP, IP, IP],
         "pagd_fft_r2c": [P, P, P],
         "pagd_fft_c2r": [P, P, P],
         "pagd_get_state": [P, P, P, IP],
@@ -264,6 +266,28 @@ class Solver:
         m = ctypes.c_double()
         self._check(self.lib.pagd_mass(self._h, self._ptr(u), ctypes.byref(m)), "mass")
         return m.value
+
+    def rhs(self, v, out=None):
+        """R(v) = M Lap mu(v)."""
+        out = self.empty_field() if out is None else out
+        self._check(self.lib.pagd_rhs(self._h, self._ptr(v), self._ptr(out)), "rhs")
+        return out
+
+    def run_adaptive(self, T, dt_min, dt_max, step_tol, tol, max_steps=10000, u_out=None):
+        """Algorithm 3 from the current state to time T; returns (times, dts,
+        evaluations per accepted step, rejected count)."""
+        scratch = (np.zeros(6 * int(np.prod(self.n))) if self.emu else
+                   __import__("torch").empty(6 * int(np.prod(self.n)), dtype=__import__("torch").float64,
+                                             device="cuda"))
+        t = (ctypes.c_double * (max_steps + 1))()
+        dts = (ctypes.c_double * max_steps)()
+        its = (ctypes.c_int * max_steps)()
+        n, rej = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.pagd_run_adaptive(self._h, T, dt_min, dt_max, step_tol, tol, max_steps,
+                                               self._ptr(scratch), self._ptr(u_out), t, dts, its,
+                                               ctypes.byref(n), ctypes.byref(rej)), "run_adaptive")
+        k = n.value
+        return np.array(t[:k + 1]), np.array(dts[:k]), np.array(its[:k]), rej.value
 
     def fft_r2c(self, u, spec=None):
         spec = self.empty_spectrum() if spec is None else spec
