@@ -720,7 +720,7 @@ pagd_status pagd_run_adaptive(pagd_solver* s, double T, double dt_min, double dt
     if (t_out) t_out[0] = 0.0;
     while (t < T && n < max_steps) {
         // tentative step from (u^n, u^{n-1}); its writes are undone on rejection
-        const int cur0 = s->cur, step0 = s->step, ref0 = s->ref_valid;
+        const int cur0 = s->cur, step0 = s->step;
         const double dtp0 = s->dt_prev;
         st = dcopy(s, save, slot(cur0 ^ 1), nb);
         if (st == PAGD_OK) st = dcopy(s, mass_save, mass, sizeof(mass_save));
@@ -776,7 +776,6 @@ pagd_status pagd_run_adaptive(pagd_solver* s, double T, double dt_min, double dt
             s->step = step0;
             s->dt_prev = dtp0;
             s->ref_valid = 0;  // the reference spectra moved with the rejected step
-            (void)ref0;
             rej++;
         }
         dtt = 0.9 * std::cbrt(step_tol / (err > 1e-300 ? err : 1e-300)) * tmp;
