@@ -330,7 +330,8 @@ def profile_form(torch, pagd, form, w, steps, warm, trace):
     its = out[0]
     agg = collections.defaultdict(lambda: [0, 0.0])
     for m, d in zip(masks[1:], np.diff(t)):
-        name = ("+".join(pagd.PHASES[p] for p in range(32) if m >> p & 1) if batch else pagd.PHASES[m])
+        name = ("+".join(pagd.PHASES[p] for p in range(32) if m >> p & 1) if batch
+                else pagd.PHASES[m & 0xFFFF] + ("/inc" if m >> 16 & 1 else ""))
         agg[name][0] += 1
         agg[name][1] += d
     tot = t[-1]

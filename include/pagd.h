@@ -198,7 +198,9 @@ pagd_status pagd_step_static(pagd_solver* s, const double* un_dev, const double*
  * phase[i] and t_us[i] (microseconds since the launch started; record 0 is the
  * start marker), at most cap records, and the number recorded to *count.
  * Phase identifiers are those of the kernel's control machine (see
- * paper_2204_07247_gb300/pagd.py PHASES).  With tracing enabled on the first
+ * paper_2204_07247_gb300/pagd.py PHASES); bit 16 is set on the phases B..E of
+ * an incremental base evaluation (transforms of the shift in the iteration
+ * precision, FP32-mixed only).  With tracing enabled on the first
  * member of a batch, pagd_batch_run records its global phases in that member
  * instead: phase[i] is then a bit mask (bit p set: some member ran phase p). */
 pagd_status pagd_set_trace(pagd_solver* s, int enable);

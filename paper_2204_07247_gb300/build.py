@@ -20,8 +20,8 @@ LIB = os.path.join(BUILD, "libpagd.so")
 EMU = os.path.join(BUILD, "libpagd_emu.so")
 # host code, one kernel translation unit per fixed line length (0: runtime length)
 # the batched kernel per iteration precision, and the learned-guess network
-SOURCES = ["pagd.cu", "pagd_k0.cu", "pagd_k64.cu", "pagd_k128.cu", "pagd_k256.cu", "pagd_k512.cu",
-           "pagd_batch_f32.cu", "pagd_batch_f64.cu", "sno.cu"]
+SOURCES = (["pagd.cu"] + [f"pagd_k{nf}_{t}.cu" for nf in (0, 64, 128, 256, 512) for t in ("f32", "f64")]
+           + ["pagd_batch_f32.cu", "pagd_batch_f64.cu", "sno.cu"])
 HEADERS = ["compat.cuh", "fft.cuh", "solver.cuh", "kernels.cuh", "batch.cuh"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 

@@ -21,7 +21,7 @@ namespace pagd {
 
 template <class T, int NF>
 __device__ __forceinline__ void batch_exec_nf(const Params& P, const Ctl& c, const Tw& t, char* wsm, double* red) {
-    exec_phase<T, NF>(P, c, t, wsm, red);
+    exec_phase<T, NF | kNoCoop>(P, c, t, wsm, red);
 }
 
 template <class T>

@@ -15,6 +15,7 @@
 #define __host__
 #define __global__
 #define __forceinline__ inline
+#define __noinline__
 #define __launch_bounds__(...)
 
 struct EmuDim3 { unsigned x, y, z; };

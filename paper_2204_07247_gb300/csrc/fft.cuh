@@ -220,4 +220,74 @@ __device__ __forceinline__ int fft_lines_fixed(cx<T>* b0, cx<T>* b1, int pitch, 
 
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
 
+// ---------------------------------------------------------------------------
+// CTA-cooperative transforms: all threads of the CTA share the nl lines of one
+// unit, the butterflies of a stage dealt round robin over (line, butterfly),
+// stages separated by a CTA barrier.  Used where a phase has fewer units than
+// warps: the lines of one unit then occupy every SM sub-partition instead of
+// one, which is what bounds an FP64 transform on a part with a low FP64 rate.
+
+__device__ __forceinline__ void cta_sync() {
+#ifndef PAGD_EMU
+    __syncthreads();
+#endif
+}
+
+template <int R, int S, class T, int LOGN>
+__device__ __forceinline__ void stage_coop(const cx<T>* src, cx<T>* dst, int pitch, int nl, int logNs,
+                                           const cx<T>* tw, int logTw, int tid, int nthr) {
+    using C = cx<T>;
+    constexpr int LR = (R == 2) ? 1 : (R == 4) ? 2 : 3;
+    constexpr int LNB = LOGN - LR;
+    constexpr int NB = 1 << LNB;
+    const int twshift = logTw - (logNs + LR);
+    const int nsm = (1 << logNs) - 1;
+    const int tot = nl << LNB;
+    for (int it = tid; it < tot; it += nthr) {
+        const int l = it >> LNB, j = it & (NB - 1);
+        const C* s = src + l * pitch;
+        C* d = dst + l * pitch;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) v[r] = s[j + r * NB];
+        const int jm = j & nsm;
+        if (jm) {
+#pragma unroll
+            for (int r = 1; r < R; r++) {
+                C w = tw[(jm * r) << twshift];
+                if (S > 0) w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        dftR<R, S>(v);
+        const int idxD = ((j - jm) << LR) + jm;
+#pragma unroll
+        for (int r = 0; r < R; r++) d[idxD + (r << logNs)] = v[r];
+    }
+}
+
+// nl lines of length 1 << LOGN in b0 (written by any thread before the call)
+// -> result in b0 (returns 0) or b1 (1), visible to every thread on return.
+// Each stage takes the largest radix (8, 4, 2) whose butterflies still cover
+// the nthr threads.
+template <int S, class T, int LOGN>
+__device__ __noinline__ int fft_lines_coop(cx<T>* b0, cx<T>* b1, int pitch, int nl, const cx<T>* tw, int logTw, int tid,
+                              int nthr) {
+    cx<T>* b[2] = {b0, b1};
+    int cur = 0, logNs = 0;
+    while (logNs < LOGN) {
+        const int rem = LOGN - logNs;
+        int lr = rem >= 3 ? 3 : rem;
+        while (lr > 1 && (nl << (LOGN - lr)) < nthr) lr--;
+        cta_sync();
+        if (lr == 3) stage_coop<8, S, T, LOGN>(b[cur], b[cur ^ 1], pitch, nl, logNs, tw, logTw, tid, nthr);
+        else if (lr == 2) stage_coop<4, S, T, LOGN>(b[cur], b[cur ^ 1], pitch, nl, logNs, tw, logTw, tid, nthr);
+        else stage_coop<2, S, T, LOGN>(b[cur], b[cur ^ 1], pitch, nl, logNs, tw, logTw, tid, nthr);
+        logNs += lr;
+        cur ^= 1;
+    }
+    cta_sync();
+    return cur;
+}
+
 }  // namespace pagd

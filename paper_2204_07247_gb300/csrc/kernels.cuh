@@ -1,8 +1,8 @@
 // kernels.cuh -- the persistent cooperative kernel and its launcher.
 //
-// Included by one translation unit per fixed line length (pagd_k*.cu), which
-// instantiate pagd_launch<T, NF> for T = float and double; the units compile in
-// parallel and link into libpagd.so.
+// Included by one translation unit per fixed line length and iteration type
+// (pagd_k<NF>_f32.cu / _f64.cu), each instantiating one pagd_launch<T, NF>; the
+// units compile in parallel and link into libpagd.so.
 #pragma once
 #include "solver.cuh"
 
@@ -60,7 +60,7 @@ static __device__ bool grid_barrier(Scal* sc, unsigned& gen) {
 }
 
 template <class T, int NF>
-__global__ void __launch_bounds__(kMaxThreads, 1) pagd_kernel(Params P) {
+__global__ void __launch_bounds__(kMaxThreads, 1) pagd_kernel(const __grid_constant__ Params P) {
     extern __shared__ __align__(16) char smem[];
     __shared__ double red[32];
     // twiddles exp(-2 pi i m / 2^logtw) staged from the global table
@@ -77,23 +77,35 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pagd_kernel(Params P) {
     const Tw tw{t64, t32, P.logtw, (int)(threadIdx.x / kWarp) * (int)gridDim.x + (int)blockIdx.x,
                 (int)gridDim.x * wpb, 0, -1};
     char* wsm = smem + tw_smem_bytes(P.logtw);
-    Ctl c = ctl_init(P);
+    // The control state is the same in every thread: it lives in shared memory
+    // and thread 0 advances it between two CTA barriers, which keeps its ~40
+    // values out of the registers of the phase code.
+    __shared__ Ctl c;
     unsigned gen = 0;
     int ntr = 0;
-    if (P.trace && blockIdx.x == 0 && threadIdx.x == 0) {
-        P.trace[0] = (unsigned long long)PH_DONE;  // start marker
-        P.trace[1] = gtimer();
-        ntr = 1;
+    if (threadIdx.x == 0) {
+        c = ctl_init(P);
+        if (P.trace && blockIdx.x == 0) {
+            P.trace[0] = (unsigned long long)PH_DONE;  // start marker
+            P.trace[1] = gtimer();
+            ntr = 1;
+        }
     }
+    __syncthreads();
     while (c.ph != PH_DONE) {
         exec_phase<T, NF>(P, c, tw, wsm, red);
         if (!grid_barrier(P.sc, gen)) break;
-        if (P.trace && blockIdx.x == 0 && threadIdx.x == 0 && ntr < P.trace_cap) {
-            P.trace[2 * ntr] = (unsigned long long)c.ph;
-            P.trace[2 * ntr + 1] = gtimer();
-            ntr++;
+        if (threadIdx.x == 0) {
+            if (P.trace && blockIdx.x == 0 && ntr < P.trace_cap) {
+                // bit 16: a phase of an incremental (T-transform) base evaluation
+                const bool incb = c.inc && (c.ph == PH_B || c.ph == PH_C || c.ph == PH_D || c.ph == PH_E);
+                P.trace[2 * ntr] = (unsigned long long)c.ph | (incb ? (1ull << 16) : 0ull);
+                P.trace[2 * ntr + 1] = gtimer();
+                ntr++;
+            }
+            ctl_advance<T>(P, c);
         }
-        ctl_advance<T>(P, c);
+        __syncthreads();
     }
     if (P.trace && blockIdx.x == 0 && threadIdx.x == 0) P.sc->ntrace = ntr;
 }
@@ -103,7 +115,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pagd_kernel(Params P) {
 // co-resident CTAs so that the device-wide barrier is safe.
 template <class T, int NF>
 cudaError_t pagd_launch(const Params& P, int grid, int threads, size_t smem, void* stream, int* grid_used) {
-    void (*kern)(Params) = pagd_kernel<T, NF>;
+    void (*kern)(const Params) = pagd_kernel<T, NF>;
     cudaError_t e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -126,6 +138,5 @@ cudaError_t pagd_launch(const Params& P, int grid, int threads, size_t smem, voi
 
 }  // namespace pagd
 
-#define PAGD_INSTANTIATE(NF)                                                                             \
-    template cudaError_t pagd::pagd_launch<float, NF>(const pagd::Params&, int, int, size_t, void*, int*);   \
-    template cudaError_t pagd::pagd_launch<double, NF>(const pagd::Params&, int, int, size_t, void*, int*);
+#define PAGD_INSTANTIATE(T, NF) \
+    template cudaError_t pagd::pagd_launch<T, NF>(const pagd::Params&, int, int, size_t, void*, int*);

@@ -53,7 +53,7 @@ struct pagd_solver {
     size_t ws_bytes;
     char* ws;
     // launch plan
-    int grid, logtw, threads;
+    int grid, logtw, threads, coop;
     size_t smem, warp_bytes;
     // state
     int have_state, step, cur, trace, ref_valid;
@@ -148,6 +148,7 @@ static Params params_for(const pagd_solver* s, char* w) {
     P.npts = s->npts;
     P.inv_npts = 1.0 / (double)s->npts;
     P.warp_bytes = (long long)s->warp_bytes;
+    P.coop = s->coop;
     const double twopi = 6.283185307179586476925286766559;
     P.k0sq = (twopi / s->L[0]) * (twopi / s->L[0]);
     P.k1sq = (twopi / s->L[last]) * (twopi / s->L[last]);
@@ -336,6 +337,14 @@ static void make_plan(pagd_solver* s) {
     }
     if (s->grid < 1) s->grid = 1;
     s->smem = tw_smem_bytes(s->logtw) + (size_t)wpb * s->warp_bytes;
+    // CTA-cooperative units for the passes with FP64 lines when a phase has
+    // fewer units than half the warps (most warps would otherwise idle and an
+    // FP64 line would run on one SM sub-partition); fixed line lengths only.
+    // PAGD_COOP=0 / 1 overrides the choice.
+    s->coop = (fixed_len(s->n[0], s->n[last]) != 0 && 2 * units <= (long long)s->grid * wpb) ? 1 : 0;
+    if (const char* e = std::getenv("PAGD_COOP")) {
+        if ((e[0] == '0' || e[0] == '1') && e[1] == 0) s->coop = fixed_len(s->n[0], s->n[last]) != 0 ? e[0] - '0' : 0;
+    }
 }
 
 // ----------------------------------------------------------------- C ABI
@@ -1129,6 +1138,7 @@ static pagd_status batch_chunk(pagd_batch* b, double dt, int nsteps, double tol,
         PI[i] = run_params(s, nullptr, dt, live[i] ? nsteps : 0, tol);
         PI[i].trace = nullptr;
         PI[i].warp_bytes = (long long)b->warp_bytes;
+        PI[i].coop = 0;  // batch warps own their units: no CTA-wide barriers
         PI[i].logtw = b->logtw;
         st = dzero(s, PI[i].sc, sizeof(Scal));
         if (st != PAGD_OK) return bfail(b, st, s->err.c_str());

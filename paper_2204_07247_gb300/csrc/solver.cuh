@@ -131,6 +131,9 @@ struct Params {
     double* LB64;
     void* YB;
     int ref_valid, refresh;
+    // the passes with an FP64 line run CTA-cooperative units (single-instance
+    // launches with fixed line lengths only)
+    int coop, pad1;
     const double2* tw64;
     const float2* tw32;
     Scal* sc;
@@ -494,6 +497,13 @@ __device__ void col_pass(const Params& P, const Tw& tw, int kin, int kout, const
 // apply step `ap`, so the global loads of up to 16 points are in flight at once.
 
 constexpr int kChunk = 16;  // points per batched load
+// points per batched load for a load record of `bytes`: at most kChunk and at
+// most 384 bytes of records per thread in flight, a power of two
+__host__ __device__ constexpr int chunk_for(int bytes, int n) {
+    int c = kChunk < n ? kChunk : n;
+    while (c > 1 && c * bytes > 384) c >>= 1;
+    return c;
+}
 
 template <int NF> __host__ __device__ __forceinline__ size_t row_fixed_smem(int kin, int szin, int kout, int szout) {
     return 2 * (size_t)(NF + 2) * ((size_t)kin * 2 * szin + (size_t)kout * 2 * szout);
@@ -511,7 +521,7 @@ __device__ void row_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
     constexpr int LOGN = ilog2c(NF), HALF = NF / 2, H1 = HALF + 1, PITCH = NF + 2;
     constexpr int E = NF / kWarp, EH = (H1 + kWarp - 1) / kWarp;
     constexpr int GCH = E < 8 ? E : 8;
-    constexpr int NPT = 2 * E, PCH = NPT < kChunk ? NPT : kChunk;
+    constexpr int NPT = 2 * E, PCH = chunk_for((int)sizeof(S), NPT);
     const int rows = P.rows;
     const long long Hs = P.H;
     const WarpCtx w = warp_ctx(P, smem);
@@ -544,17 +554,27 @@ __device__ void row_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
                 }
             }
         }
+        // the pointwise state of the first chunk is loaded before the
+        // transform, so its latency overlaps the spectra's
+        S st[PCH];
+#pragma unroll
+        for (int q = 0; q < PCH; q++) {
+            const int i = q >> 1, rr = q & 1;
+            const int x = w.lane + kWarp * i;
+            st[q] = ld((long long)(r0 + rr) * NF + x, r0 + rr, x);
+        }
         const CI* Xr = X0;
         if (kin > 0)
             Xr = fft_lines_fixed<+1, TI, LOGN, kMaxK>(X0, X1, PITCH, kin, tw_of<TI>(tw), tw.log, w.lane) ? X1 : X0;
 #pragma unroll 1
         for (int c0 = 0; c0 < NPT; c0 += PCH) {
-            S st[PCH];
+            if (c0 > 0) {
 #pragma unroll
-            for (int q = 0; q < PCH; q++) {
-                const int i = (c0 + q) >> 1, rr = (c0 + q) & 1;
-                const int x = w.lane + kWarp * i;
-                st[q] = ld((long long)(r0 + rr) * NF + x, r0 + rr, x);
+                for (int q = 0; q < PCH; q++) {
+                    const int i = (c0 + q) >> 1, rr = (c0 + q) & 1;
+                    const int x = w.lane + kWarp * i;
+                    st[q] = ld((long long)(r0 + rr) * NF + x, r0 + rr, x);
+                }
             }
 #pragma unroll
             for (int q = 0; q < PCH; q++) {
@@ -611,7 +631,7 @@ __device__ void col_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
     using S = decltype(ld(0, 0));
     constexpr int LOGN = ilog2c(NF), PITCH = NF + 2, E = NF / kWarp;
     constexpr int GCH = E < 8 ? E : 8;
-    constexpr int PCH = E < kChunk ? E : kChunk;
+    constexpr int PCH = chunk_for((int)sizeof(S), E);
     const int ncols = P.ncols;
     const long long Hs = P.H;
     const int kl = kin > kout ? kin : kout;
@@ -631,6 +651,11 @@ __device__ void col_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
                 for (int i = 0; i < GCH; i++) B0[(size_t)f * PITCH + w.lane + kWarp * (c + i)] = v[i];
             }
         }
+        // the per-wavenumber state of the first chunk is loaded before the
+        // transform, so its latency overlaps the line's
+        S st[PCH];
+#pragma unroll
+        for (int q = 0; q < PCH; q++) st[q] = ld(k1, w.lane + kWarp * q);
         const C* Xr = B0;
         C* Xi = B1;
         if (kin > 0) {
@@ -643,9 +668,10 @@ __device__ void col_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
         CO* Xo = (CO*)Xi;
 #pragma unroll 1
         for (int c0 = 0; c0 < E; c0 += PCH) {
-            S st[PCH];
+            if (c0 > 0) {
 #pragma unroll
-            for (int q = 0; q < PCH; q++) st[q] = ld(k1, w.lane + kWarp * (c0 + q));
+                for (int q = 0; q < PCH; q++) st[q] = ld(k1, w.lane + kWarp * (c0 + q));
+            }
 #pragma unroll
             for (int q = 0; q < PCH; q++) {
                 const int k0 = w.lane + kWarp * (c0 + q);
@@ -674,6 +700,170 @@ __device__ void col_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
         warp_sync();
     }
 }
+
+// ------------------------------------------------ CTA-cooperative variants
+//
+// The same passes with one unit per CTA: the threads of the CTA load the
+// unit's lines, transform them together (fft_lines_coop), share the pointwise
+// work and store, with CTA barriers in between.  For phases with fewer units
+// than warps (a 256^2 grid has 128 row units and 129 columns): the work of a
+// unit then runs on all four SM sub-partitions, which is what an FP64 line
+// needs on a part whose FP64 rate per sub-partition is low.  Shared memory is
+// the CTA's slice region (one unit needs no more than one warp's slice).
+
+constexpr int kCoopChunk = 4;  // points per thread whose loads are in flight together
+
+template <class TI, class TO, int NF, class Ld, class Ap>
+__device__ void row_pass_coop(const Params& P, const Tw& tw, int kin, int kout, const cx<TI>* src, cx<TO>* dst,
+                              char* smem, Ld&& ld, Ap&& ap) {
+    using CI = cx<TI>;
+    using CO = cx<TO>;
+    using S = decltype(ld(0ll, 0, 0));
+    constexpr int LOGN = ilog2c(NF), HALF = NF / 2, H1 = HALF + 1, PITCH = NF + 2;
+    const int rows = P.rows;
+    const long long Hs = P.H;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    CI* X0 = (CI*)smem;
+    CI* X1 = X0 + (size_t)kin * PITCH;
+    CO* Y0 = (CO*)(X1 + (size_t)kin * PITCH);
+    CO* Y1 = Y0 + (size_t)kout * PITCH;
+    const TI iscale = (TI)P.inv_npts;
+    for (int u = blockIdx.x; u < rows / 2; u += gridDim.x) {
+        const int r0 = 2 * u;
+        // inverse x-DFT inputs: complex line x of field l packs rows r0, r0 + 1
+        for (int it = tid; it < kin * NF; it += nthr) {
+            const int l = it >> LOGN, x = it & (NF - 1);
+            const int k = (x <= HALF) ? x : NF - x;
+            const CI* s0 = src + (size_t)l * Hs + (size_t)k * rows + r0;
+            CI A = s0[0], B = s0[1];
+            if (x == 0 || x == HALF) { A.y = 0; B.y = 0; }
+            X0[(size_t)l * PITCH + x] = (x <= HALF) ? CI{A.x - B.y, A.y + B.x} : CI{A.x + B.y, B.x - A.y};
+        }
+        const CI* Xr = X0;
+        if (kin > 0) Xr = fft_lines_coop<+1, TI, LOGN>(X0, X1, PITCH, kin, tw_of<TI>(tw), tw.log, tid, nthr) ? X1 : X0;
+        // pointwise: point q = rr NF + x of the unit (consecutive threads, consecutive x)
+        for (int q0 = 0; q0 < 2 * NF; q0 += nthr * kCoopChunk) {
+            S st[kCoopChunk];
+#pragma unroll
+            for (int c = 0; c < kCoopChunk; c++) {
+                const int q = q0 + tid + nthr * c;
+                if (q < 2 * NF) {
+                    const int rr = q >> LOGN, x = q & (NF - 1);
+                    st[c] = ld((long long)(r0 + rr) * NF + x, r0 + rr, x);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < kCoopChunk; c++) {
+                const int q = q0 + tid + nthr * c;
+                if (q < 2 * NF) {
+                    const int rr = q >> LOGN, x = q & (NF - 1);
+                    TI in[kMaxK];
+                    TO out[kMaxK];
+#pragma unroll
+                    for (int f = 0; f < kMaxK; f++) {
+                        if (f < kin) {
+                            const CI z = Xr[(size_t)f * PITCH + x];
+                            in[f] = (rr ? z.y : z.x) * iscale;
+                        }
+                    }
+                    ap((long long)(r0 + rr) * NF + x, r0 + rr, x, st[c], in, out);
+#pragma unroll
+                    for (int g = 0; g < kMaxK; g++) {
+                        if (g < kout) {
+                            CO* qq = Y0 + (size_t)g * PITCH + x;
+                            if (rr) qq->y = out[g];
+                            else qq->x = out[g];
+                        }
+                    }
+                }
+            }
+        }
+        if (kout > 0) {
+            const CO* Yr = fft_lines_coop<-1, TO, LOGN>(Y0, Y1, PITCH, kout, tw_of<TO>(tw), tw.log, tid, nthr) ? Y1 : Y0;
+            const TO hf = (TO)0.5;
+            for (int it = tid; it < kout * H1; it += nthr) {
+                const int g = it / H1, k = it - g * H1;
+                CO* d0 = dst + (size_t)g * Hs + r0;
+                const CO* zl = Yr + (size_t)g * PITCH;
+                const CO zk = zl[k];
+                const CO zn = zl[(NF - k) & (NF - 1)];
+                d0[(size_t)k * rows] = CO{hf * (zk.x + zn.x), hf * (zk.y - zn.y)};
+                d0[(size_t)k * rows + 1] = CO{hf * (zk.y + zn.y), hf * (zn.x - zk.x)};
+            }
+        }
+        cta_sync();  // the next unit reuses the buffers
+    }
+}
+
+template <class TI, class TO, int NF, class Ld, class Ap>
+__device__ void col_pass_coop(const Params& P, const Tw& tw, int kin, int kout, const cx<TI>* src, cx<TO>* dst,
+                              char* smem, Ld&& ld, Ap&& ap) {
+    using C = cx<TI>;
+    using CO = cx<TO>;
+    using S = decltype(ld(0, 0));
+    constexpr int LOGN = ilog2c(NF), PITCH = NF + 2;
+    const int ncols = P.ncols;
+    const long long Hs = P.H;
+    const int kl = kin > kout ? kin : kout;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    C* B0 = (C*)smem;
+    C* B1 = B0 + (size_t)kl * PITCH;
+    for (int k1 = blockIdx.x; k1 < ncols; k1 += gridDim.x) {
+        for (int it = tid; it < kin * NF; it += nthr) {
+            const int f = it >> LOGN, x = it & (NF - 1);
+            B0[(size_t)f * PITCH + x] = src[(size_t)f * Hs + (size_t)k1 * NF + x];
+        }
+        const C* Xr = B0;
+        C* Xi = B1;
+        if (kin > 0) {
+            const int r = fft_lines_coop<-1, TI, LOGN>(B0, B1, PITCH, kin, tw_of<TI>(tw), tw.log, tid, nthr);
+            Xr = r ? B1 : B0;
+            Xi = r ? B0 : B1;
+        }
+        CO* Xo = (CO*)Xi;
+        for (int q0 = 0; q0 < NF; q0 += nthr * kCoopChunk) {
+            S st[kCoopChunk];
+#pragma unroll
+            for (int c = 0; c < kCoopChunk; c++) {
+                const int k0 = q0 + tid + nthr * c;
+                if (k0 < NF) st[c] = ld(k1, k0);
+            }
+#pragma unroll
+            for (int c = 0; c < kCoopChunk; c++) {
+                const int k0 = q0 + tid + nthr * c;
+                if (k0 < NF) {
+                    C in[kMaxK];
+                    CO out[kMaxK];
+#pragma unroll
+                    for (int f = 0; f < kMaxK; f++)
+                        if (f < kin) in[f] = Xr[(size_t)f * PITCH + k0];
+                    ap(k1, k0, st[c], in, out);
+#pragma unroll
+                    for (int g = 0; g < kMaxK; g++)
+                        if (g < kout) Xo[(size_t)g * PITCH + k0] = out[g];
+                }
+            }
+        }
+        if (kout > 0) {
+            CO* scratch = (CO*)Xr;
+            const int r = fft_lines_coop<+1, TO, LOGN>(Xo, scratch, PITCH, kout, tw_of<TO>(tw), tw.log, tid, nthr);
+            const CO* Yr = r ? scratch : Xo;
+            for (int it = tid; it < kout * NF; it += nthr) {
+                const int g = it >> LOGN, x = it & (NF - 1);
+                dst[(size_t)g * Hs + (size_t)k1 * NF + x] = Yr[(size_t)g * PITCH + x];
+            }
+        }
+        cta_sync();
+    }
+}
+
+// Only passes with an FP64 line have the cooperative variant: an FP32 line is
+// latency-bound, not rate-bound, on one sub-partition, and the extra code
+// costs the FP32 passes registers.
+template <class TI, class TO> constexpr bool kHasCoop = sizeof(TI) == 8 || sizeof(TO) == 8;
+// NF | kNoCoop: line length NF without the cooperative variants (batched
+// launches, whose warps own their units, never use them)
+constexpr int kNoCoop = 1 << 20;
 
 // ------------------------------------------------------- middle axis (3D)
 //
@@ -746,42 +936,71 @@ template <class T> __device__ __forceinline__ cx<T>* cdstT(const Params& P) {
     return (cx<T>*)(P.nm > 1 ? P.NB : P.DB);
 }
 
-// dispatch: NF = 0 runs the runtime-length passes
-template <class TI, class TO, int NF, class Ld, class Ap>
+// dispatch: NF = 0 runs the runtime-length passes (NF may carry kNoCoop)
+// COOP: the pass has the CTA-cooperative variant (by default when it has an
+// FP64 line; phases with FP64 pointwise work on T lines ask for it too)
+template <class TI, class TO, int NF, bool COOP = kHasCoop<TI, TO>, class Ld, class Ap>
 __device__ __forceinline__ void rowp(const Params& P, const Tw& tw, int kin, int kout, const cx<TI>* src,
                                      cx<TO>* dst, char* smem, Ld&& ld, Ap&& ap) {
-    if constexpr (NF == 0) {
+    constexpr int L = NF & (kNoCoop - 1);
+    if constexpr (L == 0) {
         row_pass<TI, TO>(P, tw, kin, kout, src, dst, smem,
                          [&](long long p, int row, int x, const TI* in, TO* out) {
                              const auto s = ld(p, row, x);
                              ap(p, row, x, s, in, out);
                          });
     } else {
-        row_pass_fixed<TI, TO, NF>(P, tw, kin, kout, src, dst, smem, ld, ap);
+        if constexpr (COOP && !(NF & kNoCoop)) {
+            if (P.coop) {
+                row_pass_coop<TI, TO, L>(P, tw, kin, kout, src, dst, smem, ld, ap);
+                return;
+            }
+        }
+        row_pass_fixed<TI, TO, L>(P, tw, kin, kout, src, dst, smem, ld, ap);
     }
 }
 
-template <class TI, class TO, int NF, class Ld, class Ap>
+template <class TI, class TO, int NF, bool COOP = kHasCoop<TI, TO>, class Ld, class Ap>
 __device__ __forceinline__ void colp2(const Params& P, const Tw& tw, int kin, int kout, const cx<TI>* src,
                                       cx<TO>* dst, char* smem, Ld&& ld, Ap&& ap) {
-    if constexpr (NF == 0) {
+    constexpr int L = NF & (kNoCoop - 1);
+    if constexpr (L == 0) {
         col_pass<TI, TO>(P, tw, kin, kout, src, dst, smem, [&](int k1, int k0, const cx<TI>* in, cx<TO>* out) {
             const auto s = ld(k1, k0);
             ap(k1, k0, s, in, out);
         });
     } else {
-        col_pass_fixed<TI, TO, NF>(P, tw, kin, kout, src, dst, smem, ld, ap);
+        if constexpr (COOP && !(NF & kNoCoop)) {
+            if (P.coop) {
+                col_pass_coop<TI, TO, L>(P, tw, kin, kout, src, dst, smem, ld, ap);
+                return;
+            }
+        }
+        col_pass_fixed<TI, TO, L>(P, tw, kin, kout, src, dst, smem, ld, ap);
     }
 }
-template <class T, int NF, class Ld, class Ap>
+template <class T, int NF, bool COOP = kHasCoop<T, T>, class Ld, class Ap>
 __device__ __forceinline__ void colp(const Params& P, const Tw& tw, int kin, int kout, const cx<T>* src,
                                      cx<T>* dst, char* smem, Ld&& ld, Ap&& ap) {
-    colp2<T, T, NF>(P, tw, kin, kout, src, dst, smem, ld, ap);
+    colp2<T, T, NF, COOP>(P, tw, kin, kout, src, dst, smem, ld, ap);
 }
 
 struct Nil {};
 
 // ------------------------------------------------------------ phase bodies
+//
+// The FP32 iteration phases (R, CI) are inlined into the persistent kernel
+// (PAGD_HOT), where the parameters are constant-bank operands; the base
+// evaluations (exact and incremental, both with FP64 work per point) and the
+// programs are functions of their own (PAGD_COLD), so that their larger
+// working sets are allocated separately and do not spill registers in the hot
+// phases.
+#ifndef PAGD_HOT
+#define PAGD_HOT __forceinline__
+#endif
+#ifndef PAGD_COLD
+#define PAGD_COLD __noinline__
+#endif
 
 // number of fields in the iteration passes: PFC transforms v^3 differences and
 // inverts d; FCH transforms (dF', dP) and inverts (d, Lap ybar)
@@ -799,7 +1018,7 @@ __host__ __device__ __forceinline__ int k_base(int model) { return model == M_PF
 // y = VB_new - VB_old from the reference point, and (PFC) the nonlinear change
 // VB_new^3 - VB_old^3 = y (3 r^2 + 3 r y + y^2), r = VB_old.
 template <class T, int NF, bool INC>
-__device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red) {
+__device__ __forceinline__ void phase_B_impl(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red) {
     using TO = typename std::conditional<INC, T, double>::type;
     const StepK& k = step_coeffs(P, c.step);
     const int bank = c.step & 1;
@@ -930,6 +1149,15 @@ __device__ void phase_B(const Params& P, const Ctl& c, const Tw& tw, char* smem,
     }
 }
 
+template <class T, int NF>
+__device__ PAGD_COLD void phase_B_exact(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red) {
+    phase_B_impl<T, NF, false>(P, c, tw, smem, red);
+}
+template <class T, int NF>
+__device__ PAGD_COLD void phase_B_inc(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red) {
+    phase_B_impl<T, NF, true>(P, c, tw, smem, red);
+}
+
 // Spectral base gradient C0 = G'_N(VB) (Eqs. misc07 / obj:G'), its
 // preconditioned direction d0 and the first correction delta_1 = theta_v s d0.
 template <class T>
@@ -954,7 +1182,7 @@ __device__ __forceinline__ void base_direction(const Params& P, const StepK& k, 
 }
 
 template <class T, int NF>
-__device__ void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     if (leader(tw)) {
         // fold the last acceptance's mass change into the running excess
         P.mass[0] += P.mass[1];
@@ -1014,7 +1242,7 @@ __device__ void phase_C(const Params& P, const Ctl& c, const Tw& tw, char* smem)
 // FCH: physical Lap VB, then forward x-DFT of (F'(VB), P(VB)) where
 // P = -eps^2 (F'' - eta1) Lap v + (F'' - eta2) F'  (the non-Laplacian part of mu).
 template <class T, int NF>
-__device__ void phase_D(const Params& P, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_D(const Params& P, const Tw& tw, char* smem) {
     T* lbt = (T*)P.LBt;
     const double e2 = P.eps * P.eps;
     rowp<double, double, NF>(P, tw, 1, 2, P.DB64, P.NB64, smem,
@@ -1030,7 +1258,7 @@ __device__ void phase_D(const Params& P, const Tw& tw, char* smem) {
 }
 
 template <class T, int NF>
-__device__ void phase_E(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_E(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     const StepK& k = step_coeffs(P, c.step);
     const Beta B = betas(P, k, c.bsel);
     const double e2 = P.eps * P.eps;
@@ -1060,7 +1288,7 @@ __device__ void phase_E(const Params& P, const Ctl& c, const Tw& tw, char* smem)
 // the new base (v_hat += y_hat, PFC: N_hat += dN_hat) and the base gradient is
 // assembled in FP64 from them and the T-transformed small fields.
 template <class T, int NF>
-__device__ void phase_CN(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_CN(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     using C = cx<T>;
     if (leader(tw)) {
         P.mass[0] += P.mass[1];
@@ -1076,7 +1304,7 @@ __device__ void phase_CN(const Params& P, const Ctl& c, const Tw& tw, char* smem
     const double e4 = P.eps * P.eps * P.eps * P.eps;
     const bool pfc = P.model == M_PFC;
     struct St { double2 v, n, w; };
-    colp<T, NF>(
+    colp<T, NF, true>(
         P, tw, kin, 1, csrcT<T>(P), cdstT<T>(P), smem,
         [&](int k1, int k0) {
             const long long idx = (long long)k1 * P.n0 + k0;
@@ -1122,13 +1350,13 @@ __device__ void phase_CN(const Params& P, const Ctl& c, const Tw& tw, char* smem
 // transforms of the nonlinear changes F'(VB_new) - F'(VB_old) and
 // P(VB_new) - P(VB_old), written as the iteration's difference formulas.
 template <class T, int NF>
-__device__ void phase_DN(const Params& P, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_DN(const Params& P, const Tw& tw, char* smem) {
     using C = cx<T>;
     T* lbt = (T*)P.LBt;
     const T* yb = (const T*)P.YB;
     const T tau = (T)P.tau, e2 = (T)(P.eps * P.eps), eta1 = (T)P.eta1, eta2 = (T)P.eta2;
     struct St { double vb, lb; T y; };
-    rowp<T, T, NF>(
+    rowp<T, T, NF, true>(
         P, tw, 1, 2, (const C*)P.DB, (C*)P.NB, smem,
         [&](long long p, int, int) { return St{P.VB[p], P.LB64[p], yb[p]}; },
         [&](long long p, int, int, const St& s, const T* in, T* out) {
@@ -1149,7 +1377,7 @@ __device__ void phase_DN(const Params& P, const Tw& tw, char* smem) {
 }
 
 template <class T, int NF>
-__device__ void phase_EN(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_EN(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     using C = cx<T>;
     const StepK& k = step_coeffs(P, c.step);
     const Beta B = betas(P, k, c.bsel);
@@ -1157,7 +1385,7 @@ __device__ void phase_EN(const Params& P, const Ctl& c, const Tw& tw, char* smem
     const double l1 = lam_at(P, 1);
     const long long H = P.H;
     struct St { double2 lin, f1, pp; };
-    colp<T, NF>(
+    colp<T, NF, true>(
         P, tw, 2, 2, csrcT<T>(P), cdstT<T>(P), smem,
         [&](int k1, int k0) {
             const long long idx = (long long)k1 * P.n0 + k0;
@@ -1187,7 +1415,7 @@ __device__ void phase_EN(const Params& P, const Ctl& c, const Tw& tw, char* smem
 // delta_it = ybar_{it-1} + theta_v s d_{it-1}; ||d_{it-1}||_inf; then the
 // nonlinear differences at ybar_it and their forward x-DFT.
 template <class TI, class T, int NF>
-__device__ void phase_R(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red,
+__device__ PAGD_HOT void phase_R(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red,
                         const cx<TI>* src) {
     const StepK& k = step_coeffs(P, c.step);
     const int it = c.it;
@@ -1242,7 +1470,7 @@ __device__ void phase_R(const Params& P, const Ctl& c, const Tw& tw, char* smem,
 // zero mode removed), d_hat = r_hat / Lcal_hat (Algorithm 2), the spectral
 // state update, and the inverse y-DFT of d (and of Lap ybar_{it+1} for FCH).
 template <class T, int NF>
-__device__ void phase_CI(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
+__device__ PAGD_HOT void phase_CI(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     using C = cx<T>;
     const StepK& k = step_coeffs(P, c.step);
     const Beta B = betas(P, k, c.bsel);
@@ -1299,7 +1527,7 @@ __device__ void phase_CI(const Params& P, const Ctl& c, const Tw& tw, char* smem
 // accepted inside the next step's phase B.)  The mean of delta is zero in exact
 // arithmetic (Remark on discrete mass conservation) and is removed in FP64.
 template <class T>
-__device__ void phase_accept(const Params& P, const Ctl& c, const Tw& tw, double* red) {
+__device__ PAGD_COLD void phase_accept(const Params& P, const Ctl& c, const Tw& tw, double* red) {
     const StepK& k = step_coeffs(P, c.step);
     const int bank = c.step & 1;
     const T* dc = (const T*)P.DD[c.it & 1];
@@ -1341,26 +1569,26 @@ inline __device__ void phase_fail(const Params& P, const Ctl& c, const Tw& tw) {
 // ------------------------------------------------ DFT / energy / mass programs
 
 template <int NF>
-__device__ void phase_fwd_r(const Params& P, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_fwd_r(const Params& P, const Tw& tw, char* smem) {
     rowp<double, double, NF>(P, tw, 0, 1, (const double2*)nullptr, P.NB64, smem,
                              [&](long long p, int, int) { return P.in_real[p]; },
                              [&](long long, int, int, const double& u, const double*, double* out) { out[0] = u; });
 }
 template <int NF>
-__device__ void phase_fwd_c(const Params& P, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_fwd_c(const Params& P, const Tw& tw, char* smem) {
     colp<double, NF>(P, tw, 1, 0, csrc64(P), (double2*)nullptr, smem, [&](int, int) { return Nil{}; },
                      [&](int k1, int k0, const Nil&, const double2* in, double2*) {
                          P.out_spec[api_spec_index(P, k1, k0)] = in[0];
                      });
 }
 template <int NF>
-__device__ void phase_inv_c(const Params& P, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_inv_c(const Params& P, const Tw& tw, char* smem) {
     colp<double, NF>(P, tw, 0, 1, (const double2*)nullptr, cdst64(P), smem,
                      [&](int k1, int k0) { return P.in_spec[api_spec_index(P, k1, k0)]; },
                      [&](int, int, const double2& v, const double2*, double2* out) { out[0] = v; });
 }
 template <int NF>
-__device__ void phase_inv_r(const Params& P, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_inv_r(const Params& P, const Tw& tw, char* smem) {
     rowp<double, double, NF>(P, tw, 1, 0, P.DB64, (double2*)nullptr, smem,
                              [&](long long, int, int) { return Nil{}; },
                              [&](long long p, int, int, const Nil&, const double* in, double*) {
@@ -1371,7 +1599,7 @@ __device__ void phase_inv_r(const Params& P, const Tw& tw, char* smem) {
 // energy (Eqs. obj:PFC-egy / obj:FCHegy with Fourier differentiation and the
 // trapezoidal rule): red[0] pointwise part, red[1] spectral part
 template <int NF>
-__device__ void phase_en_r(const Params& P, const Tw& tw, char* smem, double* red) {
+__device__ PAGD_COLD void phase_en_r(const Params& P, const Tw& tw, char* smem, double* red) {
     double acc = 0.0;
     const bool pfc = P.model == M_PFC;
     rowp<double, double, NF>(P, tw, 0, 1, (const double2*)nullptr, P.NB64, smem,
@@ -1385,7 +1613,7 @@ __device__ void phase_en_r(const Params& P, const Tw& tw, char* smem, double* re
     }
 }
 template <int NF>
-__device__ void phase_en_c(const Params& P, const Tw& tw, char* smem, double* red) {
+__device__ PAGD_COLD void phase_en_c(const Params& P, const Tw& tw, char* smem, double* red) {
     double acc = 0.0;
     const bool pfc = P.model == M_PFC;
     const int half = P.n1 >> 1;
@@ -1405,7 +1633,7 @@ __device__ void phase_en_c(const Params& P, const Tw& tw, char* smem, double* re
     publish_sum(&P.sc->red[1], acc);
 }
 template <int NF>
-__device__ void phase_en_r2(const Params& P, const Tw& tw, char* smem, double* red) {
+__device__ PAGD_COLD void phase_en_r2(const Params& P, const Tw& tw, char* smem, double* red) {
     double acc = 0.0;
     const double e2 = P.eps * P.eps;
     rowp<double, double, NF>(P, tw, 1, 0, P.DB64, (double2*)nullptr, smem,
@@ -1443,7 +1671,7 @@ inline __device__ void phase_mass(const Params& P, const Tw& tw, double* red) {
 // kappa^2) v_hat with N = v^3; FCH mu_hat = eps^4 kappa^2 v_hat +
 // eps^2 kappa F'_hat + P_hat, P = -eps^2 (F'' - eta1) Lap v + (F'' - eta2) F'.
 template <int NF>
-__device__ void phase_rh_r0(const Params& P, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_rh_r0(const Params& P, const Tw& tw, char* smem) {
     const bool pfc = P.model == M_PFC;
     rowp<double, double, NF>(P, tw, 0, pfc ? 2 : 1, (const double2*)nullptr, P.NB64, smem,
                              [&](long long p, int, int) { return P.in_real[p]; },
@@ -1453,7 +1681,7 @@ __device__ void phase_rh_r0(const Params& P, const Tw& tw, char* smem) {
                              });
 }
 template <int NF>
-__device__ void phase_rh_c0(const Params& P, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_rh_c0(const Params& P, const Tw& tw, char* smem) {
     const bool pfc = P.model == M_PFC;
     colp<double, NF>(P, tw, pfc ? 2 : 1, 1, csrc64(P), cdst64(P), smem, [&](int, int) { return Nil{}; },
                      [&](int k1, int k0, const Nil&, const double2* in, double2* out) {
@@ -1469,7 +1697,7 @@ __device__ void phase_rh_c0(const Params& P, const Tw& tw, char* smem) {
                      });
 }
 template <int NF>
-__device__ void phase_rh_r1(const Params& P, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_rh_r1(const Params& P, const Tw& tw, char* smem) {
     const double e2 = P.eps * P.eps;
     rowp<double, double, NF>(P, tw, 1, 2, P.DB64, P.NB64, smem,
                              [&](long long p, int, int) { return P.in_real[p]; },
@@ -1480,7 +1708,7 @@ __device__ void phase_rh_r1(const Params& P, const Tw& tw, char* smem) {
                              });
 }
 template <int NF>
-__device__ void phase_rh_c1(const Params& P, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_rh_c1(const Params& P, const Tw& tw, char* smem) {
     const double e2 = P.eps * P.eps, e4 = e2 * e2;
     colp<double, NF>(P, tw, 2, 1, csrc64(P), cdst64(P), smem,
                      [&](int k1, int k0) { return P.CL64[(long long)k1 * P.n0 + k0]; },
@@ -1522,7 +1750,7 @@ inline __device__ void phase_est(const Params& P, const Tw& tw) {
 //   IM_C1: (FCH) solve
 //   IM_R2: inverse x-DFT of u^{n+1} -> written over u^{n-1}
 template <int NF>
-__device__ void phase_im_r0(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_im_r0(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     const StepK& k = step_coeffs(P, c.step);
     const double* un = P.U[c.cur];
     const double* um = P.U[c.cur ^ 1];
@@ -1561,7 +1789,7 @@ __device__ __forceinline__ double2 imex_solve(const Params& P, const StepK& k, d
     return double2{rx / den, ry / den};
 }
 template <int NF>
-__device__ void phase_im_c0(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_im_c0(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     const StepK& k = step_coeffs(P, c.step);
     if (P.model == M_PFC) {
         colp<double, NF>(P, tw, 3, 1, csrc64(P), cdst64(P), smem, [&](int, int) { return Nil{}; },
@@ -1581,7 +1809,7 @@ __device__ void phase_im_c0(const Params& P, const Ctl& c, const Tw& tw, char* s
     }
 }
 template <int NF>
-__device__ void phase_im_r1(const Params& P, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_im_r1(const Params& P, const Tw& tw, char* smem) {
     // N(u) = -kappa0 u - eps^2 Lap F'(u) - (eps^2 (F'' - eta1) - kappa2) Lap u + (F'' - eta2) F'
     const double e2 = P.eps * P.eps, kap0 = 1.0 - 2.0 * P.tau * P.tau + P.eta2;
     rowp<double, double, NF>(P, tw, 1, 2, P.DB64, P.NB64, smem,
@@ -1594,7 +1822,7 @@ __device__ void phase_im_r1(const Params& P, const Tw& tw, char* smem) {
                              });
 }
 template <int NF>
-__device__ void phase_im_c1(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_im_c1(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     const StepK& k = step_coeffs(P, c.step);
     const double e2 = P.eps * P.eps;
     struct St { double2 un, um; };
@@ -1611,7 +1839,7 @@ __device__ void phase_im_c1(const Params& P, const Ctl& c, const Tw& tw, char* s
                      });
 }
 template <int NF>
-__device__ void phase_im_r2(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
+__device__ PAGD_COLD void phase_im_r2(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     double* unew = P.U[c.cur ^ 1];
     const bool last = (c.step + 1 == P.nsteps) && P.out_real;
     rowp<double, double, NF>(P, tw, 1, 0, P.DB64, (double2*)nullptr, smem,
@@ -1869,8 +2097,8 @@ template <class T, int NF>
 __device__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red) {
     switch (c.ph) {
         case PH_B:
-            if (c.inc) phase_B<T, NF, true>(P, c, tw, smem, red);
-            else phase_B<T, NF, false>(P, c, tw, smem, red);
+            if (c.inc) phase_B_inc<T, NF>(P, c, tw, smem, red);
+            else phase_B_exact<T, NF>(P, c, tw, smem, red);
             break;
         case PH_C:
             if (c.inc) phase_CN<T, NF>(P, c, tw, smem);

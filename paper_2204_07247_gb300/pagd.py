@@ -34,7 +34,7 @@ EXPORTS = ("pagd_default_opts", "pfc_init", "fch_init", "pagd_workspace_size", "
 # phase identifiers of the persistent kernel's control machine (for traces)
 PHASES = ("B", "C", "D", "E", "R1", "CI", "RI", "ACCEPT", "FAIL", "FWD_R", "FWD_C", "INV_C", "INV_R",
           "EN_R", "EN_C", "EN_R2", "MASS", "IM_R0", "IM_C0", "IM_R1", "IM_C1", "IM_R2", "MF", "MI",
-          "START")
+          "GS", "RH_R0", "RH_C0", "RH_R1", "RH_C1", "RH_R2", "EST", "START")
 
 
 class PagdError(RuntimeError):
@@ -321,8 +321,9 @@ class Solver:
         self._check(self.lib.pagd_set_trace(self._h, 1 if enable else 0), "set_trace")
 
     def get_trace(self, cap=8192, raw=False):
-        """(phase names, end times in us) of the last launch's phases; raw:
-        the identifiers as recorded (bit masks for a batch's global phases)."""
+        """(phase names, end times in us) of the last launch's phases (suffix
+        "/inc": part of an incremental base evaluation); raw: the identifiers
+        as recorded (bit masks for a batch's global phases)."""
         ph = (ctypes.c_int * cap)()
         t = (ctypes.c_double * cap)()
         cnt = ctypes.c_int()
@@ -330,7 +331,8 @@ class Solver:
         n = min(cnt.value, cap)
         if raw:
             return [ph[i] & 0xFFFFFFFF for i in range(n)], np.array(t[:n])
-        return [PHASES[ph[i]] for i in range(n)], np.array(t[:n])
+        return ([PHASES[ph[i] & 0xFFFF] + ("/inc" if ph[i] >> 16 & 1 else "") for i in range(n)],
+                np.array(t[:n]))
 
     def close(self):
         if self._h:

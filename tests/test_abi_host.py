@@ -243,3 +243,38 @@ def test_emulated_mass_error_does_not_accumulate(emu):
         S.run(1e-3, 25, 1e-8, out)
         drift.append(abs(math.fsum(out.ravel()) - m0) / abs(m0))
     assert max(drift) <= 2e-15, drift
+
+
+@pytest.mark.parametrize("case", [c for c in CASES if c[1][0] == c[1][1] and c[1][0] >= 64])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_mixed"])
+def test_emulated_cooperative_passes_match_oracle(emu, case, precision, monkeypatch):
+    """The CTA-cooperative variants of the passes with FP64 lines (chosen for
+    grids with fewer units than warps) follow the same arithmetic: the steps
+    still match the oracle, and the FP64 steps take the same iteration counts."""
+    monkeypatch.setenv("PAGD_COOP", "1")
+    model, n, L, eps, e1, e2, tau, scheme, dt, mean = case
+    S = pagd.Solver(model, n, L, eps, e1, e2, tau, scheme=scheme, precision=precision, lib=emu)
+    P = _oracle_problem(model, n, L, eps, e1, e2, tau, scheme)
+    u0 = I.noisy_field(n, mean, 0.05, 11)
+    S.set_state(u0)
+    out = S.empty_field()
+    tol = 1e-10 if precision == "fp64" else 1e-8
+    its, res = S.run(dt, 3, tol, out)
+    ref, oits = O.run(P, u0, dt, 3, tol)
+    bound = 1e-12 if precision == "fp64" else 1e-6
+    assert np.linalg.norm(out - ref) <= bound * np.linalg.norm(ref)
+    assert all(res <= tol)
+    if precision == "fp64":
+        assert list(its) == list(oits)
+    spec = S.fft_r2c(u0)
+    ref_spec = O.fft(u0.astype(complex))[:, : n[1] // 2 + 1]
+    assert np.abs(spec[..., 0] + 1j * spec[..., 1] - ref_spec).max() <= 1e-13 * np.abs(ref_spec).max()
+
+
+def test_phase_names_follow_the_kernel_enum():
+    src = open(os.path.join(ROOT, "paper_2204_07247_gb300", "csrc", "solver.cuh")).read()
+    body = src[src.index("enum Phase {"):]
+    body = body[: body.index("};")]
+    names = re.findall(r"PH_(\w+)", body)
+    assert len(names) == len(pagd.PHASES)
+    assert [n for n in names[:-1]] == list(pagd.PHASES[:-1]) and names[-1] == "DONE"

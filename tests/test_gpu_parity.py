@@ -278,3 +278,33 @@ def test_step_by_step_equals_run(torch, lib):
     out2 = S2.empty_field()
     S2.run(w.dt, 4, w.tol, out2)
     assert np.abs(host(out) - host(out2)).max() <= 1e-13
+
+
+def test_phase_trace_structure(torch, lib):
+    """The phase trace of an FCH 128^2 FP32-mixed run: times increase, every
+    step starts with a base evaluation (B C D E, then R1), the step's first
+    evaluation is incremental once a reference exists and the last before
+    acceptance is exact, and the R1 / RI records equal the reported evaluation
+    counts."""
+    w = I.FCH256
+    S = pagd.solver_for(w, lib=lib, n=(128, 128))
+    S.set_state(dev(torch, I.noisy_field((128, 128), -0.3, 0.05, 5)))
+    S.run(w.dt, 2, w.tol)
+    S.set_trace(True)
+    its, res = S.run(w.dt, 6, w.tol)
+    names, t = S.get_trace()
+    S.set_trace(False)
+    assert names[0] == "START" and np.all(np.diff(t) >= 0)
+    body = names[1:]
+    assert body.count("R1") + body.count("RI") == int(np.sum(its))
+    assert body[:4] == ["B/inc", "C/inc", "D/inc", "E/inc"]
+    base = [i for i, n in enumerate(body) if n.startswith("B")]
+    for i in base:
+        tag = body[i][1:]
+        assert body[i:i + 5] == ["B" + tag, "C" + tag, "D" + tag, "E" + tag, "R1"]
+    # the evaluation before each acceptance (the next step's B or the final
+    # ACCEPT) is exact
+    accepts = [i for i, n in enumerate(body) if n == "ACCEPT"]
+    assert len(accepts) == 1
+    exact = [i for i in base if body[i] == "B"]
+    assert len(exact) >= 6
