@@ -531,37 +531,56 @@ __device__ void row_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
     CO* Y1 = Y0 + (size_t)kout * PITCH;
     const TI iscale = (TI)P.inv_npts;
     const URange ur = units_of(tw, rows / 2);
+    constexpr int NCH = E / GCH;  // load chunks per field
     for (int u = ur.b; u < ur.e; u += ur.s) {
         const int r0 = 2 * u;
-        for (int l = 0; l < kin; l++) {
-            const CI* s0 = src + (size_t)l * Hs + r0;
-#pragma unroll
-            for (int c = 0; c < E; c += GCH) {
-                CI a[GCH], b[GCH];
-#pragma unroll
-                for (int i = 0; i < GCH; i++) {
-                    const int x = w.lane + kWarp * (c + i);
-                    const int k = (x <= HALF) ? x : NF - x;
-                    a[i] = s0[(size_t)k * rows];
-                    b[i] = s0[(size_t)k * rows + 1];
-                }
-#pragma unroll
-                for (int i = 0; i < GCH; i++) {
-                    const int x = w.lane + kWarp * (c + i);
-                    CI A = a[i], B = b[i];
-                    if (x == 0 || x == HALF) { A.y = 0; B.y = 0; }
-                    X0[(size_t)l * PITCH + x] = (x <= HALF) ? CI{A.x - B.y, A.y + B.x} : CI{A.x + B.y, B.x - A.y};
-                }
-            }
-        }
-        // the pointwise state of the first chunk is loaded before the
-        // transform, so its latency overlaps the spectra's
+        // the pointwise state of the first chunk is loaded first, so that its
+        // latency overlaps the spectra's and the transform's
         S st[PCH];
 #pragma unroll
         for (int q = 0; q < PCH; q++) {
             const int i = q >> 1, rr = q & 1;
             const int x = w.lane + kWarp * i;
             st[q] = ld((long long)(r0 + rr) * NF + x, r0 + rr, x);
+        }
+        // spectra of the kin fields, chunk t = (field, GCH points); FP32 lines
+        // load chunk t + 1 before storing chunk t to shared memory (the
+        // compiler cannot move a global load above a shared store itself)
+        auto load_chunk = [&](int t, CI* a, CI* b) {
+            const int l = t / NCH, c = (t % NCH) * GCH;
+            const CI* s0 = src + (size_t)l * Hs + r0;
+#pragma unroll
+            for (int i = 0; i < GCH; i++) {
+                const int x = w.lane + kWarp * (c + i);
+                const int k = (x <= HALF) ? x : NF - x;
+                a[i] = s0[(size_t)k * rows];
+                b[i] = s0[(size_t)k * rows + 1];
+            }
+        };
+        auto put_chunk = [&](int t, const CI* a, const CI* b) {
+            const int l = t / NCH, c = (t % NCH) * GCH;
+#pragma unroll
+            for (int i = 0; i < GCH; i++) {
+                const int x = w.lane + kWarp * (c + i);
+                CI A = a[i], B = b[i];
+                if (x == 0 || x == HALF) { A.y = 0; B.y = 0; }
+                X0[(size_t)l * PITCH + x] = (x <= HALF) ? CI{A.x - B.y, A.y + B.x} : CI{A.x + B.y, B.x - A.y};
+            }
+        };
+        const int nt = kin * NCH;
+        if constexpr (sizeof(TI) == 4) {
+            CI a[2][GCH], b[2][GCH];
+#pragma unroll
+            for (int t = 0; t <= kMaxK * NCH; t++) {
+                if (t < nt) load_chunk(t, a[t & 1], b[t & 1]);
+                if (t >= 1 && t <= nt) put_chunk(t - 1, a[(t - 1) & 1], b[(t - 1) & 1]);
+            }
+        } else {
+            for (int t = 0; t < nt; t++) {
+                CI a[GCH], b[GCH];
+                load_chunk(t, a, b);
+                put_chunk(t, a, b);
+            }
         }
         const CI* Xr = X0;
         if (kin > 0)
@@ -639,23 +658,41 @@ __device__ void col_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
     C* B0 = (C*)w.mem;
     C* B1 = B0 + (size_t)kl * PITCH;
     const URange ur = units_of(tw, ncols);
+    constexpr int NCH = E / GCH;  // load chunks per field
     for (int k1 = ur.b; k1 < ur.e; k1 += ur.s) {
-        for (int f = 0; f < kin; f++) {
-            const C* s = src + (size_t)f * Hs + (size_t)k1 * NF;
-#pragma unroll
-            for (int c = 0; c < E; c += GCH) {
-                C v[GCH];
-#pragma unroll
-                for (int i = 0; i < GCH; i++) v[i] = s[w.lane + kWarp * (c + i)];
-#pragma unroll
-                for (int i = 0; i < GCH; i++) B0[(size_t)f * PITCH + w.lane + kWarp * (c + i)] = v[i];
-            }
-        }
-        // the per-wavenumber state of the first chunk is loaded before the
-        // transform, so its latency overlaps the line's
+        // the per-wavenumber state of the first chunk is loaded first, so that
+        // its latency overlaps the lines' and the transform's
         S st[PCH];
 #pragma unroll
         for (int q = 0; q < PCH; q++) st[q] = ld(k1, w.lane + kWarp * q);
+        // lines of the kin fields, chunk t = (field, GCH points); FP32 lines
+        // load chunk t + 1 before storing chunk t to shared memory
+        auto load_chunk = [&](int t, C* v) {
+            const int f = t / NCH, c = (t % NCH) * GCH;
+            const C* s = src + (size_t)f * Hs + (size_t)k1 * NF;
+#pragma unroll
+            for (int i = 0; i < GCH; i++) v[i] = s[w.lane + kWarp * (c + i)];
+        };
+        auto put_chunk = [&](int t, const C* v) {
+            const int f = t / NCH, c = (t % NCH) * GCH;
+#pragma unroll
+            for (int i = 0; i < GCH; i++) B0[(size_t)f * PITCH + w.lane + kWarp * (c + i)] = v[i];
+        };
+        const int nt = kin * NCH;
+        if constexpr (sizeof(TI) == 4) {
+            C v[2][GCH];
+#pragma unroll
+            for (int t = 0; t <= kMaxK * NCH; t++) {
+                if (t < nt) load_chunk(t, v[t & 1]);
+                if (t >= 1 && t <= nt) put_chunk(t - 1, v[(t - 1) & 1]);
+            }
+        } else {
+            for (int t = 0; t < nt; t++) {
+                C v[GCH];
+                load_chunk(t, v);
+                put_chunk(t, v);
+            }
+        }
         const C* Xr = B0;
         C* Xi = B1;
         if (kin > 0) {
