@@ -121,6 +121,13 @@ class ClockSampler:
 # spectral states and C0; write a state and the direction's half spectrum); 3D
 # adds the middle passes (read + write one half spectrum each way, 16.1 B)
 ITER_BYTES_2D_PFC = 48.3
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per time step of
+# the dominant kernel, from one ncu capture of a short launch of the same
+# kernel build on the same workload; the roofline's traffic is this times the
+# steps of one timed launch (the per-step traffic is flat once the working set
+# is resident).  Workloads without a capture report null.
+TRAFFIC_PER_STEP = {"fch2d_256_bdf2_fp32mixed": 2.515e6}
+BATCH_TRAFFIC_PER_STEP = {"pfc2d_batch96_128_256_512_mp_fp32mixed": 10.32e9}
 ITER_BYTES_3D_PFC = 64.4
 
 
@@ -182,7 +189,10 @@ def bench_batch(torch, pagd, bw, steps, warm, plain_steps, bytes_per_eval, peak,
         "plain_member_steps_per_s": m * plain_steps / (plain_ms / 1000.0),
         "plain_sample": f"each member alone, {plain_steps} steps after {warm} warm-up steps",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "pagd_batch_kernel<float>",
+                     "frac": achieved / peak,
+                     "traffic": (BATCH_TRAFFIC_PER_STEP[bw.name] * steps / math.ceil(steps / 4096)
+                                 if bw.name in BATCH_TRAFFIC_PER_STEP else None),
+                     "kernel": "pagd_batch_kernel<float>",
                      "bytes_model": f"{bytes_per_eval} B per point per residual evaluation of the "
                                     f"iteration passes x sum over members of points x evaluations "
                                     f"({nbytes / 1e9:.1f} GB); base evaluations not counted"},
@@ -468,7 +478,9 @@ def main():
     launches = math.ceil(K / 4096)
     achieved = bpp * n_pts * evals / launches / ((ms / 1000.0) / launches) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+            "frac": achieved / peak,
+            "traffic": TRAFFIC_PER_STEP[w.name] * K / launches if w.name in TRAFFIC_PER_STEP else None,
+            "peak_kind": peak_kind,
             "kernel": "pagd_kernel<float>",
             "bytes_model": f"{bpp} B per grid point per residual evaluation x {n_pts} points x "
                            f"{evals} evaluations"}

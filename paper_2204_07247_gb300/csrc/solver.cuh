@@ -2130,8 +2130,14 @@ __device__ void ctl_step(const Params& P, Ctl& c) {
     }
 }
 
+// Every phase but the iteration and middle passes.  PAGD_DISPATCH chooses
+// whether this switch is inlined into the kernel (default) or is one outlined
+// call site, which keeps the calls' register saving out of the hot passes.
+#ifndef PAGD_DISPATCH
+#define PAGD_DISPATCH __forceinline__
+#endif
 template <class T, int NF>
-__device__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red) {
+__device__ PAGD_DISPATCH void exec_cold(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red) {
     switch (c.ph) {
         case PH_B:
             if (c.inc) phase_B_inc<T, NF>(P, c, tw, smem, red);
@@ -2149,9 +2155,6 @@ __device__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* sm
             if (c.inc) phase_EN<T, NF>(P, c, tw, smem);
             else phase_E<T, NF>(P, c, tw, smem);
             break;
-        case PH_R1: phase_R<T, T, NF>(P, c, tw, smem, red, (const cx<T>*)P.DB); break;
-        case PH_RI: phase_R<T, T, NF>(P, c, tw, smem, red, (const cx<T>*)P.DB); break;
-        case PH_CI: phase_CI<T, NF>(P, c, tw, smem); break;
         case PH_ACCEPT: phase_accept<T>(P, c, tw, red); break;
         case PH_FAIL: phase_fail(P, c, tw); break;
         case PH_FWD_R: phase_fwd_r<NF>(P, tw, smem); break;
@@ -2169,6 +2172,21 @@ __device__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* sm
         case PH_RH_C1: phase_rh_c1<NF>(P, tw, smem); break;
         case PH_RH_R2: phase_inv_r<NF>(P, tw, smem); break;
         case PH_EST: phase_est(P, tw); break;
+        case PH_IM_R0: phase_im_r0<NF>(P, c, tw, smem); break;
+        case PH_IM_C0: phase_im_c0<NF>(P, c, tw, smem); break;
+        case PH_IM_R1: phase_im_r1<NF>(P, tw, smem); break;
+        case PH_IM_C1: phase_im_c1<NF>(P, c, tw, smem); break;
+        case PH_IM_R2: phase_im_r2<NF>(P, c, tw, smem); break;
+        default: break;
+    }
+}
+
+template <class T, int NF>
+__device__ __forceinline__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red) {
+    switch (c.ph) {
+        case PH_R1:
+        case PH_RI: phase_R<T, T, NF>(P, c, tw, smem, red, (const cx<T>*)P.DB); break;
+        case PH_CI: phase_CI<T, NF>(P, c, tw, smem); break;
         case PH_MF:
             if (c.m64) mid_pass<double, -1>(P, tw, c.mk, P.NB64, P.X64, smem);
             else mid_pass<T, -1>(P, tw, c.mk, (const cx<T>*)P.NB, (cx<T>*)P.X, smem);
@@ -2177,12 +2195,7 @@ __device__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* sm
             if (c.m64) mid_pass<double, +1>(P, tw, c.mk, P.NB64, P.DB64, smem);
             else mid_pass<T, +1>(P, tw, c.mk, (const cx<T>*)P.NB, (cx<T>*)P.DB, smem);
             break;
-        case PH_IM_R0: phase_im_r0<NF>(P, c, tw, smem); break;
-        case PH_IM_C0: phase_im_c0<NF>(P, c, tw, smem); break;
-        case PH_IM_R1: phase_im_r1<NF>(P, tw, smem); break;
-        case PH_IM_C1: phase_im_c1<NF>(P, c, tw, smem); break;
-        case PH_IM_R2: phase_im_r2<NF>(P, c, tw, smem); break;
-        default: break;
+        default: exec_cold<T, NF>(P, c, tw, smem, red); break;
     }
 }
 
