@@ -126,8 +126,8 @@ ITER_BYTES_2D_PFC = 48.3
 # kernel build on the same workload; the roofline's traffic is this times the
 # steps of one timed launch (the per-step traffic is flat once the working set
 # is resident).  Workloads without a capture report null.
-TRAFFIC_PER_STEP = {"fch2d_256_bdf2_fp32mixed": 2.515e6}
-BATCH_TRAFFIC_PER_STEP = {"pfc2d_batch96_128_256_512_mp_fp32mixed": 10.32e9}
+TRAFFIC_PER_STEP = {"fch2d_256_bdf2_fp32mixed": 2.808e6}
+BATCH_TRAFFIC_PER_STEP = {"pfc2d_batch96_128_256_512_mp_fp32mixed": 10.40e9}
 ITER_BYTES_3D_PFC = 64.4
 
 
