@@ -916,12 +916,17 @@ __host__ __device__ __forceinline__ size_t mid_warp_smem(int nm, int sz) {
 }
 __host__ __device__ __forceinline__ int mid_units(const Params& P) { return P.h1 * (P.n0 / kMidG); }
 
-template <class T, int S>
+template <class T, int S, int NF>
 __device__ void mid_pass(const Params& P, const Tw& tw, int k, const cx<T>* src, cx<T>* dst, char* smem) {
     using C = cx<T>;
+    constexpr int L = NF & (kNoCoop - 1);  // fixed line length of the launch (0: runtime)
+    // values per lane loaded before any of them is stored to shared memory
+    // (the compiler cannot move a global load above a shared store itself)
+    constexpr int CH = sizeof(T) == 4 ? 16 : 8;
     const int nm = P.nm, logm = P.logm, n0 = P.n0, rows = P.rows, gpp = P.n0 / kMidG;
     const long long H = P.H;
     const int pitch = pitch_of(nm);
+    const int nv = kMidG * nm;
     const WarpCtx w = warp_ctx(P, smem);
     C* B0 = (C*)w.mem;
     C* B1 = B0 + (size_t)kMidG * pitch;
@@ -933,20 +938,44 @@ __device__ void mid_pass(const Params& P, const Tw& tw, int k, const cx<T>* src,
             C* df = dst + (size_t)f * H;
             const size_t rowbase = (size_t)k1 * rows + (size_t)i0 * nm;    // [k1][i0][i1]
             const size_t colbase = (size_t)k1 * nm * n0 + (size_t)i0;      // [k1][km][i0]
-            for (int j = w.lane; j < kMidG * nm; j += kWarp) {
-                if (S < 0) {
-                    const int g = j >> logm, i1 = j & (nm - 1);
-                    B0[g * pitch + i1] = sf[rowbase + j];
-                } else {
-                    const int km = j / kMidG, g = j - km * kMidG;
-                    B0[g * pitch + km] = sf[colbase + (size_t)km * n0 + g];
+            for (int j0 = 0; j0 < nv; j0 += CH * kWarp) {
+                C v[CH];
+#pragma unroll
+                for (int q = 0; q < CH; q++) {
+                    const int j = j0 + w.lane + q * kWarp;
+                    if (j < nv) {
+                        if (S < 0) v[q] = sf[rowbase + j];
+                        else v[q] = sf[colbase + (size_t)(j / kMidG) * n0 + (j % kMidG)];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < CH; q++) {
+                    const int j = j0 + w.lane + q * kWarp;
+                    if (j < nv) {
+                        if (S < 0) {
+                            B0[(j >> logm) * pitch + (j & (nm - 1))] = v[q];
+                        } else {
+                            const int km = j / kMidG, g = j - km * kMidG;
+                            B0[g * pitch + km] = v[q];
+                        }
+                    }
                 }
             }
             int r = 0;
-            for (int g = 0; g < kMidG; g++)
-                r = fft_line_w<S, T>(B0 + g * pitch, B1 + g * pitch, logm, tw_of<T>(tw), tw.log, w.lane);
+            if constexpr (L > 0) {
+                if (nm == L) {
+                    // cubic grid: both lines in lockstep through the fixed-length stages
+                    r = fft_lines_fixed<S, T, ilog2c(L), kMidG>(B0, B1, pitch, kMidG, tw_of<T>(tw), tw.log, w.lane);
+                } else {
+                    for (int g = 0; g < kMidG; g++)
+                        r = fft_line_w<S, T>(B0 + g * pitch, B1 + g * pitch, logm, tw_of<T>(tw), tw.log, w.lane);
+                }
+            } else {
+                for (int g = 0; g < kMidG; g++)
+                    r = fft_line_w<S, T>(B0 + g * pitch, B1 + g * pitch, logm, tw_of<T>(tw), tw.log, w.lane);
+            }
             const C* Br = r ? B1 : B0;
-            for (int j = w.lane; j < kMidG * nm; j += kWarp) {
+            for (int j = w.lane; j < nv; j += kWarp) {
                 if (S < 0) {
                     const int km = j / kMidG, g = j - km * kMidG;
                     df[colbase + (size_t)km * n0 + g] = Br[g * pitch + km];
@@ -2188,12 +2217,12 @@ __device__ __forceinline__ void exec_phase(const Params& P, const Ctl& c, const 
         case PH_RI: phase_R<T, T, NF>(P, c, tw, smem, red, (const cx<T>*)P.DB); break;
         case PH_CI: phase_CI<T, NF>(P, c, tw, smem); break;
         case PH_MF:
-            if (c.m64) mid_pass<double, -1>(P, tw, c.mk, P.NB64, P.X64, smem);
-            else mid_pass<T, -1>(P, tw, c.mk, (const cx<T>*)P.NB, (cx<T>*)P.X, smem);
+            if (c.m64) mid_pass<double, -1, NF>(P, tw, c.mk, P.NB64, P.X64, smem);
+            else mid_pass<T, -1, NF>(P, tw, c.mk, (const cx<T>*)P.NB, (cx<T>*)P.X, smem);
             break;
         case PH_MI:
-            if (c.m64) mid_pass<double, +1>(P, tw, c.mk, P.NB64, P.DB64, smem);
-            else mid_pass<T, +1>(P, tw, c.mk, (const cx<T>*)P.NB, (cx<T>*)P.DB, smem);
+            if (c.m64) mid_pass<double, +1, NF>(P, tw, c.mk, P.NB64, P.DB64, smem);
+            else mid_pass<T, +1, NF>(P, tw, c.mk, (const cx<T>*)P.NB, (cx<T>*)P.DB, smem);
             break;
         default: exec_cold<T, NF>(P, c, tw, smem, red); break;
     }

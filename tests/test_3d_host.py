@@ -95,3 +95,45 @@ def test_emulated_3d_batch_with_2d_members(emu, monkeypatch):
         ref, _ = O.run(P, u0, 0.5, 3, 1e-8)
         un = S.get_state()[0]
         assert np.linalg.norm(un - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_emulated_3d_cubic_fixed_length_middle_pass(emu):
+    """A cubic 64^3 grid runs the middle passes through the fixed-length
+    stages (both lines of a unit in lockstep): DFT round trip and two FP64
+    steps against the oracle."""
+    n, L = (64, 64, 64), (16 * math.pi,) * 3
+    u = I.noisy_field(n, -0.25, 0.1, 5)
+    S = pagd.Solver("pfc", n, L, 0.3, lib=emu)
+    spec = S.fft_r2c(u)
+    ref = O.fft(u.astype(complex))[..., : n[-1] // 2 + 1]
+    assert np.abs(spec[..., 0] + 1j * spec[..., 1] - ref).max() <= 1e-13 * np.abs(ref).max()
+    assert np.abs(S.fft_c2r(spec) - u).max() <= 1e-14
+    P = O.Problem(O.PFC, n, L, 0.3, 0, 0, 0, scheme=O.BDF2)
+    S.set_state(u)
+    out = S.empty_field()
+    its, res = S.run(0.5, 2, 1e-10, out)
+    uref, oits = O.run(P, u, 0.5, 2, 1e-10)
+    assert np.linalg.norm(out - uref) <= 1e-12 * np.linalg.norm(uref)
+    assert list(its) == list(oits)
+
+
+def test_emulated_fp64_batch_with_cubic_member(emu, monkeypatch):
+    """An FP64 batch of a cubic 64^3 member beside a 64^2 member: both match
+    the oracle with the oracle's iteration counts."""
+    monkeypatch.setenv("PAGD_EMU_SMS", "3")
+    cases = [("pfc", (64, 64, 64), (16 * math.pi,) * 3, 0.3, "bdf2", -0.25),
+             ("pfc", (64, 64), (32 * math.pi,) * 2, 0.25, "bdf2", 0.1)]
+    solvers, u0s = [], []
+    for i, (model, n, L, eps, scheme, mean) in enumerate(cases):
+        S = pagd.Solver(model, n, L, eps, scheme=scheme, precision="fp64", lib=emu)
+        u0 = I.noisy_field(n, mean, 0.1, 30 + i)
+        S.set_state(u0)
+        solvers.append(S)
+        u0s.append(u0)
+    its, res, status = pagd.Batch(solvers).run(0.5, 2, 1e-10)
+    assert list(status) == [0, 0]
+    for (model, n, L, eps, scheme, mean), S, u0, it in zip(cases, solvers, u0s, its):
+        P = O.Problem(O.PFC, n, L, eps, scheme=O.BDF2)
+        ref, oits = O.run(P, u0, 0.5, 2, 1e-10)
+        assert np.linalg.norm(S.get_state()[0] - ref) <= 1e-12 * np.linalg.norm(ref)
+        assert list(it) == list(oits)
