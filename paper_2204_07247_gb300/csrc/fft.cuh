@@ -7,7 +7,9 @@
 // length-R DFT in registers and writes the results at
 // (j div Ns) Ns R + (j mod Ns) + r Ns (the Stockham autosort recursion: natural
 // order, no bit reversal).  Stages ping-pong between two buffers and are
-// separated by __syncwarp only: no CTA-wide barrier inside a transform.
+// separated by __syncwarp only: no CTA-wide barrier inside a transform.  (The
+// CTA-cooperative variant at the end of this file shares the lines of one unit
+// among all warps of a CTA and separates its stages by CTA barriers.)
 //
 // The transforms are the DFT of Sec. 3.2 (Fourier collocation): forward
 // unnormalised with sign -1, inverse with sign +1; the 1/n_pts factor of the

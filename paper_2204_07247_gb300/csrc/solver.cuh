@@ -5,8 +5,9 @@
 // CTA evaluates the same control state machine after each barrier, so all CTAs
 // agree on the next phase without any host round trip.
 //
-// Phases are of two kinds, both built from warp-owned lines (no CTA-wide
-// barrier inside a phase):
+// Phases are of two kinds, built from warp-owned lines (no CTA-wide barrier
+// inside a phase) or, for phases with FP64 work on grids with fewer units than
+// warps, from CTA-cooperative units (all warps of a CTA on one unit):
 //   row pass    -- per unit of one or two rows: inverse x-DFT of K_in fields
 //                  from the column-major half-spectrum buffer, a pointwise
 //                  functor, forward x-DFT of K_out fields back to such a buffer;
