@@ -36,8 +36,11 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        try:  # OpenMP only parallelises the line transforms; without it they run serially
+            subprocess.check_call(cmd[:4] + ["-fopenmp"] + cmd[4:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(cmd)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -65,6 +68,7 @@ def lib():
         D = ctypes.POINTER(ctypes.c_double)
         P = ctypes.POINTER(_Params)
         I = ctypes.POINTER(ctypes.c_int)
+        _lib.orc_set_threads.argtypes = [ctypes.c_int]
         _lib.orc_fft.argtypes = [ctypes.c_int, I, D, ctypes.c_int]
         _lib.orc_dft_brute.argtypes = [ctypes.c_int, I, D, D, ctypes.c_int]
         _lib.orc_frac_lap.argtypes = [P, D, D, ctypes.c_int]
@@ -133,6 +137,12 @@ class Problem:
             p.eta[j] = e
         p.max_iter, p.theta_mode, p.accel = self.max_iter, self.theta_mode, self.accel
         return p
+
+
+def set_threads(n: int) -> None:
+    """Threads for the oracle's line transforms (default 1).  Results do not
+    depend on the count (each line is transformed as with one thread)."""
+    lib().orc_set_threads(int(n))
 
 
 def fft(x: np.ndarray, sign: int = -1) -> np.ndarray:

@@ -138,6 +138,16 @@ static void fft_line(cplx *a, int n, int sign) {
 }
 
 /* multi-dimensional complex FFT over a row-major grid, in place, unnormalised */
+/* Threads for the line transforms of fft_nd (default 1; OpenMP builds only).
+ * The lines of one axis are independent and each is transformed exactly as
+ * with one thread, so no result depends on the count. */
+static int orc_nthreads = 1;
+
+int orc_set_threads(int t) {
+    orc_nthreads = t < 1 ? 1 : t;
+    return ORC_OK;
+}
+
 static int fft_nd(int dim, const int *n, cplx *a, int sign) {
     long tot = 1;
     int maxn = 1;
@@ -146,20 +156,28 @@ static int fft_nd(int dim, const int *n, cplx *a, int sign) {
         tot *= n[d];
         if (n[d] > maxn) maxn = n[d];
     }
-    cplx *line = (cplx *)malloc(sizeof(cplx) * (size_t)maxn);
     for (int d = 0; d < dim; d++) {
         long stride = 1;
         for (int e = d + 1; e < dim; e++) stride *= n[e];
         long nlines = tot / n[d];
-        for (long l = 0; l < nlines; l++) {
-            long inner = l % stride, outer = l / stride;
-            long base = outer * stride * n[d] + inner;
-            for (int i = 0; i < n[d]; i++) line[i] = a[base + (long)i * stride];
-            fft_line(line, n[d], sign);
-            for (int i = 0; i < n[d]; i++) a[base + (long)i * stride] = line[i];
+#ifdef _OPENMP
+#pragma omp parallel num_threads(orc_nthreads) if (orc_nthreads > 1)
+#endif
+        {
+            cplx *line = (cplx *)malloc(sizeof(cplx) * (size_t)maxn);
+#ifdef _OPENMP
+#pragma omp for schedule(static)
+#endif
+            for (long l = 0; l < nlines; l++) {
+                long inner = l % stride, outer = l / stride;
+                long base = outer * stride * n[d] + inner;
+                for (int i = 0; i < n[d]; i++) line[i] = a[base + (long)i * stride];
+                fft_line(line, n[d], sign);
+                for (int i = 0; i < n[d]; i++) a[base + (long)i * stride] = line[i];
+            }
+            free(line);
         }
     }
-    free(line);
     return ORC_OK;
 }
 

@@ -475,3 +475,24 @@ def test_learned_guess_mass_projection():
     r = O.pagd_step(P, 0, u0, u0, 0.01, 0.01, 1e-12, guess=g)
     assert r.status == O.OK and r.iters <= 2
     assert np.abs(r.u - ref.u).max() <= 1e-10
+
+
+def test_thread_count_does_not_change_results():
+    """The oracle's line transforms may run on several host threads (the
+    CPU baseline); every line is transformed as with one thread, so the
+    transforms and a whole PAGD step are bit-identical."""
+    n = (64, 32)
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    P = O.Problem(O.FCH, n, (2 * math.pi, math.pi), 0.18, 0.05, 0.07, 0.1, scheme=O.BDF2)
+    u = -0.3 + 0.05 * rng.uniform(-1, 1, n)
+    out = {}
+    try:
+        for th in (1, 4):
+            O.set_threads(th)
+            r = O.pagd_step(P, 0, u, u.copy(), 0.01, 0.01, 1e-10)
+            out[th] = (O.fft(x), r.u, r.iters)
+    finally:
+        O.set_threads(1)
+    assert np.array_equal(out[1][0], out[4][0])
+    assert np.array_equal(out[1][1], out[4][1]) and out[1][2] == out[4][2]
