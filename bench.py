@@ -293,6 +293,61 @@ def oracle_steps_per_s(w, budget_s=15.0, max_steps=20, warm=0, threads=1):
     return nst / dt, nst, float(np.mean(its)), dt
 
 
+def _oracle_problem(w, n=None, L=None):
+    from oracle import oracle as O
+    return O.Problem(O.PFC if w.model == "pfc" else O.FCH, n or w.n, L or w.L, w.eps, w.eta1, w.eta2, w.tau,
+                     scheme={"bdf2": O.BDF2, "mp": O.MP, "lbdf2": O.LBDF2, "lmp": O.LMP}[w.scheme],
+                     s=w.s, eta=w.eta, max_iter=w.max_iter)
+
+
+def oracle_batch_baseline(bw, steps=2, threads=1):
+    """The oracle on the batch's members, one of each grid size (the sizes are
+    equal shares of the batch), `steps` steps each: member steps per second."""
+    from oracle import oracle as O
+    O.set_threads(threads)
+    picked, seen = [], set()
+    for m in bw.members:
+        if m.n not in seen:
+            seen.add(m.n)
+            picked.append(m)
+    tot, done = 0.0, 0
+    for m in picked:
+        P = _oracle_problem(m)
+        un = m.u0(m.seeds[0])
+        unm1 = un.copy()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            r = O.pagd_step(P, k, un, unm1, bw.dt, bw.dt, bw.tol)
+            unm1, un = un, r.u
+        tot += time.perf_counter() - t0
+        done += steps
+    return {"value": done / tot, "unit": "member steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"{steps} steps of one member of each size ({', '.join(str(m.n) for m in picked)}), "
+                      f"{tot:.1f} s, FP64 C oracle, {threads} threads on its line transforms"}
+
+
+def oracle_3d_estimate(w, n_small=64, threads=1):
+    """The oracle on the same 3D problem at n_small^3 with the same spacing,
+    one step, extrapolated to the full grid by points x log2(points): an
+    estimate of member steps per second, labelled as such."""
+    from oracle import oracle as O
+    from paper_2204_07247_gb300 import inputs as I
+    O.set_threads(threads)
+    n = (n_small,) * len(w.n)
+    L = tuple(l * n_small / nn for l, nn in zip(w.L, w.n))
+    P = _oracle_problem(w, n, L)
+    un = I.noisy_field(n, w.mean, w.amp, w.seeds[0])
+    t0 = time.perf_counter()
+    r = O.pagd_step(P, 0, un, un.copy(), w.dt, w.dt, w.tol)
+    t = time.perf_counter() - t0
+    big, small = float(np.prod(w.n)), float(np.prod(n))
+    scale = big * math.log2(big) / (small * math.log2(small))
+    return {"value": 1.0 / (t * scale), "unit": "member steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"estimate: one step at {n_small}^3 (same spacing, {r.iters} evaluations, {t:.1f} s) "
+                      f"scaled by points x log2(points) ({scale:.0f}x) to {w.n}; FP64 C oracle, "
+                      f"{threads} threads on its line transforms"}
+
+
 def run_reference(args, w, rank):
     if rank != 0:
         return 0
@@ -488,6 +543,11 @@ def main():
                               w3.dt, w3.steps, w3.tol)
         extra["pfc3d"] = bench_batch(torch, pagd, bw3, w3.steps, W, 5, ITER_BYTES_3D_PFC, peak, rank,
                                      world, dist)
+        if rank == 0 and not args.no_cpu_baseline:
+            if extra["batched"]:
+                extra["batched"]["cpu_baseline"] = oracle_batch_baseline(I.PFC_BATCH96, 2, host_cores())
+            if extra["pfc3d"]:
+                extra["pfc3d"]["cpu_baseline"] = oracle_3d_estimate(w3, 64, host_cores())
 
     if rank != 0:
         if dist:
