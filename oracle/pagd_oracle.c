@@ -23,7 +23,7 @@
  *   - the linear IMEX schemes LBDF2 / LMP (Eq. eqn:FCH-semidis-simplicit and
  *     Sec. 3.3).
  *
- * Conventions (readings of the paper):
+ * Conventions (readings of the paper where it leaves a choice open):
  *   - grid: n[0] x ... x n[dim-1] points, index n[dim-1] fastest, spacing
  *     h_d = L_d / n_d (the paper's "h = 1/N" is read as L/N);
  *   - DFT unnormalised forward (sign -1), inverse sign +1 divided by n_pts;
