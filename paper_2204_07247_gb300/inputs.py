@@ -142,3 +142,26 @@ def pfc_batch(sizes=(128, 256, 512), per_size=32, seed0=100, steps=500) -> Batch
 
 # 96 PFC instances, 32 each at 128^2, 256^2 and 512^2, 500 steps
 PFC_BATCH96 = pfc_batch()
+
+
+# Seeded test fields for sketching the difference of two states: with w_j
+# iid U(-1, 1) per point, E[(sum_x e(x) w_j(x))^2] = |e|^2 / 3, so the mean of
+# 3 p_j^2 over the fields estimates the squared L2 norm of e = u - v from the
+# projections p_j of u and of v alone (a Johnson-Lindenstrauss sketch).
+SKETCH_SEED = 0x5EED0000
+SKETCH_COUNT = 128
+
+
+def sketch(u: np.ndarray, count: int = SKETCH_COUNT, seed: int = SKETCH_SEED) -> np.ndarray:
+    """Projections sum_x u(x) w_j(x) of a field onto `count` seeded U(-1, 1) fields."""
+    flat = np.ascontiguousarray(u, dtype=np.float64).ravel()
+    out = np.empty(count)
+    for j in range(count):
+        out[j] = float(np.dot(flat, 2.0 * uniform01(seed + j, flat.size) - 1.0))
+    return out
+
+
+def sketch_rel_l2(p_u: np.ndarray, p_v: np.ndarray, sumsq_v: float) -> float:
+    """Estimated |u - v|_2 / |v|_2 from the two sketches and sum_x v(x)^2."""
+    d = np.asarray(p_u, dtype=np.float64) - np.asarray(p_v, dtype=np.float64)
+    return math.sqrt(3.0 * float(np.mean(d * d)) / sumsq_v)
