@@ -169,24 +169,35 @@ pagd_status pagd_fft_c2r(pagd_solver* s, const double* spec_dev, double* u_dev);
 pagd_status pagd_get_state(pagd_solver* s, double* un_dev, double* unm1_dev, int* step);
 
 /* One time step with no device allocation and no caller workspace.  The paper
- * has no counterpart: this entry point exists for callers that cannot allocate
- * device memory when they need a step (code recording a CUDA graph, runtimes
- * that own the device allocator, fixed-budget embedded uses).  It uses a
- * file-scope static device array of 4 MiB as scratch (enough for every model,
- * scheme and precision up to 128 x 128); grids whose pagd_workspace_size
- * exceeds that are rejected with PAGD_EINVAL.  Every GPU that loads the
- * library holds the array until the process exits.  The solver object comes
- * from pfc_init / fch_init and supplies only the model, grid and solver
- * settings: its own state and workspace are neither needed nor touched.
+ * has no counterpart.  It is for callers that cannot allocate device memory
+ * when they need a step: runtimes that own the device allocator and forbid
+ * the libraries they host to allocate, and programs that fix their device
+ * memory budget up front.  It runs on a file-scope static device array of
+ * 8 MiB that the library carries; every GPU that loads the library holds that
+ * array until the process exits.  The array's head keeps the twiddle tables;
+ * the rest, 8,364,032 bytes, holds the step's scratch, so the solver's
+ * pagd_workspace_size must not exceed that: every 2D grid up to 128 x 128
+ * points and every 3D grid up to 16 x 16 x 16 fits in either precision
+ * (FP32_MIXED also up to 128 x 256 and 32 x 32 x 32).  Larger grids are
+ * rejected with PAGD_EINVAL and a message giving both sizes.
+ * The solver object comes from pfc_init / fch_init and supplies only the
+ * model, grid, scheme and solver settings: its own state, workspace and
+ * trace setting are neither needed nor touched (no phase trace is recorded).
  * Inputs: un_dev = u^n, unm1_dev = u^{n-1} (device, n_pts doubles; for
  * step_index 0 pass u^0 twice), step_index = n, dt = dt_{n+1}, dt_prev = dt_n
  * (ignored when step_index is 0).  Output: unp1_dev = u^{n+1} (device); it may
  * not alias un_dev or unm1_dev.  iters_out / resid_out as for pagd_step.
- * The first call on each device looks up the array's device address (make it
- * before any stream capture).  All calls share the array and it keeps the
- * previous call's contents (each call clears what must start at zero); calls
- * that overlap on the GPU race on it, so the caller must serialise them.
- * Synchronises the stream. */
+ * Each call is one step on its own: the running mass correction that
+ * pagd_run / pagd_step carry from step to step (the FP64 mean removal's
+ * rounding fed back into the next step) starts from zero in every call, so
+ * over a long chain of calls the mass drifts by the rounding of one mean
+ * removal per step (about 1e-16 relative each) instead of staying at one.
+ * The first call on each device looks up the array's device address and
+ * writes the twiddle tables there (make that first call before any stream
+ * capture).  All calls share the array and it keeps the previous call's
+ * contents (each call clears what must start at zero); calls that overlap on
+ * the GPU race on it, so the caller must serialise them.  Synchronises the
+ * stream before returning. */
 pagd_status pagd_step_static(pagd_solver* s, const double* un_dev, const double* unm1_dev,
                              int step_index, double dt, double dt_prev, double tol, double* unp1_dev,
                              int* iters_out, double* resid_out);
@@ -205,6 +216,14 @@ pagd_status pagd_step_static(pagd_solver* s, const double* un_dev, const double*
  * instead: phase[i] is then a bit mask (bit p set: some member ran phase p). */
 pagd_status pagd_set_trace(pagd_solver* s, int enable);
 pagd_status pagd_get_trace(pagd_solver* s, int* phase, double* t_us, int cap, int* count);
+
+/* Device barrier probe (instrumentation, not in the paper): one launch of the
+ * solver's persistent kernel, with the solver's launch plan, that runs `count`
+ * (1..1000000) empty phases, each ended by the device-wide barrier that also
+ * ends every phase of a time step.  *us_per_phase receives the launch's device
+ * time divided by count (CUDA events on the solver's stream).  Needs the
+ * workspace; leaves the solver state alone.  Synchronises the stream. */
+pagd_status pagd_barrier_probe(pagd_solver* s, int count, double* us_per_phase);
 
 const char* pagd_last_error(const pagd_solver* s);
 void pagd_destroy(pagd_solver* s);

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -827,18 +828,24 @@ pagd_status pagd_fft_c2r(pagd_solver* s, const double* spec_dev, double* u_dev) 
 // Allocation-free single step.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// step: code running inside a CUDA graph being built, host threads of a
-// runtime that owns the device allocator and forbids other allocations, or
-// embedded uses that fix their memory budget up front.  pagd_step_static gives
-// them one time step that uses a file-scope static device array as its
-// workspace instead of a caller-provided one.  The array has a fixed size
-// (kStaticScratchBytes, 4 MiB: enough for any supported model up to 128 x 128
-// in FP64) and every GPU that loads this library holds it until the process
-// exits.  All calls share the one array and it keeps the last call's
-// contents; everything that must start at zero is cleared by each call.  Calls
-// whose work overlaps on the GPU (on different streams, or from different host
-// threads) race on the array and must be serialised by the caller.
-constexpr size_t kStaticScratchBytes = (size_t)4 << 20;
+// step: runtimes that own the device allocator and forbid allocations by the
+// libraries they host, and programs that fix their device-memory budget up
+// front and must not grow it later.  pagd_step_static gives them one time step
+// that uses a file-scope static device array as its scratch instead of a
+// caller-provided workspace.  The array has a fixed size (kStaticScratchBytes,
+// 8 MiB) and every GPU that loads this library holds it until the process
+// exits.  Its head holds the twiddle tables, written once per device at
+// set-up; the rest holds one solver workspace (pagd_workspace_size at most
+// kStaticWorkspaceBytes: every 2D grid up to 128 x 128 points and every 3D grid
+// up to 16 x 16 x 16 in either precision).  All calls share the one array and
+// it keeps the last call's contents; everything that must start at zero is
+// cleared by each call.  Calls whose work overlaps on the GPU (on different
+// streams, or from different host threads) race on the array and must be
+// serialised by the caller.
+constexpr size_t kStaticScratchBytes = (size_t)8 << 20;
+constexpr size_t kStaticTwBytes = ((sizeof(double2) + sizeof(float2)) * kNMax + 255) & ~(size_t)255;
+constexpr size_t kStaticWorkspaceBytes = kStaticScratchBytes - kStaticTwBytes;  // 8,364,032
+static_assert(kStaticWorkspaceBytes == 8364032, "the limit stated in include/pagd.h");
 #ifndef PAGD_EMU
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 #else
@@ -846,29 +853,58 @@ alignas(256) static unsigned char g_static_scratch[kStaticScratchBytes];
 #endif
 constexpr int kMaxDevices = 64;
 static void* g_static_ptr[kMaxDevices];
-static double2 g_static_tw64[kNMax];
-static float2 g_static_tw32[kNMax];
-static bool g_static_tw_ready = false;
+static std::mutex g_static_mu;  // guards g_static_ptr and the one-time set-up
 
-// Device address of the static scratch for the current device.  In host code
-// the array's name is only a host-side stand-in, so the address is obtained
-// with cudaGetSymbolAddress, once per device, with that device current; this
-// happens on the first call on each device (make that first call before any
-// stream capture).
+// Device address of the static scratch for the current device, with the
+// twiddle tables at its head.  In host code the array's name is only a
+// host-side stand-in, so the address is obtained with cudaGetSymbolAddress,
+// once per device, with that device current, and the tables are copied there
+// with a synchronous cudaMemcpy.  This happens on the first call on each device
+// (make that first call before any stream capture); the lock makes concurrent
+// first calls from several host threads do it once.
 static pagd_status static_scratch(pagd_solver* s, char** out) {
 #ifdef PAGD_EMU
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[0]) {
+        std::vector<double2> t64(kNMax);
+        std::vector<float2> t32(kNMax);
+        for (int m = 0; m < kNMax; m++) {
+            const long double ang = -2.0L * 3.141592653589793238462643383279502884L * (long double)m / (long double)kNMax;
+            t64[m] = double2{(double)cosl(ang), (double)sinl(ang)};
+            t32[m] = float2{(float)t64[m].x, (float)t64[m].y};
+        }
+        std::memcpy(g_static_scratch, t64.data(), sizeof(double2) * kNMax);
+        std::memcpy(g_static_scratch + sizeof(double2) * kNMax, t32.data(), sizeof(float2) * kNMax);
+        g_static_ptr[0] = g_static_scratch;
+    }
     (void)s;
-    *out = (char*)g_static_scratch;
+    *out = (char*)g_static_ptr[0];
     return PAGD_OK;
 #else
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(s, e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return fail(s, PAGD_EINVAL, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_static_mu);
     if (!g_static_ptr[dev]) {
         void* ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_static_scratch);
         if (e != cudaSuccess) return cuda_fail(s, e, "cudaGetSymbolAddress of the static scratch");
+        // twiddles exp(-2 pi i m / kNMax) from the host libm in long double
+        std::vector<double2> t64(kNMax);
+        std::vector<float2> t32(kNMax);
+        for (int m = 0; m < kNMax; m++) {
+            const long double ang = -2.0L * 3.141592653589793238462643383279502884L * (long double)m / (long double)kNMax;
+            t64[m].x = (double)cosl(ang);
+            t64[m].y = (double)sinl(ang);
+            t32[m].x = (float)t64[m].x;
+            t32[m].y = (float)t64[m].y;
+        }
+        e = cudaMemcpy(ptr, t64.data(), sizeof(double2) * kNMax, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy((char*)ptr + sizeof(double2) * kNMax, t32.data(), sizeof(float2) * kNMax,
+                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(s, e, "cudaMemcpy of the static twiddle tables");
         g_static_ptr[dev] = ptr;
     }
     *out = (char*)g_static_ptr[dev];
@@ -883,35 +919,27 @@ pagd_status pagd_step_static(pagd_solver* s, const double* un_dev, const double*
     if (step_index < 0 || !(dt > 0.0) || !std::isfinite(dt) || !(tol >= 0.0) ||
         (step_index > 0 && !(dt_prev > 0.0)))
         return fail(s, PAGD_EINVAL, "bad step index / dt / dt_prev / tol");
-    if (s->ws_bytes > kStaticScratchBytes) {
+    if (s->ws_bytes > kStaticWorkspaceBytes) {
         char buf[200];
         std::snprintf(buf, sizeof(buf),
                       "grid too large for the static scratch: needs %zu bytes, the maximum is %zu "
                       "(use pagd_set_workspace and pagd_step)",
-                      s->ws_bytes, kStaticScratchBytes);
+                      s->ws_bytes, kStaticWorkspaceBytes);
         return fail(s, PAGD_EINVAL, buf);
     }
-    char* w = nullptr;
-    pagd_status st = static_scratch(s, &w);
+    char* head = nullptr;
+    pagd_status st = static_scratch(s, &head);
     if (st != PAGD_OK) return st;
-    if (!g_static_tw_ready) {
-        for (int m = 0; m < kNMax; m++) {
-            const long double ang = -2.0L * 3.141592653589793238462643383279502884L * (long double)m / (long double)kNMax;
-            g_static_tw64[m].x = (double)cosl(ang);
-            g_static_tw64[m].y = (double)sinl(ang);
-            g_static_tw32[m].x = (float)g_static_tw64[m].x;
-            g_static_tw32[m].y = (float)g_static_tw64[m].y;
-        }
-        g_static_tw_ready = true;
-    }
+    char* w = head + kStaticTwBytes;
     const size_t b = sizeof(double) * s->npts;
-    st = dcopy(s, w + s->off[O_TW64], g_static_tw64, sizeof(g_static_tw64));
-    if (st == PAGD_OK) st = dcopy(s, w + s->off[O_TW32], g_static_tw32, sizeof(g_static_tw32));
-    if (st == PAGD_OK) st = dcopy(s, w + s->off[O_U0], un_dev, b);
+    st = dcopy(s, w + s->off[O_U0], un_dev, b);
     if (st == PAGD_OK) st = dcopy(s, w + s->off[O_U1], unm1_dev, b);
     if (st == PAGD_OK) st = dzero(s, w + s->off[O_MASS], 2 * sizeof(double));
     if (st != PAGD_OK) return st;
     Params P = params_for(s, w);
+    P.tw64 = (const double2*)head;
+    P.tw32 = (const float2*)(head + sizeof(double2) * kNMax);
+    P.trace = nullptr;  // no phase trace: pagd_get_trace reads the solver's own workspace
     const bool imex = s->scheme == PAGD_LBDF2 || s->scheme == PAGD_LMP;
     P.prog = imex ? PROG_IMEX : PROG_RUN;
     P.ref_valid = 0;  // the static scratch holds no reference spectra
@@ -937,6 +965,53 @@ pagd_status pagd_step_static(pagd_solver* s, const double* un_dev, const double*
     if (sc.status != ST_OK) return fail(s, status_from(sc.status), "static-scratch step failed");
     if (sc.steps_done != 1) return fail(s, PAGD_ECUDA, "kernel ended early");
     return PAGD_OK;
+}
+
+// Device barrier probe (instrumentation, not in the paper): one launch of the
+// solver's persistent kernel with its launch plan that runs `count` empty
+// phases, each ended by the device-wide barrier; *us_per_phase receives the
+// launch's device time / count (CUDA events on the solver's stream).
+pagd_status pagd_barrier_probe(pagd_solver* s, int count, double* us_per_phase) {
+    if (!s || count < 1 || count > 1000000 || !us_per_phase) return PAGD_EINVAL;
+    if (!s->ws) return fail(s, PAGD_ESTATE, "no workspace");
+    Params P = base_params(s);
+    P.prog = PROG_BARRIER;
+    P.nsteps = count;
+    P.trace = nullptr;
+#ifdef PAGD_EMU
+    pagd_status st = run_program(s, P);
+    *us_per_phase = 0.0;
+    return st;
+#else
+    cudaEvent_t e0, e1;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e != cudaSuccess) return cuda_fail(s, e, "cudaEventCreate");
+    e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(s, e, "cudaEventCreate");
+    }
+    pagd_status st = PAGD_OK;
+    e = cudaEventRecord(e0, (cudaStream_t)s->stream);
+    if (e == cudaSuccess) {
+        st = run_program(s, P);
+        e = cudaEventRecord(e1, (cudaStream_t)s->stream);
+    }
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PAGD_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(s, e, "barrier probe timing");
+    Scal sc;
+    st = dcopy(s, &sc, P.sc, sizeof(Scal));
+    if (st == PAGD_OK) st = dsync(s);
+    if (st != PAGD_OK) return st;
+    if (sc.bar_error) return fail(s, PAGD_ETIMEOUT, "device barrier timed out");
+    *us_per_phase = 1000.0 * (double)ms / (double)count;
+    return PAGD_OK;
+#endif
 }
 
 pagd_status pagd_set_trace(pagd_solver* s, int enable) {

@@ -37,7 +37,7 @@ enum { M_PFC = 0, M_FCH = 1 };
 enum { S_BDF2 = 0, S_MP = 1, S_LBDF2 = 2, S_LMP = 3 };
 enum { P_FP64 = 0, P_MIXED = 1 };
 enum { PROG_RUN = 0, PROG_FFT_FWD = 1, PROG_FFT_INV = 2, PROG_ENERGY = 3, PROG_MASS = 4,
-       PROG_IMEX = 5, PROG_RHS = 6, PROG_EST = 7 };
+       PROG_IMEX = 5, PROG_RHS = 6, PROG_EST = 7, PROG_BARRIER = 8 };
 enum { ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ECUDA = 3, ST_ENOCONV = 4, ST_EPRECOND = 5,
        ST_ENAN = 6, ST_ESTATE = 7, ST_ETIMEOUT = 8 };
 enum { FLAG_PRECOND = 1 };
@@ -48,6 +48,7 @@ enum Phase {
     PH_IM_R0, PH_IM_C0, PH_IM_R1, PH_IM_C1, PH_IM_R2,
     PH_MF, PH_MI, PH_GS,
     PH_RH_R0, PH_RH_C0, PH_RH_R1, PH_RH_C1, PH_RH_R2, PH_EST,
+    PH_NOP,  // an empty phase (barrier probe)
     PH_DONE
 };
 
@@ -1967,6 +1968,7 @@ __host__ __device__ inline Ctl ctl_init(const Params& P) {
         case PROG_ENERGY: c.ph = PH_EN_R; break;
         case PROG_RHS: c.ph = PH_RH_R0; break;
         case PROG_EST: c.ph = PH_EST; break;
+        case PROG_BARRIER: c.ph = (P.nsteps > 0) ? PH_NOP : PH_DONE; break;
         default: c.ph = PH_MASS; break;
     }
     return c;
@@ -2156,6 +2158,10 @@ __device__ void ctl_step(const Params& P, Ctl& c) {
         case PH_RH_C0: c.ph = (P.model == M_PFC) ? PH_RH_R2 : PH_RH_R1; break;
         case PH_RH_R1: c.ph = PH_RH_C1; break;
         case PH_RH_C1: c.ph = PH_RH_R2; break;
+        case PH_NOP:
+            c.step++;
+            c.ph = (c.step >= P.nsteps) ? PH_DONE : PH_NOP;
+            break;
         default: c.ph = PH_DONE; break;
     }
 }

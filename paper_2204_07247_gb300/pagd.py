@@ -27,14 +27,14 @@ SCHEMES = {"bdf2": BDF2, "mp": MP, "lbdf2": LBDF2, "lmp": LMP}
 PRECISIONS = {"fp64": FP64, "fp32_mixed": FP32_MIXED}
 EXPORTS = ("pagd_default_opts", "pfc_init", "fch_init", "pagd_workspace_size", "pagd_set_workspace",
            "pagd_set_state", "pagd_step", "pagd_step_with_guess", "pagd_run", "pagd_run_host", "pagd_energy", "pagd_mass",
-           "pagd_rhs", "pagd_run_adaptive", "pagd_fft_r2c", "pagd_fft_c2r", "pagd_get_state", "pagd_step_static", "pagd_set_trace",
+           "pagd_rhs", "pagd_run_adaptive", "pagd_fft_r2c", "pagd_fft_c2r", "pagd_get_state", "pagd_step_static", "pagd_barrier_probe", "pagd_set_trace",
            "pagd_get_trace", "pagd_last_error", "pagd_destroy", "pagd_batch_create",
            "pagd_batch_workspace_size", "pagd_batch_set_workspace", "pagd_batch_run",
            "pagd_batch_last_error", "pagd_batch_destroy")
 # phase identifiers of the persistent kernel's control machine (for traces)
 PHASES = ("B", "C", "D", "E", "R1", "CI", "RI", "ACCEPT", "FAIL", "FWD_R", "FWD_C", "INV_C", "INV_R",
           "EN_R", "EN_C", "EN_R2", "MASS", "IM_R0", "IM_C0", "IM_R1", "IM_C1", "IM_R2", "MF", "MI",
-          "GS", "RH_R0", "RH_C0", "RH_R1", "RH_C1", "RH_R2", "EST", "START")
+          "GS", "RH_R0", "RH_C0", "RH_R1", "RH_C1", "RH_R2", "EST", "NOP", "START")
 
 
 class PagdError(RuntimeError):
@@ -72,6 +72,7 @@ def _declare(lib):
         "pagd_fft_c2r": [P, P, P],
         "pagd_get_state": [P, P, P, IP],
         "pagd_step_static": [P, P, P, i, d, d, d, P, IP, D],
+        "pagd_barrier_probe": [P, i, D],
         "pagd_set_trace": [P, i],
         "pagd_get_trace": [P, IP, D, i, IP],
         "pagd_last_error": [P],
@@ -316,6 +317,13 @@ class Solver:
                                               dt_prev, tol, self._ptr(u_out), ctypes.byref(it),
                                               ctypes.byref(r)), "step_static")
         return it.value, r.value
+
+    def barrier_probe(self, count=2000):
+        """Device time per empty phase of the persistent kernel (microseconds):
+        the cost of one device-wide barrier with this solver's launch plan."""
+        us = ctypes.c_double()
+        self._check(self.lib.pagd_barrier_probe(self._h, int(count), ctypes.byref(us)), "barrier_probe")
+        return us.value
 
     def set_trace(self, enable=True):
         self._check(self.lib.pagd_set_trace(self._h, 1 if enable else 0), "set_trace")
