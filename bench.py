@@ -264,11 +264,12 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def oracle_steps_per_s(w, budget_s=15.0, max_steps=20, warm=0, threads=1):
+def oracle_steps_per_s(w, budget_s=15.0, max_steps=20, warm=0, threads=1, final=None):
     """The FP64 CPU oracle as it stands on a bounded sample of the workload:
     `warm` untimed steps, then up to max_steps timed steps of the same
     trajectory (fewer once budget_s is spent); `threads` host threads share
-    its line transforms."""
+    its line transforms.  final (a dict, optional) receives the oracle's last
+    state and its step count from u0."""
     from oracle import oracle as O
     O.set_threads(threads)
     P = O.Problem(O.PFC if w.model == "pfc" else O.FCH, w.n, w.L, w.eps, w.eta1, w.eta2, w.tau,
@@ -290,7 +291,92 @@ def oracle_steps_per_s(w, budget_s=15.0, max_steps=20, warm=0, threads=1):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
+    if final is not None:
+        final["u"], final["steps"] = un, warm + nst
     return nst / dt, nst, float(np.mean(its)), dt
+
+
+def gpu_rel_l2_vs_oracle(torch, pagd, w, u_oracle, nsteps, seed=1):
+    """|u_gpu - u_oracle|_2 / |u_oracle|_2 after nsteps steps from u0 (full
+    fields: the oracle state comes from the CPU-baseline run)."""
+    S = pagd.solver_for(w)
+    S.set_state(torch.from_numpy(w.u0(seed)).cuda())
+    out = S.empty_field()
+    S.run(w.dt, nsteps, w.tol, out)
+    u = out.cpu().numpy()
+    return float(np.linalg.norm(u - u_oracle) / np.linalg.norm(u_oracle))
+
+
+def reference_fixture(name):
+    p = os.path.join(ROOT, "tests", "golden", f"oracle_{name}.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        return json.load(fh)
+
+
+def gpu_vs_reference(torch, pagd, w):
+    """The plain GPU trajectory from u0 against the oracle's stored reference
+    trajectory (tests/golden, written by oracle/reference_runs.py): relative L2
+    error at each checkpoint from the two sketches, with the oracle's own
+    tolerance floor and twin-run amplification beside it."""
+    rec = reference_fixture(w.name)
+    if rec is None:
+        return None
+    S = pagd.solver_for(w)
+    S.set_state(torch.from_numpy(w.u0(rec["seed"])).cuda())
+    out = S.empty_field()
+    done, rows = 0, {}
+    for step in sorted(int(k) for k in rec["states"]):
+        S.run(w.dt, step - done, w.tol, out)
+        done = step
+        ref = rec["states"][str(step)]
+        est = I.sketch_rel_l2(I.sketch(out.cpu().numpy(), rec["sketch"]["count"], rec["sketch"]["seed"]),
+                              ref["sketch"], ref["sumsq"])
+        rows[str(step)] = {"rel_l2_est": est,
+                           "oracle_tol_floor": rec.get("tol_floor", {}).get("rel_l2", {}).get(str(step)),
+                           "twin_amplification": rec.get("twin", {}).get("amplification", {}).get(str(step))}
+    return {"reference": f"tests/golden/oracle_{w.name}.json (FP64 oracle, seed {rec['seed']})",
+            "estimator": f"{rec['sketch']['count']}-projection sketch", "checkpoints": rows}
+
+
+def bench_pfc64(torch, pagd, warm, cores, cpu=True):
+    """PFC 2D 64^2 MP FP64 (100 steps): GPU steps/s, its error against the
+    oracle over the whole run, and the oracle timed in full on the host."""
+    w = I.PFC64
+    S = pagd.solver_for(w)
+    S.set_state(torch.from_numpy(w.u0(1)).cuda())
+    S.run(w.dt, warm, w.tol)
+    S.set_state(torch.from_numpy(w.u0(1)).cuda())
+    flush_l2(torch)
+    out = S.empty_field()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    its, res = S.run(w.dt, w.steps, w.tol, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    row = {"workload": w.name, "steps": w.steps, "ms": ms, "steps_per_s": w.steps / (ms / 1000.0),
+           "iters_per_step": float(np.mean(its)), "max_resid": float(np.max(res)), "gpu_launches": 1,
+           "roofline": {"bound": "latency", "note": "64^2 FP64: 4096 points per phase, far below the "
+                        "machine's parallelism; bound by the device barriers and the per-unit latency"}}
+    if cpu:
+        from oracle import oracle as O
+        fin = {}
+        v1, n1, oits, sec1 = oracle_steps_per_s(w, budget_s=60.0, max_steps=w.steps, threads=1, final=fin)
+        row["cpu_baseline"] = {"value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"the whole run ({n1} steps, {sec1:.1f} s), FP64 C oracle, 1 thread"}
+        row["oracle_iters_per_step"] = oits
+        if fin["steps"] == w.steps:
+            u = out.cpu().numpy()
+            row["rel_l2_vs_oracle"] = float(np.linalg.norm(u - fin["u"]) / np.linalg.norm(fin["u"]))
+        O.set_threads(cores)
+        vN, nN, _, secN = oracle_steps_per_s(w, budget_s=30.0, max_steps=w.steps, threads=cores)
+        row["cpu_baseline"]["all_cores_value"] = vN
+        row["cpu_baseline"]["all_cores"] = cores
+    row["vs_reference_trajectory"] = gpu_vs_reference(torch, pagd, w)
+    return row
 
 
 def _oracle_problem(w, n=None, L=None):
@@ -511,16 +597,33 @@ def main():
     e2e = {"value": world * K / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": 2 * 8 * n_pts / K, "d2h_bytes_per_step": (8 * n_pts + 16 * K + 64) / K}
 
-    # IMEX (LBDF2) side by side, same workload and device
-    S3 = pagd.solver_for(w, scheme="lbdf2", precision="fp64")
-    S3.set_state(u0)
-    S3.run(w.dt, W, 0.0)
-    torch.cuda.synchronize()
-    e0.record()
-    S3.run(w.dt, K, 0.0)
-    e1.record()
-    torch.cuda.synchronize()
-    imex_sps = K / (e0.elapsed_time(e1) / 1000.0)
+    # the other schemes side by side (MP fully implicit, the IMEX LBDF2 / LMP),
+    # same workload, device and step count
+    side = {}
+    for scheme, prec, tol in (("mp", w.precision, w.tol), ("lbdf2", "fp64", 0.0), ("lmp", "fp64", 0.0)):
+        S3 = pagd.solver_for(w, scheme=scheme, precision=prec)
+        S3.set_state(u0)
+        S3.run(w.dt, W, tol)
+        torch.cuda.synchronize()
+        e0.record()
+        its3, _ = S3.run(w.dt, K, tol)
+        e1.record()
+        torch.cuda.synchronize()
+        side[scheme] = {"steps_per_s": K / (e0.elapsed_time(e1) / 1000.0),
+                        "iters_per_step": float(np.mean(its3)), "precision": prec}
+    imex_sps = side["lbdf2"]["steps_per_s"]
+
+    # what binds the step: device barriers per step x the measured cost of one
+    # (an empty phase of the same launch plan), from a short traced run
+    S4 = pagd.solver_for(w)
+    S4.set_state(u0)
+    S4.run(w.dt, W, w.tol)
+    S4.set_trace(True)
+    its4, _ = S4.run(w.dt, 20, w.tol)
+    names4, t4 = S4.get_trace()
+    S4.set_trace(False)
+    phases_per_step = (len(names4) - 1) / 20.0
+    barrier_us = S4.barrier_probe(2000)
 
     # the batched form (PFC, 96 members of 128^2 / 256^2 / 512^2) and the 3D
     # workload (PFC 256^3, two seeds in one batch), each timed on its own
@@ -530,6 +633,8 @@ def main():
         extra["pgd_vs_pagd"] = bench_pgd_vs_pagd(torch, pagd, w, 100)
         extra["cost_to_accuracy"] = bench_cost_to_accuracy(torch, pagd, w, 0.064,
                                                            [4e-3, 2e-3, 1e-3, 5e-4])
+    if not args.no_forms and rank == 0:
+        extra["pfc64"] = bench_pfc64(torch, pagd, W, host_cores(), cpu=not args.no_cpu_baseline)
     if not args.no_forms and rank == 0:
         # learned initial iterate (FCH 512^2): train on solver trajectories, then
         # PAGD from the network's proposal vs from the extrapolation
@@ -567,12 +672,24 @@ def main():
             "peak_kind": peak_kind,
             "kernel": "pagd_kernel<float>",
             "bytes_model": f"{bpp} B per grid point per residual evaluation x {n_pts} points x "
-                           f"{evals} evaluations"}
+                           f"{evals} evaluations",
+            "frac_is": "a lower bound: the 256^2 working set stays in L2, HBM is not the binding resource",
+            "binding": {"kind": "latency", "phases_per_step": phases_per_step,
+                        "barrier_us": barrier_us,
+                        "barrier_share": phases_per_step * barrier_us / (1000.0 * ms / K),
+                        "phase_us_mean": 1000.0 * ms / K / phases_per_step,
+                        "note": "every phase ends in a device-wide barrier; a phase's work is one "
+                                "row pair or column per warp (128 / 129 units on 152 SMs), so its "
+                                "time is the latency of one unit plus the barrier"}}
     cpu = None
+    rel_short = None
     if not args.no_cpu_baseline:
         # all host cores on the oracle's line transforms, and one core beside it
         cores = host_cores()
-        v, nst, oits, secs = oracle_steps_per_s(w, budget_s=15.0, max_steps=20, threads=cores)
+        fin = {}
+        v, nst, oits, secs = oracle_steps_per_s(w, budget_s=15.0, max_steps=20, threads=cores, final=fin)
+        rel_short = {"steps": fin["steps"],
+                     "rel_l2": gpu_rel_l2_vs_oracle(torch, pagd, w, fin["u"], fin["steps"])}
         v1, nst1, _, secs1 = oracle_steps_per_s(w, budget_s=8.0, max_steps=20, threads=1)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"first {nst} steps of the same workload ({secs:.1f} s), FP64 C oracle, "
@@ -589,7 +706,9 @@ def main():
                    "parallelism": f"replicas{world}", "l2": "flushed before the timed run; "
                    "the 256^2 working set (~6 MB) is L2-resident across steps by design",
                    "iters_per_step": evals / K, "max_resid": float(np.max(res)),
-                   "imex_lbdf2_steps_per_s": imex_sps},
+                   "imex_lbdf2_steps_per_s": imex_sps, "schemes_side_by_side": side},
+        "rel_l2_vs_oracle": rel_short,
+        "vs_reference_trajectory": gpu_vs_reference(torch, pagd, w),
         "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": ck,
