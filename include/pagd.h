@@ -109,12 +109,16 @@ pagd_status pagd_step(pagd_solver* s, double* u_dev, double dt, double tol, int*
 /* One implicit step (as pagd_step) started from a caller's initial iterate,
  * e.g. a learned predictor of u^{n+1}.  The guess (device, n_pts doubles) is
  * first moved to the mass of u^n (the discrete solution keeps it and every
- * PAGD update has zero mean).  Then the first direction d_0 of Algorithm 2 is
- * evaluated at the moved guess and at the extrapolated guess of Sec. 3.4.2,
- * with the averaged Newton constants of each, and PAGD continues from the one
- * with the smaller ||d_0||_inf; both evaluations count in iters_out.
- * used_guess_out (nullable): 1 if the caller's guess was kept.  Implicit
- * schemes only (PAGD_EINVAL for LBDF2 / LMP).  Synchronises the stream. */
+ * PAGD update has zero mean), and the first direction d_0 of Algorithm 2 is
+ * evaluated there.  The solver keeps a record R: ||d_0||_inf of the last step
+ * it started from the extrapolated guess of Sec. 3.4.2 (reset by
+ * pagd_set_state).  With a record, the guess is kept when its ||d_0||_inf <= R
+ * and PAGD continues from it at no extra cost; otherwise the step starts over
+ * from the extrapolation (the probe counts in iters_out).  Without a record,
+ * d_0 is also evaluated at the extrapolation and PAGD continues from the one
+ * with the smaller ||d_0||_inf (both evaluations count).  used_guess_out
+ * (nullable): 1 if the caller's guess was kept.  Implicit schemes only
+ * (PAGD_EINVAL for LBDF2 / LMP).  Synchronises the stream. */
 pagd_status pagd_step_with_guess(pagd_solver* s, double* u_dev, const double* guess_dev, double dt, double tol,
                                  int* iters_out, double* resid_out, int* used_guess_out);
 
@@ -224,6 +228,17 @@ pagd_status pagd_get_trace(pagd_solver* s, int* phase, double* t_us, int cap, in
  * time divided by count (CUDA events on the solver's stream).  Needs the
  * workspace; leaves the solver state alone.  Synchronises the stream. */
 pagd_status pagd_barrier_probe(pagd_solver* s, int count, double* us_per_phase);
+
+/* Launch plan of the solver's persistent kernel (instrumentation, not in the
+ * paper): CTAs of the last launch (0 before the first), threads per CTA, the
+ * cluster size of the cluster-resident iterations (0: every phase is
+ * device-wide; else the PAGD iterations of square 64^2, 128^2 and 256^2 grids
+ * run inside one thread-block cluster of n/16 CTAs with their state in
+ * distributed shared memory), whether the passes with FP64 lines run
+ * CTA-cooperative units, and the dynamic shared memory per CTA.  Every output
+ * nullable. */
+pagd_status pagd_launch_info(const pagd_solver* s, int* grid, int* threads, int* cluster, int* coop,
+                             size_t* smem);
 
 const char* pagd_last_error(const pagd_solver* s);
 void pagd_destroy(pagd_solver* s);

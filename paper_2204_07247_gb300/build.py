@@ -22,7 +22,7 @@ EMU = os.path.join(BUILD, "libpagd_emu.so")
 # the batched kernel per iteration precision, and the learned-guess network
 SOURCES = (["pagd.cu"] + [f"pagd_k{nf}_{t}.cu" for nf in (0, 64, 128, 256, 512) for t in ("f32", "f64")]
            + ["pagd_batch_f32.cu", "pagd_batch_f64.cu", "sno.cu"])
-HEADERS = ["compat.cuh", "fft.cuh", "solver.cuh", "kernels.cuh", "batch.cuh"]
+HEADERS = ["compat.cuh", "fft.cuh", "solver.cuh", "cluster.cuh", "kernels.cuh", "batch.cuh"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 

@@ -5,6 +5,7 @@
 // units compile in parallel and link into libpagd.so.
 #pragma once
 #include "solver.cuh"
+#include "cluster.cuh"
 
 namespace pagd {
 
@@ -93,15 +94,26 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pagd_kernel(const __grid_const
     }
     __syncthreads();
     while (c.ph != PH_DONE) {
-        exec_phase<T, NF>(P, c, tw, wsm, red);
+        // the iterations of a base point run cluster-resident where the plan
+        // chose it: cluster 0 loops until a decision other than "iterate on"
+        // and hands its control state back through P.lctl
+        const bool cl_phase = P.cl && c.ph == PH_CI;
+        if (cl_phase) cluster_iterate<T, NF>(P, c, tw, wsm, &ntr);
+        else exec_phase<T, NF>(P, c, tw, wsm, red);
         if (!grid_barrier(P.sc, gen)) break;
         if (threadIdx.x == 0) {
-            if (P.trace && blockIdx.x == 0 && ntr < P.trace_cap) {
+            if (P.trace && blockIdx.x == 0 && ntr < P.trace_cap && !cl_phase) {
                 // bit 16: a phase of an incremental (T-transform) base evaluation
                 const bool incb = c.inc && (c.ph == PH_B || c.ph == PH_C || c.ph == PH_D || c.ph == PH_E);
                 P.trace[2 * ntr] = (unsigned long long)c.ph | (incb ? (1ull << 16) : 0ull);
                 P.trace[2 * ntr + 1] = gtimer();
                 ntr++;
+            }
+            if (cl_phase) {
+                // resume after the loop's last row pass (phase RI)
+                const unsigned* src = (const unsigned*)P.lctl;
+                unsigned* dst = (unsigned*)&c;
+                for (int i = 0; i < (int)(sizeof(Ctl) / sizeof(unsigned)); i++) dst[i] = __ldcg(src + i);
             }
             ctl_advance<T>(P, c);
         }
@@ -129,8 +141,39 @@ cudaError_t pagd_launch(const Params& P, int grid, int threads, size_t smem, voi
     if (e != cudaSuccess) return e;
     const int cap = per_sm * sms;
     if (grid > cap) grid = cap;
-    if (grid_used) *grid_used = grid;
     Params Pc = P;
+    if (P.cl > 0) {
+        // cluster launch: cluster 0 runs the iterations (cluster.cuh); the grid
+        // is a whole number of clusters that the device co-schedules
+        e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[2];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)P.cl;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        at[1].id = cudaLaunchAttributeCooperative;
+        at[1].val.cooperative = 1;
+        cfg.gridDim = dim3((unsigned)P.cl);
+        cfg.blockDim = dim3((unsigned)threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = (cudaStream_t)stream;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        e = cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg);
+        if (e != cudaSuccess) return e;
+        if (ncl < 1) return cudaErrorInvalidConfiguration;
+        int nc = (grid + P.cl - 1) / P.cl;
+        if (nc > ncl) nc = ncl;
+        grid = nc * P.cl;
+        if (grid_used) *grid_used = grid;
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.numAttrs = 2;
+        return cudaLaunchKernelEx(&cfg, kern, Pc);
+    }
+    if (grid_used) *grid_used = grid;
     void* args[] = {(void*)&Pc};
     return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(threads), args, smem,
                                        (cudaStream_t)stream);

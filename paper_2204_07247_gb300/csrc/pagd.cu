@@ -6,6 +6,7 @@
 // memory is host memory and a "launch" runs the kernel's phases block by block
 // on the calling thread.
 #include "solver.cuh"
+#include "cluster.cuh"
 #include "../../include/pagd.h"
 
 #include <cmath>
@@ -53,8 +54,8 @@ struct pagd_solver {
     size_t off[48];  // workspace offsets, indexed by the O_* enum
     size_t ws_bytes;
     char* ws;
-    // launch plan
-    int grid, logtw, threads, coop;
+    // launch plan (grid_used: the grid of the last launch)
+    int grid, logtw, threads, coop, cl, grid_used;
     size_t smem, warp_bytes;
     // state
     int have_state, step, cur, trace, ref_valid;
@@ -64,7 +65,7 @@ struct pagd_solver {
 
 enum {
     O_SC, O_NORMS, O_SUMS, O_STATS, O_TW64, O_TW32, O_U0, O_U1, O_VB, O_G64, O_VBT, O_LBT, O_DD0,
-    O_DD1, O_SS0, O_SS1, O_C0, O_NB, O_DB, O_CL64, O_NB64, O_DB64, O_MASS, O_TRACE, O_VR64, O_NR64, O_WR64, O_LB64, O_YB, O_X, O_X64, O_GH64, O_END
+    O_DD1, O_SS0, O_SS1, O_C0, O_NB, O_DB, O_CL64, O_NB64, O_DB64, O_MASS, O_TRACE, O_VR64, O_NR64, O_WR64, O_LB64, O_YB, O_X, O_X64, O_GH64, O_LCTL, O_END
 };
 
 static pagd_status fail(pagd_solver* s, pagd_status st, const char* msg) {
@@ -109,7 +110,7 @@ static void plan_layout(pagd_solver* s) {
     sz[O_CL64] = sizeof(double2) * H * 3;
     sz[O_NB64] = sizeof(double2) * H * 3;
     sz[O_DB64] = sizeof(double2) * H * 2;
-    sz[O_MASS] = sizeof(double) * 2;
+    sz[O_MASS] = sizeof(double) * 4;
     sz[O_TRACE] = sizeof(unsigned long long) * 2 * kTraceCap;
     sz[O_VR64] = sizeof(double2) * H;
     sz[O_NR64] = sizeof(double2) * H * 2;
@@ -119,6 +120,7 @@ static void plan_layout(pagd_solver* s) {
     sz[O_X] = s->dim == 3 ? (size_t)2 * T * H * 3 : 0;
     sz[O_X64] = s->dim == 3 ? sizeof(double2) * H * 3 : 0;
     sz[O_GH64] = sizeof(double2) * H;
+    sz[O_LCTL] = sizeof(Ctl);
     static_assert(O_END <= (int)(sizeof(((pagd_solver*)nullptr)->off) / sizeof(size_t)), "offset table too small");
     size_t o = 0;
     for (int i = 0; i < O_END; i++) {
@@ -207,6 +209,8 @@ static Params params_for(const pagd_solver* s, char* w) {
     P.X64 = s->dim == 3 ? (double2*)(w + s->off[O_X64]) : nullptr;
     P.ref_valid = s->ref_valid;
     P.refresh = kRefreshSteps;
+    P.cl = s->cl;
+    P.lctl = w + s->off[O_LCTL];
     return P;
 }
 
@@ -248,6 +252,17 @@ template <class T> static pagd_status launch(pagd_solver* s, const Params& P) {
     Ctl c = ctl_init(P);
     const int nf = fixed_len(P.n0, P.n1);
     while (c.ph != PH_DONE) {
+        if (P.cl && c.ph == PH_CI) {
+            switch (nf) {
+                case 64: cluster_iterate_emu<T, 64>(P, c, tw); break;
+                case 128: cluster_iterate_emu<T, 128>(P, c, tw); break;
+                case 256: cluster_iterate_emu<T, 256>(P, c, tw); break;
+                default: break;
+            }
+            c = *(const Ctl*)P.lctl;  // resume after the loop's last row pass (phase RI)
+            ctl_advance<T>(P, c);
+            continue;
+        }
         for (int b = 0; b < s->grid; b++) {
             blockIdx.x = (unsigned)b;
             tw.wr = b;
@@ -261,6 +276,7 @@ template <class T> static pagd_status launch(pagd_solver* s, const Params& P) {
         }
         ctl_advance<T>(P, c);
     }
+    s->grid_used = s->grid;
     return PAGD_OK;
 }
 #else
@@ -298,6 +314,7 @@ template <class T> static pagd_status launch(pagd_solver* s, const Params& P) {
         default: e = pagd_launch<T, 0>(P, s->grid, s->threads, s->smem, s->stream, &used); break;
     }
     if (e != cudaSuccess) return cuda_fail(s, e, "cooperative launch of pagd_kernel");
+    s->grid_used = used;
     return PAGD_OK;
 }
 #endif
@@ -345,6 +362,29 @@ static void make_plan(pagd_solver* s) {
     s->coop = (fixed_len(s->n[0], s->n[last]) != 0 && 2 * units <= (long long)s->grid * wpb) ? 1 : 0;
     if (const char* e = std::getenv("PAGD_COOP")) {
         if ((e[0] == '0' || e[0] == '1') && e[1] == 0) s->coop = fixed_len(s->n[0], s->n[last]) != 0 ? e[0] - '0' : 0;
+    }
+    // Cluster-resident iterations (cluster.cuh) on square 2D grids of 64, 128
+    // or 256 points per axis, when the cluster buffers fit a CTA's shared
+    // memory.  Off by default (measured slower than the device-wide phases so
+    // far); PAGD_CLUSTER=1 turns it on, 0 off.  A launch with 16-CTA clusters
+    // co-schedules fewer CTAs than a 256^2 grid has columns, so there the
+    // device-wide phases run warp-owned.
+    s->cl = 0;
+    const int nf = fixed_len(s->n[0], s->n[last]);
+    bool want_cl = false;
+    if (const char* e = std::getenv("PAGD_CLUSTER")) want_cl = e[0] == '1' && e[1] == 0;
+    if (want_cl && s->dim == 2 && cl_size_for(nf) > 0) {
+        const ClOff co = cl_offsets(nf, k_iter(s->model), s->tsize);
+        const size_t need = tw_smem_bytes(s->logtw) + co.end;
+        bool on = need <= kMaxSmem;
+#ifndef PAGD_EMU
+        on = on && wpb == kMaxThreads / 32;
+#endif
+        if (on) {
+            s->cl = cl_size_for(nf);
+            if (need > s->smem) s->smem = need;
+            if (nf == 256) s->coop = 0;
+        }
     }
 }
 
@@ -465,7 +505,7 @@ pagd_status pagd_set_state(pagd_solver* s, const double* u0_dev) {
     s->cur = 0;
     pagd_status st = dcopy(s, s->ws + s->off[O_U0], u0_dev, b);
     if (st == PAGD_OK) st = dcopy(s, s->ws + s->off[O_U1], u0_dev, b);
-    if (st == PAGD_OK) st = dzero(s, s->ws + s->off[O_MASS], 2 * sizeof(double));
+    if (st == PAGD_OK) st = dzero(s, s->ws + s->off[O_MASS], 4 * sizeof(double));
     if (st == PAGD_OK) st = dsync(s);
     if (st != PAGD_OK) return st;
     s->have_state = 1;
@@ -596,7 +636,7 @@ pagd_status pagd_run_host(pagd_solver* s, const double* u0_host, double* u_host_
     s->cur = 0;
     pagd_status st = dcopy(s, s->ws + s->off[O_U0], u0_host, b);
     if (st == PAGD_OK) st = dcopy(s, s->ws + s->off[O_U1], u0_host, b);
-    if (st == PAGD_OK) st = dzero(s, s->ws + s->off[O_MASS], 2 * sizeof(double));
+    if (st == PAGD_OK) st = dzero(s, s->ws + s->off[O_MASS], 4 * sizeof(double));
     if (st != PAGD_OK) return st;
     s->have_state = 1;
     s->step = 0;
@@ -934,7 +974,7 @@ pagd_status pagd_step_static(pagd_solver* s, const double* un_dev, const double*
     const size_t b = sizeof(double) * s->npts;
     st = dcopy(s, w + s->off[O_U0], un_dev, b);
     if (st == PAGD_OK) st = dcopy(s, w + s->off[O_U1], unm1_dev, b);
-    if (st == PAGD_OK) st = dzero(s, w + s->off[O_MASS], 2 * sizeof(double));
+    if (st == PAGD_OK) st = dzero(s, w + s->off[O_MASS], 4 * sizeof(double));
     if (st != PAGD_OK) return st;
     Params P = params_for(s, w);
     P.tw64 = (const double2*)head;
@@ -1012,6 +1052,21 @@ pagd_status pagd_barrier_probe(pagd_solver* s, int count, double* us_per_phase) 
     *us_per_phase = 1000.0 * (double)ms / (double)count;
     return PAGD_OK;
 #endif
+}
+
+// Launch plan of the solver's persistent kernel (instrumentation): CTAs of
+// the last launch (0 before the first), threads per CTA, cluster size of the
+// cluster-resident iterations (0: device-wide phases only), whether the
+// passes with FP64 lines run CTA-cooperative units, dynamic shared memory.
+pagd_status pagd_launch_info(const pagd_solver* s, int* grid, int* threads, int* cluster, int* coop,
+                             size_t* smem) {
+    if (!s) return PAGD_EINVAL;
+    if (grid) *grid = s->grid_used;
+    if (threads) *threads = s->threads;
+    if (cluster) *cluster = s->cl;
+    if (coop) *coop = s->coop;
+    if (smem) *smem = s->smem;
+    return PAGD_OK;
 }
 
 pagd_status pagd_set_trace(pagd_solver* s, int enable) {
@@ -1214,6 +1269,7 @@ static pagd_status batch_chunk(pagd_batch* b, double dt, int nsteps, double tol,
         PI[i].trace = nullptr;
         PI[i].warp_bytes = (long long)b->warp_bytes;
         PI[i].coop = 0;  // batch warps own their units: no CTA-wide barriers
+        PI[i].cl = 0;    // and every phase of a batch is device-wide
         PI[i].logtw = b->logtw;
         st = dzero(s, PI[i].sc, sizeof(Scal));
         if (st != PAGD_OK) return bfail(b, st, s->err.c_str());

@@ -135,11 +135,16 @@ struct Params {
     int ref_valid, refresh;
     // the passes with an FP64 line run CTA-cooperative units (single-instance
     // launches with fixed line lengths only)
-    int coop, pad1;
+    int coop;
+    // cluster-resident iterations (cluster.cuh): the cluster size (0: off) and
+    // the control state the loop hands back to the device-wide machine (a Ctl)
+    int cl;
+    void* lctl;
     const double2* tw64;
     const float2* tw32;
     Scal* sc;
-    double* mass;  // persistent {K, D}: mass excess since set_state and this step's change
+    double* mass;  // persistent {K, D, R}: mass excess since set_state, this step's change, and
+                   // R, ||d_0||_inf of the last step started from the extrapolation (0: none)
     unsigned long long* trace;  // nullable: (phase, globaltimer) pairs, one per completed phase
     int trace_cap;
     unsigned long long* norms;
@@ -162,10 +167,14 @@ struct Ctl {
     int after, mk, m64;  // 3D middle pass: the phase after it, its fields, FP64 buffers
     int gok;             // GH64 holds this step's g_hat (an exact evaluation made it)
     int bsel;            // bank of the averaged-Newton sums of the current evaluation
-    int gmode;           // caller's guess: 0 none, 1 probing it, 2 probing the extrapolation,
+    int gmode;           // caller's guess: 0 none, 1 at it (kept when its first direction is no
+                         // larger than the record), 2 probing the extrapolation,
                          // 3 iterating from it, 4 iterating from the extrapolation
     double gnorm;        // ||d_0||_inf at the caller's guess
     int acc_used;        // the step pending acceptance started from the caller's guess
+    // record of the extrapolation's first direction: evaluation rec_ev of bank
+    // rec_bank was one; the next phase B / ACCEPT stores its norm (P.mass[2])
+    int rec_pending, rec_ev, rec_bank;
     int acc, acc_cur, acc_it, acc_lastev, acc_ev, reb, ereb, inc, ref_ok, exact_done;
     double resid, base_nrm, best_nrm, acc_resid;
 };
@@ -1108,7 +1117,9 @@ __device__ __forceinline__ void phase_B_impl(const Params& P, const Ctl& c, cons
     // rebase: the candidate of this step
     const T* dreb = (const T*)P.DD[c.it & 1];
     const double mreb = c.reb ? ldcg(&P.sums[(size_t)bank * P.nslots + c.lastev]) / (double)P.npts : 0.0;
-    if (!c.reb) {
+    // a new step clears its bank's norm and sum slots (a restart of the same
+    // step from another initial guess keeps counting in them)
+    if (!c.reb && c.gmode != 2 && c.gmode != 3 && c.gmode != 4) {
         for (long long q = gt; q < P.nslots; q += gs) {
             P.norms[(size_t)bank * P.nslots + q] = 0ull;
             P.sums[(size_t)bank * P.nslots + q] = 0.0;
@@ -1118,6 +1129,7 @@ __device__ __forceinline__ void phase_B_impl(const Params& P, const Ctl& c, cons
             P.sc->beta_sum[bank ^ 1][1] = 0.0;
         }
     }
+    if (c.rec_pending && leader(tw)) P.mass[2] = bits_dbl(ldcg(&P.norms[(size_t)c.rec_bank * P.nslots + c.rec_ev]));
     if (c.acc && leader(tw)) {
         P.stats[c.step - 1].iters = c.acc_ev;
         P.stats[c.step - 1].status = ST_OK;
@@ -1615,6 +1627,7 @@ __device__ PAGD_COLD void phase_accept(const Params& P, const Ctl& c, const Tw& 
         if (P.out_real) P.out_real[p] = x;
     }
     publish_sum(&P.mass[1], dmass);
+    if (c.rec_pending && leader(tw)) P.mass[2] = bits_dbl(ldcg(&P.norms[(size_t)c.rec_bank * P.nslots + c.rec_ev]));
     if (leader(tw)) {
         P.stats[c.step].iters = c.ev;
         P.stats[c.step].status = ST_OK;
@@ -1951,6 +1964,7 @@ __host__ __device__ inline Ctl ctl_init(const Params& P) {
     c.gmode = 0;
     c.gnorm = 0.0;
     c.acc_used = 0;
+    c.rec_pending = 0; c.rec_ev = 0; c.rec_bank = 0;
     c.inc = inc_eval(P, c.ref_ok, P.step0, 1);
     c.resid = 0.0; c.base_nrm = 0.0; c.best_nrm = 0.0; c.acc_resid = 0.0;
     switch (P.prog) {
@@ -2023,6 +2037,97 @@ __host__ __device__ inline void mid_insert(const Params& P, int pph, int pinc, i
     c.m64 = m64;
 }
 
+// The decision after an evaluation (phase R1 or RI of the evaluation numbered
+// c.ev) whose ||d||_inf is nrm: accept, fail, probe the other initial guess,
+// move the base, or iterate on (c.ph = PH_CI).  Shared by the device-wide phase
+// sequence and the cluster-resident iteration loop, so both take the same
+// decisions from the same norms.
+template <class T>
+__device__ void ctl_eval(const Params& P, Ctl& c, double nrm) {
+    const bool t64 = sizeof(T) == 8;
+    const int bank = c.step & 1;
+    c.lastev = c.ev;
+    c.ev++;
+    c.resid = nrm;
+    if (!(nrm <= 1.0e300)) { c.fail = ST_ENAN; c.ph = PH_FAIL; return; }
+    if (c.ph == PH_R1 || nrm < c.best_nrm) { c.best_nrm = nrm; c.best_ev = c.ev; }
+    if (c.ph == PH_R1) c.base_nrm = nrm;
+    // the first direction of a step from the extrapolation (Sec. 3.4.2): the
+    // record a caller's guess is judged against
+    if (c.ph == PH_R1 && !c.ereb && (c.gmode == 0 || c.gmode == 2 || c.gmode == 4)) {
+        c.rec_pending = 1;
+        c.rec_ev = c.lastev;
+        c.rec_bank = bank;
+    }
+    const double rec = (c.ph == PH_R1 && c.gmode == 1 && !c.ereb) ? ldcg(&P.mass[2]) : 0.0;
+    if (c.ph == PH_R1 && c.gmode == 1 && !c.ereb && rec > 0.0 && nrm <= rec) {
+        c.gmode = 3;  // the guess is kept: no second probe, it iterates on from here
+    }
+    const bool fp32_norm = P.precision == P_MIXED && !t64 && c.ph == PH_RI;
+    // Only an exact FP64 evaluation certifies a step.  An incremental
+    // base evaluation (T transforms of the shift from the reference
+    // point) errs by about 1e-7 of that shift, so when its norm reaches
+    // tol the base moves there and is evaluated exactly.
+    const bool inc_norm = c.ph == PH_R1 && c.inc;
+    if (nrm <= P.tol && !fp32_norm && !inc_norm) {
+        if (c.step + 1 < P.nsteps) {
+            // accepted inside the next step's phase B
+            c.acc = 1;
+            c.acc_cur = c.cur;
+            c.acc_it = c.it;
+            c.acc_lastev = c.lastev;
+            c.acc_ev = c.ev;
+            c.acc_resid = nrm;
+            c.acc_used = c.gmode == 1 || c.gmode == 3;
+            c.step++;
+            c.cur ^= 1;
+            c.exact_done = 0;
+            c.gok = 0;
+            c.gmode = 0;
+            c.bsel = c.step & 1;
+            c.inc = t64 ? 0 : inc_eval(P, c.ref_ok, P.step0 + c.step, 1);
+            c.ph = PH_B;
+        } else {
+            c.ph = PH_ACCEPT;
+        }
+    } else if (c.ev >= P.max_iter || c.ev + 1 >= P.nslots) {
+        c.fail = ST_ENOCONV;
+        c.ph = PH_FAIL;
+    } else if (c.ph == PH_R1 && c.gmode == 1 && rec > 0.0 && nrm > rec) {
+        // the guess's first direction is larger than the extrapolation's was
+        // on the last step: start this step over from the extrapolation
+        c.gmode = 4;
+        c.bsel = bank;
+        c.inc = t64 ? 0 : inc_eval(P, c.ref_ok, P.step0 + c.step, 1);
+        c.ph = PH_B;
+    } else if (c.ph == PH_R1 && c.gmode == 1 && !(rec > 0.0)) {
+        // no record yet: the first direction at the extrapolated guess as
+        // well, and the smaller of the two is kept
+        c.gnorm = nrm;
+        c.gmode = 2;
+        c.bsel = bank;
+        c.inc = t64 ? 0 : inc_eval(P, c.ref_ok, P.step0 + c.step, 1);
+        c.ph = PH_B;
+    } else if (c.ph == PH_R1 && c.gmode == 2 && nrm > c.gnorm) {
+        c.gmode = 3;  // back to the caller's guess
+        c.bsel = 3;
+        c.inc = t64 ? 0 : inc_eval(P, c.ref_ok, P.step0 + c.step, 1);
+        c.ph = PH_B;
+    } else if ((fp32_norm && (nrm <= P.tol || nrm <= kRebaseRatio * c.base_nrm ||
+                              c.ev - c.best_ev >= kStagnation)) ||
+               (inc_norm && nrm <= P.tol)) {
+        if (c.rech >= P.max_recheck) { c.fail = ST_ENOCONV; c.ph = PH_FAIL; return; }
+        c.rech++;
+        c.reb = 1;
+        // a rebase that may accept is evaluated exactly; one that only
+        // moves the base past the FP32 floor may be incremental
+        c.inc = (nrm <= P.tol || !c.exact_done) ? 0 : inc_eval(P, c.ref_ok, P.step0 + c.step, 0);
+        c.ph = PH_B;
+    } else {
+        c.ph = PH_CI;
+    }
+}
+
 template <class T>
 __device__ void ctl_step(const Params& P, Ctl& c);
 
@@ -2042,14 +2147,14 @@ __device__ void ctl_advance(const Params& P, Ctl& c) {
 
 template <class T>
 __device__ void ctl_step(const Params& P, Ctl& c) {
-    const bool t64 = sizeof(T) == 8;
     const int bank = c.step & 1;
     switch (c.ph) {
         case PH_GS: c.ph = PH_B; break;
         case PH_B:
             // a new step restarts the counts, except the repeated new-step
             // evaluations of the guess probe (they count in the step's cost)
-            if (!c.reb && c.gmode != 2 && c.gmode != 3) { c.ev = 0; c.rech = 0; }
+            if (!c.reb && c.gmode != 2 && c.gmode != 3 && c.gmode != 4) { c.ev = 0; c.rech = 0; }
+            c.rec_pending = 0;  // phase B stored it
             c.ereb = c.reb;  // the evaluation started by B is a rebase (kept through C..E)
             c.acc = 0;
             c.reb = 0;
@@ -2073,72 +2178,7 @@ __device__ void ctl_step(const Params& P, Ctl& c) {
             break;
         case PH_D: c.ph = PH_E; break;
         case PH_R1:
-        case PH_RI: {
-            const double nrm = bits_dbl(ldcg(&P.norms[(size_t)bank * P.nslots + c.ev]));
-            c.lastev = c.ev;
-            c.ev++;
-            c.resid = nrm;
-            if (!(nrm <= 1.0e300)) { c.fail = ST_ENAN; c.ph = PH_FAIL; break; }
-            if (c.ph == PH_R1 || nrm < c.best_nrm) { c.best_nrm = nrm; c.best_ev = c.ev; }
-            if (c.ph == PH_R1) c.base_nrm = nrm;
-            const bool fp32_norm = P.precision == P_MIXED && !t64 && c.ph == PH_RI;
-            // Only an exact FP64 evaluation certifies a step.  An incremental
-            // base evaluation (T transforms of the shift from the reference
-            // point) errs by about 1e-7 of that shift, so when its norm reaches
-            // tol the base moves there and is evaluated exactly.
-            const bool inc_norm = c.ph == PH_R1 && c.inc;
-            if (nrm <= P.tol && !fp32_norm && !inc_norm) {
-                if (c.step + 1 < P.nsteps) {
-                    // accepted inside the next step's phase B
-                    c.acc = 1;
-                    c.acc_cur = c.cur;
-                    c.acc_it = c.it;
-                    c.acc_lastev = c.lastev;
-                    c.acc_ev = c.ev;
-                    c.acc_resid = nrm;
-                    c.acc_used = c.gmode == 1 || c.gmode == 3;
-                    c.step++;
-                    c.cur ^= 1;
-                    c.exact_done = 0;
-                    c.gok = 0;
-                    c.gmode = 0;
-                    c.bsel = c.step & 1;
-                    c.inc = t64 ? 0 : inc_eval(P, c.ref_ok, P.step0 + c.step, 1);
-                    c.ph = PH_B;
-                } else {
-                    c.ph = PH_ACCEPT;
-                }
-            } else if (c.ev >= P.max_iter || c.ev + 1 >= P.nslots) {
-                c.fail = ST_ENOCONV;
-                c.ph = PH_FAIL;
-            } else if (c.ph == PH_R1 && c.gmode == 1) {
-                // first direction at the caller's guess; now the same at the
-                // extrapolated guess, and the smaller of the two is kept
-                c.gnorm = nrm;
-                c.gmode = 2;
-                c.bsel = bank;
-                c.inc = t64 ? 0 : inc_eval(P, c.ref_ok, P.step0 + c.step, 1);
-                c.ph = PH_B;
-            } else if (c.ph == PH_R1 && c.gmode == 2 && nrm > c.gnorm) {
-                c.gmode = 3;  // back to the caller's guess
-                c.bsel = 3;
-                c.inc = t64 ? 0 : inc_eval(P, c.ref_ok, P.step0 + c.step, 1);
-                c.ph = PH_B;
-            } else if ((fp32_norm && (nrm <= P.tol || nrm <= kRebaseRatio * c.base_nrm ||
-                                      c.ev - c.best_ev >= kStagnation)) ||
-                       (inc_norm && nrm <= P.tol)) {
-                if (c.rech >= P.max_recheck) { c.fail = ST_ENOCONV; c.ph = PH_FAIL; break; }
-                c.rech++;
-                c.reb = 1;
-                // a rebase that may accept is evaluated exactly; one that only
-                // moves the base past the FP32 floor may be incremental
-                c.inc = (nrm <= P.tol || !c.exact_done) ? 0 : inc_eval(P, c.ref_ok, P.step0 + c.step, 0);
-                c.ph = PH_B;
-            } else {
-                c.ph = PH_CI;
-            }
-            break;
-        }
+        case PH_RI: ctl_eval<T>(P, c, bits_dbl(ldcg(&P.norms[(size_t)bank * P.nslots + c.ev]))); break;
         case PH_CI: c.ph = PH_RI; c.it++; break;
         case PH_ACCEPT: c.step++; c.cur ^= 1; c.ph = PH_DONE; break;
         case PH_IM_R2:

@@ -27,7 +27,7 @@ SCHEMES = {"bdf2": BDF2, "mp": MP, "lbdf2": LBDF2, "lmp": LMP}
 PRECISIONS = {"fp64": FP64, "fp32_mixed": FP32_MIXED}
 EXPORTS = ("pagd_default_opts", "pfc_init", "fch_init", "pagd_workspace_size", "pagd_set_workspace",
            "pagd_set_state", "pagd_step", "pagd_step_with_guess", "pagd_run", "pagd_run_host", "pagd_energy", "pagd_mass",
-           "pagd_rhs", "pagd_run_adaptive", "pagd_fft_r2c", "pagd_fft_c2r", "pagd_get_state", "pagd_step_static", "pagd_barrier_probe", "pagd_set_trace",
+           "pagd_rhs", "pagd_run_adaptive", "pagd_fft_r2c", "pagd_fft_c2r", "pagd_get_state", "pagd_step_static", "pagd_barrier_probe", "pagd_launch_info", "pagd_set_trace",
            "pagd_get_trace", "pagd_last_error", "pagd_destroy", "pagd_batch_create",
            "pagd_batch_workspace_size", "pagd_batch_set_workspace", "pagd_batch_run",
            "pagd_batch_last_error", "pagd_batch_destroy")
@@ -73,6 +73,7 @@ def _declare(lib):
         "pagd_get_state": [P, P, P, IP],
         "pagd_step_static": [P, P, P, i, d, d, d, P, IP, D],
         "pagd_barrier_probe": [P, i, D],
+        "pagd_launch_info": [P, IP, IP, IP, IP, ctypes.POINTER(ctypes.c_size_t)],
         "pagd_set_trace": [P, i],
         "pagd_get_trace": [P, IP, D, i, IP],
         "pagd_last_error": [P],
@@ -317,6 +318,15 @@ class Solver:
                                               dt_prev, tol, self._ptr(u_out), ctypes.byref(it),
                                               ctypes.byref(r)), "step_static")
         return it.value, r.value
+
+    def launch_info(self):
+        """{grid (of the last launch), threads, cluster, coop, smem} of the
+        solver's persistent kernel."""
+        g, t, c, co = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        sm = ctypes.c_size_t()
+        self._check(self.lib.pagd_launch_info(self._h, ctypes.byref(g), ctypes.byref(t), ctypes.byref(c),
+                                              ctypes.byref(co), ctypes.byref(sm)), "launch_info")
+        return {"grid": g.value, "threads": t.value, "cluster": c.value, "coop": co.value, "smem": sm.value}
 
     def barrier_probe(self, count=2000):
         """Device time per empty phase of the persistent kernel (microseconds):
