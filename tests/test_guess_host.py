@@ -60,3 +60,31 @@ def test_step_with_guess_rejects_imex(emu):
     with pytest.raises(pagd.PagdError) as e:
         S.step_with_guess(S.empty_field(), u0, 0.1, 1e-8)
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_step_with_guess_against_the_record(emu, case):
+    """After a plain step the solver holds the record R (||d_0||_inf of that
+    step from the extrapolation).  A guess with ||d_0||_inf <= R is kept at no
+    extra cost: the evaluations equal the oracle's from that guess.  A poor
+    guess costs its one probe and the step starts over from the extrapolation."""
+    model, n, L, eps, e1, e2, tau, scheme, dt, mean = case
+    P = O.Problem(O.PFC if model == "pfc" else O.FCH, n, L, eps, e1, e2, tau,
+                  scheme={"bdf2": O.BDF2, "mp": O.MP}[scheme])
+    tol = 1e-10
+    u0 = I.noisy_field(n, mean, 0.05, 5)
+    u1 = O.pagd_step(P, 0, u0, u0, dt, dt, tol).u
+    tight = O.pagd_step(P, 1, u1, u0, dt, dt, 1e-13).u
+    good = tight + 1e-7 * I.noisy_field(n, 0.0, 1.0, 9) + 0.3
+    bad = I.noisy_field(n, mean, 0.5, 11)
+    for g, expect_used in ((good, True), (bad, False)):
+        S = pagd.Solver(model, n, L, eps, e1, e2, tau, scheme=scheme, precision="fp64", lib=emu)
+        S.set_state(u0)
+        S.step(S.empty_field(), dt, tol)  # the plain step that sets the record
+        out = S.empty_field()
+        its, res, used = S.step_with_guess(out, g, dt, tol)
+        assert used == expect_used
+        ref = O.pagd_step(P, 1, u1, u0, dt, dt, tol, guess=g if used else None)
+        assert np.linalg.norm(out - ref.u) <= 1e-12 * np.linalg.norm(ref.u)
+        assert its == ref.iters + (0 if used else 1), (its, ref.iters)
+        assert res <= tol
