@@ -639,7 +639,8 @@ def main():
         # learned initial iterate (FCH 512^2): train on solver trajectories, then
         # PAGD from the network's proposal vs from the extrapolation
         from paper_2204_07247_gb300 import learned
-        extra["learned"] = learned.run_study(torch, I.FCH512, list(range(1000, 1008)), [0, 1], 64, 16, 300)
+        extra["learned"] = learned.run_study(torch, I.FCH512, list(range(1000, 1016)), [2000, 2001], [0, 1, 2, 3],
+                                             96, 16, 600)
     if not args.no_forms:
         extra["batched"] = bench_batch(torch, pagd, I.PFC_BATCH96, I.PFC_BATCH96.steps, W, 20,
                                        ITER_BYTES_2D_PFC, peak, rank, world, dist)

@@ -74,7 +74,11 @@ def train(torch, net, traj, iters, batch, lr, s_in, s_out, seed=0):
 def evaluate(torch, w, net, seeds, steps, s_in, s_out, skip=20):
     """PAGD evaluations per step and device time per step, from the
     extrapolated initial iterate (plain) and from the network's proposal
-    (learned, through pagd_step_with_guess; inference included)."""
+    (learned, through pagd_step_with_guess; inference included).  Both forms
+    start after the same `skip` plain steps; the last of them gives the solver
+    its record of the extrapolation's first direction, against which each
+    proposal is judged (kept at no extra cost when its first direction is no
+    larger, else the step starts over from the extrapolation)."""
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     res = {"plain": {"evals": [], "ms": 0.0}, "learned": {"evals": [], "ms": 0.0, "used": 0}}
     for seed in seeds:
@@ -83,7 +87,6 @@ def evaluate(torch, w, net, seeds, steps, s_in, s_out, skip=20):
             S.set_state(torch.from_numpy(w.u0(seed)).cuda())
             S.run(w.dt, skip + 1, w.tol)
             out = torch.empty(w.n, dtype=torch.float64, device="cuda")
-            un, unm1, _ = S.get_state()
             torch.cuda.synchronize()
             e0.record()
             for _ in range(steps):
@@ -105,28 +108,32 @@ def evaluate(torch, w, net, seeds, steps, s_in, s_out, skip=20):
         r["evals_per_step"] = float(np.mean(r["evals"]))
         r["steps_per_s"] = n / (r["ms"] / 1000.0)
         del r["evals"]
+    res["learned"]["kept_fraction"] = res["learned"]["used"] / n
     return res
 
 
-def run_study(torch, w, train_seeds, test_seeds, steps_train, steps_test, iters, batch=4, lr=1e-3,
+def run_study(torch, w, train_seeds, val_seeds, test_seeds, steps_train, steps_test, iters, batch=4, lr=1e-3,
               channels=16, layers=4, modes=(16, 16)):
-    """Collect, train, evaluate; a dict for the benchmark line."""
+    """Collect training and (disjoint) validation trajectories, train, and
+    evaluate on test seeds disjoint from both; a dict for the benchmark line."""
     traj = trajectories(torch, w, train_seeds, steps_train)
+    vtraj = trajectories(torch, w, val_seeds, max(4, batch))
     s_in, s_out = scales(torch, traj)
     net = SB.SNO(w.n, channels=channels, layers=layers, modes=modes, batch=batch, seed=1)
-    val = [(i % traj.shape[0], (7 * i) % (traj.shape[1] - 2)) for i in range(batch)]
-    val_before = batch_loss(torch, net, traj, val, s_in, s_out)
+    val = [(i % vtraj.shape[0], i % (vtraj.shape[1] - 2)) for i in range(batch)]
+    val_before = batch_loss(torch, net, vtraj, val, s_in, s_out)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     hist = train(torch, net, traj, iters, batch, lr, s_in, s_out)
     e1.record()
     torch.cuda.synchronize()
-    val_after = batch_loss(torch, net, traj, val, s_in, s_out)
+    val_after = batch_loss(torch, net, vtraj, val, s_in, s_out)
+    del traj, vtraj
     ev = evaluate(torch, w, net, test_seeds, steps_test, s_in, s_out)
-    del traj
     return {"workload": w.name, "network": f"{layers} spectral layers, {channels} channels, "
             f"{modes[0]}x{modes[1]} modes, GELU, FP32", "train": {"trajectories": len(train_seeds),
             "steps": steps_train, "iters": iters, "batch": batch, "ms": e0.elapsed_time(e1),
             "loss_first": hist[0], "loss_last": float(np.mean(hist[-10:])),
-            "fixed_batch_loss_before": val_before, "fixed_batch_loss_after": val_after},
+            "validation_seeds": list(val_seeds), "validation_loss_before": val_before,
+            "validation_loss_after": val_after},
             "test": {"seeds": list(test_seeds), "steps": steps_test}, **ev}
