@@ -147,12 +147,17 @@ def bench_batch(torch, pagd, bw, steps, warm, plain_steps, bytes_per_eval, peak,
         R.sum_over_ranks(0.0, dist, "cuda")
         R.max_over_ranks(0.0, dist, "cuda")
         return None
-    sol = []
+    sol, u0s = [], []
     for w in members:
         S = pagd.solver_for(w)
-        S.set_state(torch.from_numpy(w.u0(w.seeds[0])).cuda())
+        u0s.append(torch.from_numpy(w.u0(w.seeds[0])).cuda())
+        S.set_state(u0s[-1])
         sol.append(S)
     B = pagd.Batch(sol)
+    # the launch shape chosen by timing (before, and outside, the timed region)
+    from paper_2204_07247_gb300 import autotune
+    schedule = autotune.tune_batch(torch, B, u0s, bw.dt, bw.tol, steps=2)
+    del u0s
     B.run(bw.dt, warm, bw.tol)
     flush_l2(torch)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -186,6 +191,7 @@ def bench_batch(torch, pagd, bw, steps, warm, plain_steps, bytes_per_eval, peak,
         "iters_per_step": float(its.mean()), "max_iters": int(its.max()), "max_resid": float(res.max()),
         "all_ok": bool(np.all(status == 0)), "gpu_launches": math.ceil(steps / 4096),
         "scaling": "strong" if world > 1 else "weak",
+        "schedule": schedule,
         "plain_member_steps_per_s": m * plain_steps / (plain_ms / 1000.0),
         "plain_sample": f"each member alone, {plain_steps} steps after {warm} warm-up steps",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -640,7 +646,7 @@ def main():
         # PAGD from the network's proposal vs from the extrapolation
         from paper_2204_07247_gb300 import learned
         extra["learned"] = learned.run_study(torch, I.FCH512, list(range(1000, 1016)), [2000, 2001], [0, 1, 2, 3],
-                                             96, 16, 600)
+                                             96, 16, 600, batched_seeds=list(range(4, 12)))
     if not args.no_forms:
         extra["batched"] = bench_batch(torch, pagd, I.PFC_BATCH96, I.PFC_BATCH96.steps, W, 20,
                                        ITER_BYTES_2D_PFC, peak, rank, world, dist)

@@ -278,6 +278,28 @@ pagd_status pagd_batch_set_workspace(pagd_batch* b, void* dev_ptr, size_t bytes)
 pagd_status pagd_batch_run(pagd_batch* b, double dt, int nsteps, double tol, int* iters_out, double* resid_out,
                            int* status_out);
 
+/* Launch shape of the batched kernel (not in the paper): warps per CTA
+ * (1..8; each warp has its own shared-memory slice for one unit's lines) and
+ * CTAs per SM (1..8; the grid is that many per SM, capped at the co-resident
+ * count).  Together they fix how the units of every global phase are tiled
+ * over the machine.  PAGD_EINVAL when the slices or the CTAs do not fit.
+ * pagd_batch_create chooses as many warps per CTA as fit, one CTA per SM;
+ * paper_2204_07247_gb300/autotune.py times candidate shapes and keeps the
+ * fastest.  pagd_batch_launch_info: CTAs of the last launch (the planned grid
+ * before the first), warps per CTA, dynamic shared memory per CTA (nullable
+ * outputs). */
+pagd_status pagd_batch_set_shape(pagd_batch* b, int warps_per_cta, int ctas_per_sm);
+pagd_status pagd_batch_launch_info(const pagd_batch* b, int* grid, int* warps_per_cta, size_t* smem);
+
+/* One step of every member in one launch, each from its own initial iterate
+ * (the batched form of pagd_step_with_guess, with the same judging of each
+ * guess against that member's record): guesses[count] device fields (n_pts
+ * doubles each, a null entry starts that member from the extrapolation).
+ * Outputs as pagd_batch_run with nsteps = 1, and used_guess_out [count]
+ * (nullable): 1 where the member's guess was kept.  Synchronises the stream. */
+pagd_status pagd_batch_step_with_guess(pagd_batch* b, const double* const* guesses, double dt, double tol,
+                                       int* iters_out, double* resid_out, int* status_out, int* used_guess_out);
+
 const char* pagd_batch_last_error(const pagd_batch* b);
 void pagd_batch_destroy(pagd_batch* b);
 

@@ -64,6 +64,13 @@ pagd_status sno_loss_grad(sno_net* s, const float* params, const double* un, con
  * t = 1, 2, ... the update count, lr the step size. */
 pagd_status sno_adam_step(sno_net* s, float* params, const float* grad, float* m, float* v, int t, double lr);
 
+/* BF16 weights: weights[i] = master[i] rounded to the nearest BF16 value (ties
+ * to even), stored as FP32 (device arrays of param_count values; may not
+ * alias).  With these weights the network computes in FP32 on BF16-valued
+ * parameters; training keeps the FP32 master copy for Adam and re-rounds
+ * after every update. */
+pagd_status sno_round_bf16(sno_net* s, const float* master, float* weights);
+
 const char* sno_last_error(const sno_net* s);
 void sno_destroy(sno_net* s);
 

@@ -57,10 +57,17 @@ __host__ __device__ constexpr int cl_size_for(int nf) {
     return (nf == 64 || nf == 128 || nf == 256) ? nf / kClRows : 0;
 }
 
-// byte offsets of the cluster buffers in a CTA's warp region (after the
-// twiddle tables); tsz = sizeof(T), K fields per pass
+// Layout of a CTA's cluster region (byte offsets after the twiddle tables;
+// tsz = sizeof(T), K fields per pass).  The two exchange buffers are laid out
+// so that what one warp sends to one CTA is a contiguous run (eight 16-byte
+// chunks from a row pair, sixteen 8-byte values from a column), and their
+// strides are padded so that the local reads spread over all banks:
+//   nbx  row pass -> column pass, [pair p][field][slot][rr] (x0 = 2 p + rr),
+//        ps complex values per pair;
+//   dbx  column pass -> row pass, [k1][field][local row], qs values per k1.
 struct ClOff {
-    unsigned d[2], s[2], g0, nbx, dbx, scr, part, end;
+    unsigned d[2], s[2], nbx, dbx, scr, part, qc, end;
+    int ps, qs;
 };
 __host__ __device__ inline unsigned cl_take(size_t& q, size_t b) {
     const size_t r = q;
@@ -71,16 +78,18 @@ __host__ __device__ inline ClOff cl_offsets(int nf, int K, int tsz) {
     const size_t c = 2 * (size_t)tsz;
     const size_t pitch = (size_t)nf + 2;
     ClOff o;
+    o.ps = K * 2 * kClSlots + (K == 2 ? 2 : 0);
+    o.qs = K * kClRows + 6;
     size_t q = 0;
-    o.d[0] = cl_take(q, (size_t)kClRows * nf * tsz);       // delta, rows x n
+    o.d[0] = cl_take(q, (size_t)kClRows * nf * tsz);          // delta, rows x n
     o.d[1] = cl_take(q, (size_t)kClRows * nf * tsz);
-    o.s[0] = cl_take(q, (size_t)kClSlots * nf * c);        // delta_hat, slots x n
+    o.s[0] = cl_take(q, (size_t)kClSlots * nf * c);           // delta_hat, slots x n
     o.s[1] = cl_take(q, (size_t)kClSlots * nf * c);
-    o.g0 = cl_take(q, (size_t)kClSlots * nf * c);          // C0
-    o.nbx = cl_take(q, (size_t)kClSlots * K * pitch * c);  // row -> column: [slot][field][x0]
-    o.dbx = cl_take(q, (size_t)kClUnits * K * pitch * c);  // column -> row: [pair][field][2 k1 + rr]
-    o.scr = cl_take(q, (size_t)kClUnits * K * pitch * c);  // one K-line buffer per unit
+    o.nbx = cl_take(q, (size_t)(nf / 2) * o.ps * c);
+    o.dbx = cl_take(q, (size_t)(nf / 2 + 1) * o.qs * c);
+    o.scr = cl_take(q, (size_t)kClUnits * 2 * K * pitch * c);  // two K-line buffers per unit
     o.part = cl_take(q, (size_t)kClUnits * 2 * sizeof(double));
+    o.qc = cl_take(q, 16 * sizeof(double));
     o.end = (unsigned)q;
     return o;
 }
@@ -106,8 +115,10 @@ __host__ __device__ inline int cl_col(int rank, int u) { return rank * kClUnits 
 __host__ __device__ inline int cl_owner(int k, int half) { return k < half ? k / kClUnits : 0; }
 __host__ __device__ inline int cl_slot(int k, int half) { return k < half ? k % kClUnits : kClUnits; }
 
+// the per-loop constants (betas, scheme coefficients, wavenumber scales) in
+// the iteration precision, computed once per loop entry
 template <class T> struct ClConst {
-    T m2, b0, b2, b4, aim, c0, e2, e4, ts, tau, eta1, eta2;
+    T m2, b0, b2, b4, aim, c0, e2, e4, ts, tau, eta1, eta2, k0s, k1s;
 };
 
 template <class T>
@@ -127,7 +138,16 @@ __device__ __forceinline__ ClConst<T> cl_const(const Params& P, const Ctl& c) {
     q.tau = (T)P.tau;
     q.eta1 = (T)P.eta1;
     q.eta2 = (T)P.eta2;
+    q.k0s = (T)P.k0sq;
+    q.k1s = (T)P.k1sq;
     return q;
+}
+
+// kappa at (k1, k0) of an n x n grid from the scales, as kappa_t computes it
+template <class T, int NF>
+__device__ __forceinline__ T cl_kappa(const ClConst<T>& q, int k1, int k0) {
+    const int r0 = (k0 <= (NF >> 1)) ? k0 : k0 - NF;
+    return q.k1s * (T)(k1 * k1) + q.k0s * (T)(r0 * r0);
 }
 
 // the column-pass point of phase_CI: from the spectral state (sc, sp, g0) and
@@ -161,6 +181,21 @@ __device__ __forceinline__ void cl_ci_point(const ClConst<T>& q, bool pfc, T l, 
     }
 }
 
+// two neighbouring complex values (rows 2 p, 2 p + 1 of one column) as one
+// 16-byte store where the element type allows it
+__device__ __forceinline__ void cl_st2(float2* p, float2 a, float2 b) {
+#ifdef PAGD_EMU
+    p[0] = a;
+    p[1] = b;
+#else
+    *(float4*)p = make_float4(a.x, a.y, b.x, b.y);
+#endif
+}
+__device__ __forceinline__ void cl_st2(double2* p, double2 a, double2 b) {
+    p[0] = a;
+    p[1] = b;
+}
+
 // Column pass of iteration it (phase_CI) on this CTA's units.
 template <class T, int NF>
 __device__ __forceinline__ void cl_col_pass(const Params& P, const Ctl& c, const ClCtx& x, const ClOff& o,
@@ -169,46 +204,48 @@ __device__ __forceinline__ void cl_col_pass(const Params& P, const Ctl& c, const
     constexpr int LOGN = ilog2c(NF), HALF = NF / 2, PITCH = NF + 2, E = NF / kWarp;
     const int K = k_iter(P.model);
     const bool pfc = P.model == M_PFC;
-    const ClConst<T> q = cl_const<T>(P, c);
+    const ClConst<T> q = *(const ClConst<T>*)(x.base + o.qc);
     const int it = c.it;
     const T l = (T)lam_at(P, it), ln = (T)lam_at(P, it + 1);
     C* S0 = (C*)(x.base + o.s[it & 1]);        // delta_hat_it
     C* S1 = (C*)(x.base + o.s[(it - 1) & 1]);  // delta_hat_{it-1}, overwritten with delta_hat_{it+1}
-    const C* G0 = (const C*)(x.base + o.g0);
-    C* NBX = (C*)(x.base + o.nbx);
+    const C* G0 = (const C*)P.C0;              // the base gradient (global, L2-resident)
+    const C* NBX = (const C*)(x.base + o.nbx);
     C* DBX = (C*)(x.base + o.dbx);
+    const int ps = o.ps, qs = o.qs;
     for (int u = warp; u < kClUnits; u += nwarps) {
-        C* sc = (C*)(x.base + o.scr) + (size_t)u * K * PITCH;
+        C* b0 = (C*)(x.base + o.scr) + (size_t)u * 2 * K * PITCH;
+        C* b1 = b0 + (size_t)K * PITCH;
         const bool pair = (x.rank == 0 && u == 0);
         const int k1 = cl_col(x.rank, u);
-        C* lines = NBX + (size_t)u * K * PITCH;
-        C* b0 = lines;
-        C* b1 = sc;
-        if (pair) {
-            // z = col(0) + i col(n/2): both real along the first axis
-            const C* lh = NBX + (size_t)kClUnits * K * PITCH;
-            for (int f = 0; f < K; f++)
+        // the base gradient of the unit's column, issued before the transform
+        C g0v[E];
+        if (!pair) {
 #pragma unroll
-                for (int i = 0; i < E; i++) {
-                    const int x0 = lane + kWarp * i;
-                    sc[(size_t)f * PITCH + x0] = C{lines[(size_t)f * PITCH + x0].x, lh[(size_t)f * PITCH + x0].x};
-                }
-            b0 = sc;
-            b1 = lines;
+            for (int i = 0; i < E; i++) g0v[i] = G0[(size_t)k1 * NF + lane + kWarp * i];
         }
+        // gather the unit's lines (columns 0 and n/2 packed as z = a + i b: both real)
+        for (int f = 0; f < K; f++)
+#pragma unroll
+            for (int i = 0; i < E; i++) {
+                const int x0 = lane + kWarp * i;
+                const C* src = NBX + (size_t)(x0 >> 1) * ps + (size_t)(f * kClSlots) * 2 + (x0 & 1);
+                b0[(size_t)f * PITCH + x0] = pair ? C{src[0].x, src[2 * kClUnits].x} : src[2 * u];
+            }
         const int r = fft_lines_fixed<-1, T, LOGN, kClMaxK>(b0, b1, PITCH, K, tw_of<T>(tw), tw.log, lane);
         C* Xr = r ? b1 : b0;
         C* Xf = r ? b0 : b1;
         if (!pair) {
-#pragma unroll 2
+            const size_t sb = (size_t)u * NF;
+#pragma unroll
             for (int i = 0; i < E; i++) {
                 const int k0 = lane + kWarp * i;
-                const size_t idx = (size_t)u * NF + k0;
                 C in[kClMaxK], out[kClMaxK];
                 for (int f = 0; f < K; f++) in[f] = Xr[(size_t)f * PITCH + k0];
                 C sn;
-                cl_ci_point<T>(q, pfc, l, ln, kappa_t<T>(P, k1, k0), S0[idx], S1[idx], G0[idx], in, sn, out);
-                S1[idx] = sn;
+                cl_ci_point<T>(q, pfc, l, ln, cl_kappa<T, NF>(q, k1, k0), S0[sb + k0], S1[sb + k0], g0v[i], in, sn,
+                               out);
+                S1[sb + k0] = sn;
                 for (int f = 0; f < K; f++) Xr[(size_t)f * PITCH + k0] = out[f];
             }
         } else {
@@ -233,10 +270,11 @@ __device__ __forceinline__ void cl_col_pass(const Params& P, const Ctl& c, const
                 for (int s = 0; s < ns; s++) {
                     const size_t ia = (size_t)kk[s], ib = sh + (size_t)kk[s];
                     C sn;
-                    cl_ci_point<T>(q, pfc, l, ln, kappa_t<T>(P, 0, kk[s]), S0[ia], S1[ia], G0[ia], A[s], sn, oa[s]);
+                    cl_ci_point<T>(q, pfc, l, ln, cl_kappa<T, NF>(q, 0, kk[s]), S0[ia], S1[ia], G0[ia], A[s], sn,
+                                   oa[s]);
                     S1[ia] = sn;
-                    cl_ci_point<T>(q, pfc, l, ln, kappa_t<T>(P, HALF, kk[s]), S0[ib], S1[ib], G0[ib], Bv[s], sn,
-                                   ob[s]);
+                    cl_ci_point<T>(q, pfc, l, ln, cl_kappa<T, NF>(q, HALF, kk[s]), S0[ib], S1[ib],
+                                   G0[(size_t)HALF * NF + kk[s]], Bv[s], sn, ob[s]);
                     S1[ib] = sn;
                 }
                 if (ns == 1)
@@ -256,19 +294,19 @@ __device__ __forceinline__ void cl_col_pass(const Params& P, const Ctl& c, const
         }
         const int r2 = fft_lines_fixed<+1, T, LOGN, kClMaxK>(Xr, Xf, PITCH, K, tw_of<T>(tw), tw.log, lane);
         const C* Yr = r2 ? Xf : Xr;
-        // scatter the inverse transforms to the row owners: DBX[pair][f][2 k1 + rr]
+        // scatter to the row owners: DBX[k1][f][local row], 16 consecutive rows
+        // per owner CTA
 #pragma unroll 2
         for (int i = 0; i < E; i++) {
             const int x0 = lane + kWarp * i;
-            const int own = x0 / kClRows, pr = (x0 % kClRows) >> 1, rr = x0 & 1;
-            C* dst = x.peer(DBX, own) + (size_t)pr * K * PITCH;
+            C* dst = x.peer(DBX, x0 / kClRows) + (x0 % kClRows);
             for (int f = 0; f < K; f++) {
                 const C w = Yr[(size_t)f * PITCH + x0];
                 if (!pair) {
-                    dst[(size_t)f * PITCH + 2 * k1 + rr] = w;
+                    dst[(size_t)k1 * qs + f * kClRows] = w;
                 } else {
-                    dst[(size_t)f * PITCH + rr] = C{w.x, (T)0};
-                    dst[(size_t)f * PITCH + 2 * HALF + rr] = C{w.y, (T)0};
+                    dst[f * kClRows] = C{w.x, (T)0};
+                    dst[(size_t)HALF * qs + f * kClRows] = C{w.y, (T)0};
                 }
             }
         }
@@ -288,7 +326,7 @@ __device__ __forceinline__ void cl_row_pass(const Params& P, const Ctl& c, const
     constexpr int EH = (HALF + 1 + kWarp - 1) / kWarp;
     const int K = k_iter(P.model);
     const bool pfc = P.model == M_PFC;
-    const ClConst<T> q = cl_const<T>(P, c);
+    const ClConst<T> q = *(const ClConst<T>*)(x.base + o.qc);
     const int it = c.it;
     const T lp = (T)lam_at(P, it - 1), l = (T)lam_at(P, it);
     T* dcur = (T*)(x.base + o.d[it & 1]);          // delta_{it-2} -> delta_it
@@ -296,13 +334,15 @@ __device__ __forceinline__ void cl_row_pass(const Params& P, const Ctl& c, const
     const T* vbt = (const T*)P.VBt;
     const T* lbt = (const T*)P.LBt;
     C* NBX = (C*)(x.base + o.nbx);
+    const C* DBX = (const C*)(x.base + o.dbx);
     double* part = (double*)(x.base + o.part);
     const T iscale = (T)P.inv_npts;
+    const int ps = o.ps, qs = o.qs;
     for (int u = warp; u < kClUnits; u += nwarps) {
         const int lr0 = 2 * u;                       // local rows lr0, lr0 + 1
         const int r0 = x.rank * kClRows + lr0;       // global rows
-        C* blk = (C*)(x.base + o.dbx) + (size_t)u * K * PITCH;
-        C* sc = (C*)(x.base + o.scr) + (size_t)u * K * PITCH;
+        C* b0 = (C*)(x.base + o.scr) + (size_t)u * 2 * K * PITCH;
+        C* b1 = b0 + (size_t)K * PITCH;
         // base fields of the two rows (global, L2-resident): issued first
         T vb[2 * E], lb[2 * E];
 #pragma unroll
@@ -319,16 +359,17 @@ __device__ __forceinline__ void cl_row_pass(const Params& P, const Ctl& c, const
             for (int i = 0; i < E; i++) {
                 const int xx = lane + kWarp * i;
                 const int k = (xx <= HALF) ? xx : NF - xx;
-                C A = blk[(size_t)f * PITCH + 2 * k], B = blk[(size_t)f * PITCH + 2 * k + 1];
+                const C* src = DBX + (size_t)k * qs + f * kClRows + lr0;
+                C A = src[0], B = src[1];
                 if (xx == 0 || xx == HALF) {
                     A.y = 0;
                     B.y = 0;
                 }
-                sc[(size_t)f * PITCH + xx] = (xx <= HALF) ? C{A.x - B.y, A.y + B.x} : C{A.x + B.y, B.x - A.y};
+                b0[(size_t)f * PITCH + xx] = (xx <= HALF) ? C{A.x - B.y, A.y + B.x} : C{A.x + B.y, B.x - A.y};
             }
-        const int r = fft_lines_fixed<+1, T, LOGN, kClMaxK>(sc, blk, PITCH, K, tw_of<T>(tw), tw.log, lane);
-        C* Xr = r ? blk : sc;
-        C* Xf = r ? sc : blk;
+        const int r = fft_lines_fixed<+1, T, LOGN, kClMaxK>(b0, b1, PITCH, K, tw_of<T>(tw), tw.log, lane);
+        C* Xr = r ? b1 : b0;
+        C* Xf = r ? b0 : b1;
         T amax = (T)0;
         double asum = 0.0;
 #pragma unroll
@@ -372,6 +413,9 @@ __device__ __forceinline__ void cl_row_pass(const Params& P, const Ctl& c, const
         const int r2 = fft_lines_fixed<-1, T, LOGN, kClMaxK>(Xr, Xf, PITCH, K, tw_of<T>(tw), tw.log, lane);
         const C* Yr = r2 ? Xf : Xr;
         const T hf = (T)0.5;
+        // scatter to the column owners: NBX[pair][f][slot][rr], eight slots of
+        // one owner side by side
+        const size_t pb = (size_t)(r0 >> 1) * ps;
         for (int f = 0; f < K; f++)
 #pragma unroll
             for (int i = 0; i < EH; i++) {
@@ -379,9 +423,8 @@ __device__ __forceinline__ void cl_row_pass(const Params& P, const Ctl& c, const
                 if (k <= HALF) {
                     const C zk = Yr[(size_t)f * PITCH + k];
                     const C zn = Yr[(size_t)f * PITCH + ((NF - k) & (NF - 1))];
-                    C* dst = x.peer(NBX, cl_owner(k, HALF)) + ((size_t)cl_slot(k, HALF) * K + f) * PITCH + r0;
-                    dst[0] = C{hf * (zk.x + zn.x), hf * (zk.y - zn.y)};
-                    dst[1] = C{hf * (zk.y + zn.y), hf * (zn.x - zk.x)};
+                    C* dst = x.peer(NBX, cl_owner(k, HALF)) + pb + (size_t)(f * kClSlots + cl_slot(k, HALF)) * 2;
+                    cl_st2(dst, C{hf * (zk.x + zn.x), hf * (zk.y - zn.y)}, C{hf * (zk.y + zn.y), hf * (zn.x - zk.x)});
                 }
             }
         const T wm = warp_max(amax);
@@ -416,7 +459,7 @@ template <class T, int NF>
 __device__ __forceinline__ void cl_transfer(const Params& P, const Ctl& c, const ClCtx& x, const ClOff& o,
                                             bool load) {
     using C = cx<T>;
-    constexpr int HALF = NF / 2, PITCH = NF + 2;
+    constexpr int HALF = NF / 2;
     const int K = k_iter(P.model);
     const int tid = (int)threadIdx.x, nt = (int)blockDim.x;
     const long long rowbase = (long long)x.rank * kClRows * NF;
@@ -429,6 +472,7 @@ __device__ __forceinline__ void cl_transfer(const Params& P, const Ctl& c, const
         }
     }
     const int nslot = (x.rank == 0) ? kClSlots : kClUnits;
+    C* nbx = (C*)(x.base + o.nbx);
     for (int sl = 0; sl < nslot; sl++) {
         const int k1 = (sl == kClUnits) ? HALF : cl_col(x.rank, sl);
         const size_t gi = (size_t)k1 * NF, li = (size_t)sl * NF;
@@ -440,19 +484,15 @@ __device__ __forceinline__ void cl_transfer(const Params& P, const Ctl& c, const
                 else gs[i] = ls[i];
             }
         }
-        C* lg = (C*)(x.base + o.g0) + li;
-        const C* gg = (const C*)P.C0 + gi;
-        C* ln = (C*)(x.base + o.nbx) + (size_t)sl * K * PITCH;
         C* gn = (C*)P.NB + (size_t)k1 * P.rows;
-        for (int i = tid; i < NF; i += nt) {
-            if (load) lg[i] = gg[i];
-        }
         for (int f = 0; f < K; f++)
             for (int i = tid; i < NF; i += nt) {
-                if (load) ln[(size_t)f * PITCH + i] = gn[(size_t)f * P.H + i];
-                else gn[(size_t)f * P.H + i] = ln[(size_t)f * PITCH + i];
+                C* ln = nbx + (size_t)(i >> 1) * o.ps + (size_t)(f * kClSlots + sl) * 2 + (i & 1);
+                if (load) *ln = gn[(size_t)f * P.H + i];
+                else gn[(size_t)f * P.H + i] = *ln;
             }
     }
+    if (load && threadIdx.x == 0) *(ClConst<T>*)(x.base + o.qc) = cl_const<T>(P, c);
 }
 
 // The loop bookkeeping after a row pass (thread 0 of each CTA, on the CTA's

@@ -1107,7 +1107,7 @@ pagd_status pagd_get_trace(pagd_solver* s, int* phase, double* t_us, int cap, in
 
 struct pagd_batch {
     std::vector<pagd_solver*> m;
-    int tsize, logtw, grid, threads;
+    int tsize, logtw, grid, threads, wpb, grid_used;
     size_t warp_bytes, smem, ws_bytes;
     char* ws;
     void* stream;
@@ -1141,7 +1141,7 @@ template <class T> static pagd_status batch_launch(pagd_batch* b, const BatchPar
     char* base = (char*)(((uintptr_t)sm.data() + 15) & ~(uintptr_t)15);
     double red[32];
     gridDim.x = (unsigned)b->grid;
-    blockDim.x = kEmuBatchWarps;
+    blockDim.x = (unsigned)b->wpb;
     threadIdx.x = 0;
     const int ntw = 1 << B.logtw;
     double2* t64 = (double2*)base;
@@ -1154,7 +1154,7 @@ template <class T> static pagd_status batch_launch(pagd_batch* b, const BatchPar
     std::vector<Ctl> ctl(B.count);
     std::vector<long long> G(B.count + 1);
     for (int i = 0; i < B.count; i++) ctl[i] = ctl_init(B.PI[i]);
-    const int wpb = kEmuBatchWarps;
+    const int wpb = b->wpb;
     const long long nw = (long long)b->grid * wpb;
     for (;;) {
         G[0] = 0;
@@ -1195,6 +1195,7 @@ template <class T> static pagd_status batch_launch(pagd_batch* b, const BatchPar
         std::snprintf(buf, sizeof(buf), "cooperative launch of pagd_batch_kernel: %s", cudaGetErrorString(e));
         return bfail(b, PAGD_ECUDA, buf);
     }
+    b->grid_used = used;
     return PAGD_OK;
 }
 #endif
@@ -1231,6 +1232,7 @@ pagd_status pagd_batch_create(pagd_batch** out, pagd_solver* const* members, int
     int wpb = fixed < kMaxSmem ? (int)std::min<size_t>((size_t)(kMaxThreads / 32), (kMaxSmem - fixed) / b->warp_bytes) : 0;
     if (wpb < 1) wpb = 1;
 #endif
+    b->wpb = wpb;
     b->threads = wpb * 32;
     b->smem = tw_smem_bytes(b->logtw) + batch_ctl_bytes(count) + (size_t)wpb * b->warp_bytes;
     if (b->smem > kMaxSmem) {
@@ -1241,6 +1243,42 @@ pagd_status pagd_batch_create(pagd_batch** out, pagd_solver* const* members, int
     b->ws_bytes = batch_off_params() + sizeof(Params) * (size_t)count;
     b->ws = nullptr;
     *out = b;
+    return PAGD_OK;
+}
+
+// Launch shape of the batched kernel: warps per CTA (each with its slice of
+// shared memory for one unit's lines) and CTAs per SM (the grid is that many
+// per SM, capped at the co-resident count when launched).  Together they fix
+// how the units of every global phase are tiled over the machine; an
+// autotuner times the candidates and keeps the fastest.
+pagd_status pagd_batch_set_shape(pagd_batch* b, int warps_per_cta, int ctas_per_sm) {
+    if (!b || warps_per_cta < 1 || warps_per_cta > kMaxThreads / 32 || ctas_per_sm < 1 || ctas_per_sm > 8)
+        return PAGD_EINVAL;
+    const size_t smem = tw_smem_bytes(b->logtw) + batch_ctl_bytes((int)b->m.size()) + (size_t)warps_per_cta * b->warp_bytes;
+    if (smem > kMaxSmem) return bfail(b, PAGD_EINVAL, "the warps' shared-memory slices do not fit one CTA");
+#ifndef PAGD_EMU
+    int dev = 0, cap = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e != cudaSuccess) return bfail(b, PAGD_ECUDA, cudaGetErrorString(e));
+    if ((size_t)ctas_per_sm * (smem + 1024) > (size_t)cap)
+        return bfail(b, PAGD_EINVAL, "that many CTAs per SM do not fit the SM's shared memory");
+    if (ctas_per_sm * warps_per_cta * 32 > 2048) return bfail(b, PAGD_EINVAL, "too many threads per SM");
+#endif
+    b->wpb = warps_per_cta;
+    b->threads = warps_per_cta * 32;
+    b->smem = smem;
+    b->grid = ctas_per_sm * num_sms();
+    return PAGD_OK;
+}
+
+// The batched kernel's launch plan: CTAs of the last launch (the planned grid
+// before the first), warps per CTA, dynamic shared memory per CTA.
+pagd_status pagd_batch_launch_info(const pagd_batch* b, int* grid, int* warps_per_cta, size_t* smem) {
+    if (!b) return PAGD_EINVAL;
+    if (grid) *grid = b->grid_used > 0 ? b->grid_used : b->grid;
+    if (warps_per_cta) *warps_per_cta = b->wpb;
+    if (smem) *smem = b->smem;
     return PAGD_OK;
 }
 
@@ -1259,7 +1297,8 @@ pagd_status pagd_batch_set_workspace(pagd_batch* b, void* dev_ptr, size_t bytes)
 }
 
 static pagd_status batch_chunk(pagd_batch* b, double dt, int nsteps, double tol, std::vector<int>& live,
-                               int done, int total_steps, int* iters_out, double* resid_out, int* status_out) {
+                               int done, int total_steps, int* iters_out, double* resid_out, int* status_out,
+                               const double* const* guesses = nullptr, int* used_out = nullptr) {
     const int count = (int)b->m.size();
     std::vector<Params> PI(count);
     pagd_status st = PAGD_OK;
@@ -1271,6 +1310,7 @@ static pagd_status batch_chunk(pagd_batch* b, double dt, int nsteps, double tol,
         PI[i].coop = 0;  // batch warps own their units: no CTA-wide barriers
         PI[i].cl = 0;    // and every phase of a batch is device-wide
         PI[i].logtw = b->logtw;
+        PI[i].guess = guesses ? guesses[i] : nullptr;  // the first step's initial iterate (nullable)
         st = dzero(s, PI[i].sc, sizeof(Scal));
         if (st != PAGD_OK) return bfail(b, st, s->err.c_str());
     }
@@ -1303,7 +1343,8 @@ static pagd_status batch_chunk(pagd_batch* b, double dt, int nsteps, double tol,
         pagd_solver* s = b->m[i];
         const pagd_status si =
             run_finish(s, PI[i], dt, nsteps, iters_out ? iters_out + (size_t)i * total_steps + done : nullptr,
-                       resid_out ? resid_out + (size_t)i * total_steps + done : nullptr, bs.bar_error != 0);
+                       resid_out ? resid_out + (size_t)i * total_steps + done : nullptr, bs.bar_error != 0,
+                       used_out ? used_out + (size_t)i * total_steps + done : nullptr);
         if (si != PAGD_OK) {
             live[i] = 0;
             if (status_out) status_out[i] = si;
@@ -1343,6 +1384,28 @@ pagd_status pagd_batch_run(pagd_batch* b, double dt, int nsteps, double tol, int
         done += c;
     }
     return first;
+}
+
+pagd_status pagd_batch_step_with_guess(pagd_batch* b, const double* const* guesses, double dt, double tol,
+                                       int* iters_out, double* resid_out, int* status_out, int* used_guess_out) {
+    if (!b) return PAGD_EINVAL;
+    if (!b->ws) return bfail(b, PAGD_ESTATE, "no batch workspace");
+    if (!guesses) return bfail(b, PAGD_EINVAL, "null guess array");
+    if (!(dt > 0.0) || !std::isfinite(dt) || !(tol >= 0.0)) return bfail(b, PAGD_EINVAL, "bad dt / tol");
+    const int count = (int)b->m.size();
+    for (int i = 0; i < count; i++) {
+        pagd_solver* s = b->m[i];
+        if (!s->ws || !s->have_state) return bfail(b, PAGD_ESTATE, "every member needs a workspace and a state");
+        if (s->stream != b->stream) return bfail(b, PAGD_EINVAL, "members must share one stream");
+        if (guesses[i] && (s->scheme == PAGD_LBDF2 || s->scheme == PAGD_LMP))
+            return bfail(b, PAGD_EINVAL, "an initial iterate applies to the implicit schemes only");
+    }
+    std::vector<int> live(count, 1);
+    if (status_out)
+        for (int i = 0; i < count; i++) status_out[i] = PAGD_OK;
+    if (used_guess_out)
+        for (int i = 0; i < count; i++) used_guess_out[i] = 0;
+    return batch_chunk(b, dt, 1, tol, live, 0, 1, iters_out, resid_out, status_out, guesses, used_guess_out);
 }
 
 const char* pagd_batch_last_error(const pagd_batch* b) { return b ? b->err.c_str() : "null batch"; }

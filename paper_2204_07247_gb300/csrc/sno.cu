@@ -25,6 +25,7 @@
 // separable stages per direction), not with a full FFT.
 #include "../../include/pagd_sno.h"
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -423,6 +424,14 @@ __global__ void k_lift_scatter(const float* sums, float* grad, int C) {
 }
 
 // Adam (Kingma and Ba, 2015) with bias correction
+// the weights as BF16 numbers (round to nearest even), kept in FP32 storage:
+// the network computes with them and accumulates in FP32, Adam updates the
+// FP32 master copy they are rounded from
+__global__ void k_round_bf16(const float* src, float* dst, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = __bfloat162float(__float2bfloat16_rn(src[i]));
+}
+
 __global__ void k_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
                        float eps, float c1, float c2) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -661,6 +670,14 @@ pagd_status sno_adam_step(sno_net* s, float* params, const float* grad, float* m
     const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
     k_adam<<<(unsigned)((n + kThr - 1) / kThr), kThr, 0, (cudaStream_t)s->stream>>>(params, grad, m, v, n, (float)lr,
                                                                                    b1, b2, 1e-8f, c1, c2);
+    CK(cudaGetLastError());
+    return PAGD_OK;
+}
+
+pagd_status sno_round_bf16(sno_net* s, const float* master, float* weights) {
+    if (!s || !master || !weights) return PAGD_EINVAL;
+    const long long n = (long long)param_count(s->d);
+    k_round_bf16<<<(unsigned)((n + kThr - 1) / kThr), kThr, 0, (cudaStream_t)s->stream>>>(master, weights, n);
     CK(cudaGetLastError());
     return PAGD_OK;
 }

@@ -112,14 +112,74 @@ def evaluate(torch, w, net, seeds, steps, s_in, s_out, skip=20):
     return res
 
 
+def batched_study(torch, w, net, s_in, s_out, seeds, steps, skip=20):
+    """Member steps per second of len(seeds) instances of w advanced (a) each
+    alone by the single-instance kernel from the extrapolation (plain), (b)
+    together by one batched launch per step chunk (batched), and (c) together,
+    one batched launch per step with every member started from the network's
+    proposal (batched + learned: one batched inference per step, each guess
+    judged against its member's record).  All three start from the same states
+    after `skip` plain steps."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def start():
+        sols = []
+        for seed in seeds:
+            S = pagd.solver_for(w)
+            S.set_state(torch.from_numpy(w.u0(seed)).cuda())
+            S.run(w.dt, skip + 1, w.tol)  # the last of these sets the record
+            sols.append(S)
+        return sols
+
+    m = len(seeds)
+    out = {"workload": w.name, "members": m, "steps": steps}
+    sols = start()
+    torch.cuda.synchronize()
+    e0.record()
+    ev = 0
+    for S in sols:
+        its, _ = S.run(w.dt, steps, w.tol)
+        ev += int(np.sum(its))
+    e1.record()
+    torch.cuda.synchronize()
+    out["plain"] = {"member_steps_per_s": m * steps / (e0.elapsed_time(e1) / 1000.0), "evals_per_step": ev / (m * steps)}
+    B = pagd.Batch(start())
+    torch.cuda.synchronize()
+    e0.record()
+    its, _, status = B.run(w.dt, steps, w.tol)
+    e1.record()
+    torch.cuda.synchronize()
+    out["batched"] = {"member_steps_per_s": m * steps / (e0.elapsed_time(e1) / 1000.0),
+                      "evals_per_step": float(its.mean()), "all_ok": bool(np.all(status == 0))}
+    sols = start()
+    B = pagd.Batch(sols)
+    ev, kept = 0, 0
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        st = [S.get_state() for S in sols]
+        un = torch.stack([s[0] for s in st])
+        unm1 = torch.stack([s[1] for s in st])
+        g = net.predict(un, unm1, 1.0, s_in, s_out)
+        its, _, status, used = B.step_with_guess([g[i] for i in range(m)], w.dt, w.tol)
+        ev += int(np.sum(its))
+        kept += int(np.sum(used))
+    e1.record()
+    torch.cuda.synchronize()
+    out["batched_learned"] = {"member_steps_per_s": m * steps / (e0.elapsed_time(e1) / 1000.0),
+                              "evals_per_step": ev / (m * steps), "kept_fraction": kept / (m * steps)}
+    return out
+
+
 def run_study(torch, w, train_seeds, val_seeds, test_seeds, steps_train, steps_test, iters, batch=4, lr=1e-3,
-              channels=16, layers=4, modes=(16, 16)):
+              channels=16, layers=4, modes=(16, 16), batched_seeds=None):
     """Collect training and (disjoint) validation trajectories, train, and
     evaluate on test seeds disjoint from both; a dict for the benchmark line."""
     traj = trajectories(torch, w, train_seeds, steps_train)
     vtraj = trajectories(torch, w, val_seeds, max(4, batch))
     s_in, s_out = scales(torch, traj)
-    net = SB.SNO(w.n, channels=channels, layers=layers, modes=modes, batch=batch, seed=1)
+    nb = max(batch, len(batched_seeds or ()))
+    net = SB.SNO(w.n, channels=channels, layers=layers, modes=modes, batch=nb, seed=1, bf16=True)
     val = [(i % vtraj.shape[0], i % (vtraj.shape[1] - 2)) for i in range(batch)]
     val_before = batch_loss(torch, net, vtraj, val, s_in, s_out)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -130,8 +190,10 @@ def run_study(torch, w, train_seeds, val_seeds, test_seeds, steps_train, steps_t
     val_after = batch_loss(torch, net, vtraj, val, s_in, s_out)
     del traj, vtraj
     ev = evaluate(torch, w, net, test_seeds, steps_test, s_in, s_out)
+    if batched_seeds:
+        ev["batched_forms"] = batched_study(torch, w, net, s_in, s_out, batched_seeds, steps_test)
     return {"workload": w.name, "network": f"{layers} spectral layers, {channels} channels, "
-            f"{modes[0]}x{modes[1]} modes, GELU, FP32", "train": {"trajectories": len(train_seeds),
+            f"{modes[0]}x{modes[1]} modes, GELU, BF16 weights with FP32 accumulation (FP32 Adam master)", "train": {"trajectories": len(train_seeds),
             "steps": steps_train, "iters": iters, "batch": batch, "ms": e0.elapsed_time(e1),
             "loss_first": hist[0], "loss_last": float(np.mean(hist[-10:])),
             "validation_seeds": list(val_seeds), "validation_loss_before": val_before,

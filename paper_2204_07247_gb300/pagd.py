@@ -29,7 +29,9 @@ EXPORTS = ("pagd_default_opts", "pfc_init", "fch_init", "pagd_workspace_size", "
            "pagd_set_state", "pagd_step", "pagd_step_with_guess", "pagd_run", "pagd_run_host", "pagd_energy", "pagd_mass",
            "pagd_rhs", "pagd_run_adaptive", "pagd_fft_r2c", "pagd_fft_c2r", "pagd_get_state", "pagd_step_static", "pagd_barrier_probe", "pagd_launch_info", "pagd_set_trace",
            "pagd_get_trace", "pagd_last_error", "pagd_destroy", "pagd_batch_create",
-           "pagd_batch_workspace_size", "pagd_batch_set_workspace", "pagd_batch_run",
+           "pagd_batch_workspace_size", "pagd_batch_set_workspace", "pagd_batch_run", "pagd_batch_set_shape",
+           "pagd_batch_step_with_guess",
+           "pagd_batch_launch_info",
            "pagd_batch_last_error", "pagd_batch_destroy")
 # phase identifiers of the persistent kernel's control machine (for traces)
 PHASES = ("B", "C", "D", "E", "R1", "CI", "RI", "ACCEPT", "FAIL", "FWD_R", "FWD_C", "INV_C", "INV_R",
@@ -82,6 +84,9 @@ def _declare(lib):
         "pagd_batch_workspace_size": [P, ctypes.POINTER(ctypes.c_size_t)],
         "pagd_batch_set_workspace": [P, P, ctypes.c_size_t],
         "pagd_batch_run": [P, d, i, d, IP, D, IP],
+        "pagd_batch_set_shape": [P, i, i],
+        "pagd_batch_step_with_guess": [P, ctypes.POINTER(P), d, d, IP, D, IP, IP],
+        "pagd_batch_launch_info": [P, IP, IP, ctypes.POINTER(ctypes.c_size_t)],
         "pagd_batch_last_error": [P],
         "pagd_batch_destroy": [P],
     }
@@ -411,6 +416,35 @@ class Batch:
         if check:
             self._check(st, "batch_run")
         return iters[:, :nsteps], res[:, :nsteps], status
+
+    def step_with_guess(self, guesses, dt, tol, check=True):
+        """One step of every member from its guess (None: the extrapolation);
+        returns (iters [count], resid [count], status [count], used [count])."""
+        cnt = len(self.members)
+        arr = (ctypes.c_void_p * cnt)(*[None if g is None else self.members[0]._ptr(g).value for g in guesses])
+        iters = np.zeros(cnt, dtype=np.int32)
+        res = np.zeros(cnt, dtype=np.float64)
+        status = np.zeros(cnt, dtype=np.int32)
+        used = np.zeros(cnt, dtype=np.int32)
+        st = self.lib.pagd_batch_step_with_guess(self._h, arr, dt, tol,
+                                                 iters.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                                 res.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                 status.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                                 used.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        if check:
+            self._check(st, "batch_step_with_guess")
+        return iters, res, status, used.astype(bool)
+
+    def set_shape(self, warps_per_cta, ctas_per_sm):
+        """Launch shape of the batched kernel; False if it does not fit."""
+        return self.lib.pagd_batch_set_shape(self._h, int(warps_per_cta), int(ctas_per_sm)) == 0
+
+    def launch_info(self):
+        g, w = ctypes.c_int(), ctypes.c_int()
+        sm = ctypes.c_size_t()
+        self._check(self.lib.pagd_batch_launch_info(self._h, ctypes.byref(g), ctypes.byref(w), ctypes.byref(sm)),
+                    "batch_launch_info")
+        return {"grid": g.value, "warps_per_cta": w.value, "smem": sm.value}
 
     def close(self):
         if self._h:

@@ -15,7 +15,7 @@ from . import inputs as I
 from . import pagd
 
 EXPORTS = ("sno_create", "sno_param_count", "sno_workspace_size", "sno_set_workspace", "sno_predict",
-           "sno_loss_grad", "sno_adam_step", "sno_last_error", "sno_destroy")
+           "sno_loss_grad", "sno_adam_step", "sno_round_bf16", "sno_last_error", "sno_destroy")
 
 
 def _declare(lib):
@@ -31,6 +31,7 @@ def _declare(lib):
         "sno_predict": [P, P, P, P, d, d, d, i, P],
         "sno_loss_grad": [P, P, P, P, P, d, d, d, i, P, ctypes.POINTER(ctypes.c_double)],
         "sno_adam_step": [P, P, P, P, P, i, d],
+        "sno_round_bf16": [P, P, P],
         "sno_last_error": [P],
         "sno_destroy": [P],
     }
@@ -50,9 +51,12 @@ def _p(t):
 
 class SNO:
     """The network on an n0 x n1 grid: channels, layers, kept modes (M0, M1),
-    and the largest number of samples per call (batch)."""
+    and the largest number of samples per call (batch).  bf16: the network
+    computes with its weights rounded to BF16 (FP32 accumulation); Adam keeps
+    the FP32 master copy and the weights are re-rounded after every update."""
 
-    def __init__(self, n, channels=16, layers=4, modes=(16, 16), batch=4, seed=0, lib=None, stream=None):
+    def __init__(self, n, channels=16, layers=4, modes=(16, 16), batch=4, seed=0, lib=None, stream=None,
+                 bf16=False):
         import torch
         self.torch = torch
         self.lib = _declare(lib if lib is not None else pagd.load())
@@ -72,7 +76,10 @@ class SNO:
         base = self.ws.data_ptr()
         self._check(self.lib.sno_set_workspace(self._h, ctypes.c_void_p(base + ((-base) % 256)), wb.value),
                     "set_workspace")
-        self.params = torch.from_numpy(self.initial_params(seed)).cuda()
+        self.bf16 = bool(bf16)
+        self.master = torch.from_numpy(self.initial_params(seed)).cuda()
+        self.params = torch.empty_like(self.master) if self.bf16 else self.master
+        self._round()
         self.m = torch.zeros_like(self.params)
         self.v = torch.zeros_like(self.params)
         self.grad = torch.zeros_like(self.params)
@@ -100,6 +107,10 @@ class SNO:
         assert o == self.nparams
         return out
 
+    def _round(self):
+        if self.bf16:
+            self._check(self.lib.sno_round_bf16(self._h, _p(self.master), _p(self.params)), "round_bf16")
+
     def _check(self, st, what):
         if st != 0:
             msg = self.lib.sno_last_error(self._h) if self._h else b""
@@ -121,8 +132,9 @@ class SNO:
 
     def adam(self, lr):
         self.t += 1
-        self._check(self.lib.sno_adam_step(self._h, _p(self.params), _p(self.grad), _p(self.m), _p(self.v),
+        self._check(self.lib.sno_adam_step(self._h, _p(self.master), _p(self.grad), _p(self.m), _p(self.v),
                                            self.t, lr), "adam")
+        self._round()
 
     def close(self):
         if self._h:

@@ -139,3 +139,30 @@ def test_batch_rejects_bad_membership(emu):
     with pytest.raises(pagd.PagdError) as e:
         Bt.run(0.1, 1, 1e-8)  # no state set
     assert e.value.status == 7
+
+
+def test_launch_shape_changes_the_schedule_not_the_results():
+    """pagd_batch_set_shape (the autotuner's knob) retiles the global phases
+    over other warp and CTA counts; the members' steps agree with the default
+    shape up to the summation order of the reductions."""
+    lib = pagd.load_emulation()
+    ws = [("pfc", (16, 16), (8 * math.pi,) * 2, (0.25,), "mp"), ("fch", (32, 16), (2 * math.pi, math.pi),
+          (0.18, 0.05, 0.07, 0.1), "bdf2"), ("pfc", (32, 32), (16 * math.pi,) * 2, (0.25,), "bdf2")]
+    outs = []
+    for shape in (None, (1, 2), (2, 4)):
+        sols = []
+        for k, (model, n, L, args, scheme) in enumerate(ws):
+            S = pagd.Solver(model, n, L, *args, scheme=scheme, precision="fp32_mixed", lib=lib)
+            S.set_state(I.noisy_field(n, 0.1 if model == "pfc" else -0.3, 0.05, 60 + k))
+            sols.append(S)
+        B = pagd.Batch(sols)
+        if shape:
+            assert B.set_shape(*shape)
+            info = B.launch_info()
+            assert info["warps_per_cta"] == shape[0]
+        B.run(0.05 if ws[0][0] == "pfc" else 1e-3, 3, 1e-8)
+        outs.append([S.get_state()[0].copy() for S in sols])
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b)
+    assert not pagd.Batch(sols).set_shape(9, 1)

@@ -135,3 +135,75 @@ def test_batch96_full_run_properties(torch, batch96):
         assert st == bw.steps
         assert np.all(np.isfinite(un))
         assert abs(un.sum() - u0.sum()) <= 1e-12 * abs(u0.sum())
+
+
+def test_launch_shapes_agree_and_autotuner_keeps_the_fastest(torch, lib):
+    """The autotuner's knob (warps per CTA x CTAs per SM) retiles the global
+    phases; every shape gives the same steps up to the summation order, and
+    tune_batch keeps the shape it timed fastest and restores the states."""
+    from paper_2204_07247_gb300 import autotune
+    ms = [m for m in I.PFC_BATCH96.members[::16]]
+    sols, u0s = [], []
+    for m in ms:
+        S = pagd.solver_for(m, lib=lib)
+        u0s.append(dev(torch, m.u0(m.seeds[0])))
+        S.set_state(u0s[-1])
+        sols.append(S)
+    B = pagd.Batch(sols)
+    rep = autotune.tune_batch(torch, B, u0s, 0.1, 1e-8, steps=1)
+    assert len(rep["candidates"]) >= 2
+    best = min(rep["candidates"], key=lambda r: r["ms_per_step"])
+    assert rep["chosen"]["warps_per_cta"] == best["warps_per_cta"]
+    assert all(S.get_state()[2] == 0 for S in sols)  # states restored
+    B.run(0.1, 3, 1e-8)
+    ref = [host(S.get_state()[0]) for S in sols]
+    for w, c in ((2, 2), (1, 4)):
+        assert B.set_shape(w, c)
+        for S, u0 in zip(sols, u0s):
+            S.set_state(u0)
+        _, res, status = B.run(0.1, 3, 1e-8)
+        assert np.all(status == 0) and np.all(res <= 1e-8)
+        for S, r in zip(sols, ref):
+            assert np.linalg.norm(host(S.get_state()[0]) - r) <= 1e-6 * np.linalg.norm(r)
+
+
+def test_batch_step_with_guess_matches_single_members(torch, lib):
+    """pagd_batch_step_with_guess: each member of one launch takes the step it
+    takes alone through pagd_step_with_guess (a good guess kept, a poor one
+    abandoned for the extrapolation, no guess: the plain step)."""
+    w = I.FCH256
+    P = O.Problem(O.FCH, w.n, w.L, w.eps, w.eta1, w.eta2, w.tau, scheme=O.BDF2)
+    u0s = [w.u0(80 + k) for k in range(3)]
+    guesses = []
+    for k, u0 in enumerate(u0s):
+        u1 = O.pagd_step(P, 0, u0, u0, w.dt, w.dt, 1e-12).u
+        tight = O.pagd_step(P, 1, u1, u0, w.dt, w.dt, 1e-12).u
+        guesses.append([dev(torch, tight + 1e-8 * I.noisy_field(w.n, 0.0, 1.0, 9)),
+                        dev(torch, I.noisy_field(w.n, w.mean, 0.3, 11)), None][k])
+
+    def fresh():
+        out = []
+        for u0 in u0s:
+            S = pagd.solver_for(w, lib=lib)
+            S.set_state(dev(torch, u0))
+            S.step(S.empty_field(), w.dt, w.tol)  # the record
+            out.append(S)
+        return out
+
+    ref = []
+    for S, g in zip(fresh(), guesses):
+        o = S.empty_field()
+        if g is None:
+            S.step(o, w.dt, w.tol)
+            used = False
+        else:
+            _, _, used = S.step_with_guess(o, g, w.dt, w.tol)
+        ref.append((host(o), used))
+    sols = fresh()
+    B = pagd.Batch(sols)
+    its, res, status, used = B.step_with_guess(guesses, w.dt, w.tol)
+    assert np.all(status == 0) and np.all(res <= w.tol)
+    assert list(used) == [True, False, False]
+    for S, (o, u) in zip(sols, ref):
+        un = host(S.get_state()[0])
+        assert np.linalg.norm(un - o) <= 1e-6 * np.linalg.norm(o)

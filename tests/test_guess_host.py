@@ -88,3 +88,47 @@ def test_step_with_guess_against_the_record(emu, case):
         assert np.linalg.norm(out - ref.u) <= 1e-12 * np.linalg.norm(ref.u)
         assert its == ref.iters + (0 if used else 1), (its, ref.iters)
         assert res <= tol
+
+
+def test_batch_step_with_guess_matches_single_members(emu):
+    """pagd_batch_step_with_guess: every member of one launch takes the step
+    pagd_step_with_guess takes alone (a member without a guess takes the plain
+    step), including the judging against each member's record."""
+    model, n, L, eps, e1, e2, tau, scheme, dt, mean = CASES[0]
+    P = O.Problem(O.FCH, n, L, eps, e1, e2, tau, scheme=O.BDF2)
+    tol = 1e-10
+    u0s = [I.noisy_field(n, mean, 0.05, 70 + k) for k in range(3)]
+    guesses = []
+    for k, u0 in enumerate(u0s):
+        u1 = O.pagd_step(P, 0, u0, u0, dt, dt, tol).u
+        tight = O.pagd_step(P, 1, u1, u0, dt, dt, 1e-13).u
+        guesses.append([tight + 1e-7 * I.noisy_field(n, 0.0, 1.0, 9), I.noisy_field(n, mean, 0.5, 11), None][k])
+
+    def fresh():
+        out = []
+        for u0 in u0s:
+            S = pagd.Solver(model, n, L, eps, e1, e2, tau, scheme=scheme, precision="fp64", lib=emu)
+            S.set_state(u0)
+            S.step(S.empty_field(), dt, tol)  # the record
+            out.append(S)
+        return out
+
+    alone = fresh()
+    ref = []
+    for S, g in zip(alone, guesses):
+        o = S.empty_field()
+        if g is None:
+            its, res = S.step(o, dt, tol)
+            used = False
+        else:
+            its, res, used = S.step_with_guess(o, g, dt, tol)
+        ref.append((o, its, used))
+    sols = fresh()
+    B = pagd.Batch(sols)
+    its, res, status, used = B.step_with_guess(guesses, dt, tol)
+    assert np.all(status == 0) and np.all(res <= tol)
+    for S, (o, it, u), k, uu in zip(sols, ref, its, used):
+        un = S.get_state()[0]
+        assert np.linalg.norm(un - o) <= 1e-12 * np.linalg.norm(o)
+        assert k == it and bool(uu) == bool(u)
+    assert list(used) == [True, False, False]
