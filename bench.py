@@ -346,6 +346,45 @@ def gpu_vs_reference(torch, pagd, w):
             "estimator": f"{rec['sketch']['count']}-projection sketch", "checkpoints": rows}
 
 
+def batch_vs_reference(torch, pagd, names):
+    """Members with a stored oracle reference trajectory (tests/golden), run
+    together as one batch from u0 through the reference's checkpoints: the
+    relative L2 error at each (sketch estimate) beside the oracle's own
+    tolerance floor."""
+    recs = [reference_fixture(n) for n in names]
+    recs = [r for r in recs if r is not None]
+    if not recs:
+        return None
+    ws = [I.Workload(r["workload"], r["model"], tuple(r["n"]), tuple(r["L"]), r["eps"], r["eta1"], r["eta2"],
+                     r["tau"], r["M"], r["scheme"], "fp32_mixed", r["dt"], 0, r["tol"], r["mean"], r["amp"],
+                     (r["seed"],), r["s"], tuple(r["eta"])) for r in recs]
+    sols = []
+    for r, w in zip(recs, ws):
+        S = pagd.solver_for(w)
+        S.set_state(torch.from_numpy(w.u0(r["seed"])).cuda())
+        sols.append(S)
+    B = pagd.Batch(sols) if len(sols) > 1 else None
+    out = {r["workload"]: {} for r in recs}
+    done = 0
+    for step in sorted({int(k) for r in recs for k in r["states"]}):
+        if B is not None:
+            B.run(ws[0].dt, step - done, ws[0].tol)
+        else:
+            sols[0].run(ws[0].dt, step - done, ws[0].tol)
+        done = step
+        for r, S in zip(recs, sols):
+            if str(step) not in r["states"]:
+                continue
+            ref = r["states"][str(step)]
+            u = S.get_state()[0].cpu().numpy()
+            out[r["workload"]][str(step)] = {
+                "rel_l2_est": I.sketch_rel_l2(I.sketch(u, r["sketch"]["count"], r["sketch"]["seed"]), ref["sketch"],
+                                              ref["sumsq"]),
+                "oracle_tol_floor": r.get("tol_floor", {}).get("rel_l2", {}).get(str(step))}
+    return {"reference": "tests/golden (FP64 oracle)", "form": "batched" if B is not None else "plain",
+            "members": out}
+
+
 def bench_pfc64(torch, pagd, warm, cores, cpu=True):
     """PFC 2D 64^2 MP FP64 (100 steps): GPU steps/s, its error against the
     oracle over the whole run, and the oracle timed in full on the host."""
@@ -653,8 +692,16 @@ def main():
         w3 = I.PFC3D256
         bw3 = I.BatchWorkload(w3.name + "_x2", [w3, dataclasses.replace(w3, seeds=(w3.seeds[1],))],
                               w3.dt, w3.steps, w3.tol)
-        extra["pfc3d"] = bench_batch(torch, pagd, bw3, w3.steps, W, 5, ITER_BYTES_3D_PFC, peak, rank,
+        extra["pfc3d"] = bench_batch(torch, pagd, bw3, w3.steps, W, w3.steps, ITER_BYTES_3D_PFC, peak, rank,
                                      world, dist)
+        if rank == 0:
+            firsts = ["pfc2d_128_mp_fp32mixed_i0", "pfc2d_256_mp_fp32mixed_i32", "pfc2d_512_mp_fp32mixed_i64"]
+            if extra["batched"]:
+                extra["batched"]["vs_reference_trajectory"] = batch_vs_reference(torch, pagd, firsts)
+            if extra["pfc3d"]:
+                extra["pfc3d"]["vs_reference_trajectory"] = {
+                    "at_64^3_same_spacing": batch_vs_reference(torch, pagd, ["pfc3d_64_bdf2_fp32mixed"]),
+                    "at_256^3": batch_vs_reference(torch, pagd, [w3.name])}
         if rank == 0 and not args.no_cpu_baseline:
             # secondary baselines: a failure here is reported, never fatal to the line
             for key, fn in (("batched", lambda: oracle_batch_baseline(I.PFC_BATCH96, 2, host_cores())),
