@@ -167,6 +167,7 @@ def bench_batch(torch, pagd, bw, steps, warm, plain_steps, bytes_per_eval, peak,
     e1.record()
     torch.cuda.synchronize()
     ms = R.max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+    launch = B.launch_info()
     npts = np.array([int(np.prod(w.n)) for w in members], dtype=np.float64)
     evals = its.sum(axis=1).astype(np.float64)
     nbytes = R.sum_over_ranks(float((evals * npts).sum()) * bytes_per_eval, dist, "cuda")
@@ -192,6 +193,9 @@ def bench_batch(torch, pagd, bw, steps, warm, plain_steps, bytes_per_eval, peak,
         "all_ok": bool(np.all(status == 0)), "gpu_launches": math.ceil(steps / 4096),
         "scaling": "strong" if world > 1 else "weak",
         "schedule": schedule,
+        "launch": {**launch, "strategy": "member after member through the single-instance kernel (every member "
+                                         "alone fills every warp of the launch)" if launch["sequential"]
+                   else "one batched launch per chunk"},
         "plain_member_steps_per_s": m * plain_steps / (plain_ms / 1000.0),
         "plain_sample": f"each member alone, {plain_steps} steps after {warm} warm-up steps",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -457,26 +461,25 @@ def oracle_batch_baseline(bw, steps=2, threads=1):
                       f"{tot:.1f} s, FP64 C oracle, {threads} threads on its line transforms"}
 
 
-def oracle_3d_estimate(w, n_small=64, threads=1):
-    """The oracle on the same 3D problem at n_small^3 with the same spacing,
-    one step, extrapolated to the full grid by points x log2(points): an
-    estimate of member steps per second, labelled as such."""
+def oracle_3d_measured(w, threads=1, steps=1):
+    """The oracle on the full 3D workload, `steps` steps from u0 of the
+    first seed, timed: member steps per second (a bounded sample; one 256^3
+    step is tens of seconds on the host cores)."""
     from oracle import oracle as O
-    from paper_2204_07247_gb300 import inputs as I
     O.set_threads(threads)
-    n = (n_small,) * len(w.n)
-    L = tuple(l * n_small / nn for l, nn in zip(w.L, w.n))
-    P = _oracle_problem(w, n, L)
-    un = I.noisy_field(n, w.mean, w.amp, w.seeds[0])
+    P = _oracle_problem(w)
+    un = w.u0(w.seeds[0])
+    unm1 = un.copy()
+    its = []
     t0 = time.perf_counter()
-    r = O.pagd_step(P, 0, un, un.copy(), w.dt, w.dt, w.tol)
+    for k in range(steps):
+        r = O.pagd_step(P, k, un, unm1, w.dt, w.dt, w.tol)
+        its.append(r.iters)
+        unm1, un = un, r.u
     t = time.perf_counter() - t0
-    big, small = float(np.prod(w.n)), float(np.prod(n))
-    scale = big * math.log2(big) / (small * math.log2(small))
-    return {"value": 1.0 / (t * scale), "unit": "member steps/s", "cores": threads, "kind": "oracle",
-            "sample": f"estimate: one step at {n_small}^3 (same spacing, {r.iters} evaluations, {t:.1f} s) "
-                      f"scaled by points x log2(points) ({scale:.0f}x) to {w.n}; FP64 C oracle, "
-                      f"{threads} threads on its line transforms"}
+    return {"value": steps / t, "unit": "member steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"measured: the first {steps} step(s) of {w.n} from u0 ({its} PAGD evaluations, {t:.1f} s), "
+                      f"FP64 C oracle, {threads} threads on its line transforms"}
 
 
 def run_reference(args, w, rank):
@@ -507,9 +510,11 @@ def run_reference(args, w, rank):
 FORMS = ("single", "batched", "pfc3d")
 
 
-def form_solvers(torch, pagd, form, w):
+def form_solvers(torch, pagd, form, w, grid=None):
     """Solvers (state set) and a runner for one form: the single-instance
-    workload w, the 96-member batch, or the two-seed 3D batch."""
+    workload w, the 96-member batch, or the two-seed 3D batch (grid: the 3D
+    members at grid^3 with the same spacing, for a capture that must stay
+    small)."""
     if form == "single":
         S = pagd.solver_for(w)
         S.set_state(torch.from_numpy(w.u0(1)).cuda())
@@ -517,7 +522,10 @@ def form_solvers(torch, pagd, form, w):
     if form == "batched":
         members = I.PFC_BATCH96.members
     else:
-        members = [I.PFC3D256, dataclasses.replace(I.PFC3D256, seeds=(I.PFC3D256.seeds[1],))]
+        w3 = I.PFC3D256
+        if grid:
+            w3 = dataclasses.replace(w3, n=(grid,) * 3, L=tuple(l * grid / n for l, n in zip(w3.L, w3.n)))
+        members = [w3, dataclasses.replace(w3, seeds=(w3.seeds[1],))]
     sol = []
     for m in members:
         S = pagd.solver_for(m)
@@ -528,11 +536,11 @@ def form_solvers(torch, pagd, form, w):
     return sol, (lambda k: B.run(m0.dt, k, m0.tol)), m0.dt
 
 
-def profile_form(torch, pagd, form, w, steps, warm, trace):
+def profile_form(torch, pagd, form, w, steps, warm, trace, grid=None):
     """One warm-up launch, then one launch of `steps` steps (the launch an ncu
     capture with -s 1 -c 1 takes); with trace, print its phase breakdown."""
     import collections
-    sol, run, _ = form_solvers(torch, pagd, form, w)
+    sol, run, _ = form_solvers(torch, pagd, form, w, grid)
     run(warm)
     if trace:
         sol[0].set_trace(True)
@@ -571,6 +579,8 @@ def main():
     ap.add_argument("--profile", choices=FORMS, help="one warm-up launch and one launch of --steps steps of "
                     "a form, then exit (the launch for ncu -s 1 -c 1)")
     ap.add_argument("--trace", choices=FORMS, help="print the phase trace of --steps steps of a form")
+    ap.add_argument("--profile-grid", type=int, default=None,
+                    help="with --profile / --trace pfc3d: the 3D members at this grid^3, same spacing")
     args = ap.parse_args()
     w = I.WORKLOADS[args.workload]
 
@@ -593,7 +603,7 @@ def main():
     W = max(3, args.warmup)
     K = max(1, args.steps)
     if args.profile or args.trace:
-        return profile_form(torch, pagd, args.profile or args.trace, w, K, W, bool(args.trace))
+        return profile_form(torch, pagd, args.profile or args.trace, w, K, W, bool(args.trace), args.profile_grid)
     S = pagd.solver_for(w)
     u0 = torch.from_numpy(w.u0(1 + rank)).cuda()
     S.set_state(u0)
@@ -705,7 +715,7 @@ def main():
         if rank == 0 and not args.no_cpu_baseline:
             # secondary baselines: a failure here is reported, never fatal to the line
             for key, fn in (("batched", lambda: oracle_batch_baseline(I.PFC_BATCH96, 2, host_cores())),
-                            ("pfc3d", lambda: oracle_3d_estimate(w3, 64, host_cores()))):
+                            ("pfc3d", lambda: oracle_3d_measured(w3, host_cores(), 1))):
                 if extra[key]:
                     try:
                         extra[key]["cpu_baseline"] = fn()

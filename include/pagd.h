@@ -268,7 +268,12 @@ pagd_status pagd_batch_workspace_size(const pagd_batch* b, size_t* bytes);
 pagd_status pagd_batch_set_workspace(pagd_batch* b, void* dev_ptr, size_t bytes);
 
 /* Advance every member nsteps steps of size dt to tolerance tol (as pagd_run),
- * in one device launch per chunk of at most 4096 steps.  Outputs, all
+ * in one device launch per chunk of at most 4096 steps.  When every member
+ * alone fills every warp of the batched launch in every phase (e.g. 3D grids
+ * of 256^3), one launch adds no concurrency and members that drift apart in
+ * their phases would slow every global phase to its slowest part; such
+ * batches run member after member through the single-instance kernel
+ * (pagd_batch_launch_info reports it); pagd_batch_step_with_guess likewise.  Outputs, all
  * nullable host arrays: iters_out / resid_out [count x nsteps], member-major
  * (entries after a member's failing step are not written); status_out [count]
  * per-member status.  Returns PAGD_OK when every member completed, else the
@@ -286,10 +291,12 @@ pagd_status pagd_batch_run(pagd_batch* b, double dt, int nsteps, double tol, int
  * pagd_batch_create chooses as many warps per CTA as fit, one CTA per SM;
  * paper_2204_07247_gb300/autotune.py times candidate shapes and keeps the
  * fastest.  pagd_batch_launch_info: CTAs of the last launch (the planned grid
- * before the first), warps per CTA, dynamic shared memory per CTA (nullable
- * outputs). */
+ * before the first), warps per CTA, dynamic shared memory per CTA, and
+ * whether the last run went member after member (nullable outputs; see
+ * pagd_batch_run). */
 pagd_status pagd_batch_set_shape(pagd_batch* b, int warps_per_cta, int ctas_per_sm);
-pagd_status pagd_batch_launch_info(const pagd_batch* b, int* grid, int* warps_per_cta, size_t* smem);
+pagd_status pagd_batch_launch_info(const pagd_batch* b, int* grid, int* warps_per_cta, size_t* smem,
+                                   int* sequential);
 
 /* One step of every member in one launch, each from its own initial iterate
  * (the batched form of pagd_step_with_guess, with the same judging of each

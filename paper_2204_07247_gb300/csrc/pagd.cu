@@ -608,6 +608,17 @@ pagd_status pagd_run(pagd_solver* s, double* u_dev, double dt, int nsteps, doubl
     return PAGD_OK;
 }
 
+// one step from the caller's initial iterate, the new state kept in the solver
+// (u_dev nullable)
+static pagd_status run_with_guess(pagd_solver* s, const double* guess_dev, double dt, double tol, int* iters_out,
+                                  double* resid_out, int* used_guess_out, double* u_dev = nullptr) {
+    Params P = run_params(s, u_dev, dt, 1, tol);
+    P.guess = guess_dev;
+    pagd_status st = run_program(s, P);
+    if (st != PAGD_OK) return st;
+    return run_finish(s, P, dt, 1, iters_out, resid_out, false, used_guess_out);
+}
+
 pagd_status pagd_step_with_guess(pagd_solver* s, double* u_dev, const double* guess_dev, double dt, double tol,
                                  int* iters_out, double* resid_out, int* used_guess_out) {
     if (!s) return PAGD_EINVAL;
@@ -616,11 +627,7 @@ pagd_status pagd_step_with_guess(pagd_solver* s, double* u_dev, const double* gu
     if (s->scheme == PAGD_LBDF2 || s->scheme == PAGD_LMP)
         return fail(s, PAGD_EINVAL, "an initial iterate applies to the implicit schemes only");
     if (!(dt > 0.0) || !std::isfinite(dt) || !(tol >= 0.0)) return fail(s, PAGD_EINVAL, "bad dt / tol");
-    Params P = run_params(s, u_dev, dt, 1, tol);
-    P.guess = guess_dev;
-    pagd_status st = run_program(s, P);
-    if (st != PAGD_OK) return st;
-    return run_finish(s, P, dt, 1, iters_out, resid_out, false, used_guess_out);
+    return run_with_guess(s, guess_dev, dt, tol, iters_out, resid_out, used_guess_out, u_dev);
 }
 
 pagd_status pagd_step(pagd_solver* s, double* u_dev, double dt, double tol, int* iters_out, double* resid_out) {
@@ -1108,6 +1115,7 @@ pagd_status pagd_get_trace(pagd_solver* s, int* phase, double* t_us, int cap, in
 struct pagd_batch {
     std::vector<pagd_solver*> m;
     int tsize, logtw, grid, threads, wpb, grid_used;
+    int sequential;  // the last run went member after member (batch_members_fill_the_device)
     size_t warp_bytes, smem, ws_bytes;
     char* ws;
     void* stream;
@@ -1273,9 +1281,12 @@ pagd_status pagd_batch_set_shape(pagd_batch* b, int warps_per_cta, int ctas_per_
 }
 
 // The batched kernel's launch plan: CTAs of the last launch (the planned grid
-// before the first), warps per CTA, dynamic shared memory per CTA.
-pagd_status pagd_batch_launch_info(const pagd_batch* b, int* grid, int* warps_per_cta, size_t* smem) {
+// before the first), warps per CTA, dynamic shared memory per CTA, and whether
+// the last run went member after member.
+pagd_status pagd_batch_launch_info(const pagd_batch* b, int* grid, int* warps_per_cta, size_t* smem,
+                                   int* sequential) {
     if (!b) return PAGD_EINVAL;
+    if (sequential) *sequential = b->sequential;
     if (grid) *grid = b->grid_used > 0 ? b->grid_used : b->grid;
     if (warps_per_cta) *warps_per_cta = b->wpb;
     if (smem) *smem = b->smem;
@@ -1359,6 +1370,30 @@ static pagd_status batch_chunk(pagd_batch* b, double dt, int nsteps, double tol,
     return first;
 }
 
+// Whether every member alone fills every warp of the batched launch in every
+// phase (row pairs, columns, middle-axis groups): a single launch then adds no
+// concurrency, and members that drift apart in their phases make every global
+// phase as slow as its slowest part, so such batches run member after member
+// through the single-instance kernel.
+static bool batch_members_fill_the_device(const pagd_batch* b) {
+    // PAGD_BATCH_SEQ=0 / 1 forces the batched launch / member after member
+    if (const char* e = std::getenv("PAGD_BATCH_SEQ")) {
+        if ((e[0] == '0' || e[0] == '1') && e[1] == 0) return e[0] == '1';
+    }
+#ifdef PAGD_EMU
+    return false;  // the emulation exists to exercise the batched kernel
+#endif
+    const long long warps = (long long)b->grid * b->wpb;
+    for (const pagd_solver* s : b->m) {
+        const long long rows = rows_of(s), nm = s->dim == 3 ? s->n[1] : 1;
+        long long units = rows / 2;
+        units = std::min(units, (long long)s->h1 * nm);
+        if (s->dim == 3) units = std::min(units, (long long)s->h1 * (s->n[0] / kMidG));
+        if (units < warps) return false;
+    }
+    return b->m.size() > 1;
+}
+
 pagd_status pagd_batch_run(pagd_batch* b, double dt, int nsteps, double tol, int* iters_out, double* resid_out,
                            int* status_out) {
     if (!b) return PAGD_EINVAL;
@@ -1375,6 +1410,23 @@ pagd_status pagd_batch_run(pagd_batch* b, double dt, int nsteps, double tol, int
     if (status_out)
         for (int i = 0; i < count; i++) status_out[i] = PAGD_OK;
     pagd_status first = PAGD_OK;
+    b->sequential = batch_members_fill_the_device(b) ? 1 : 0;
+    if (b->sequential) {
+        for (int i = 0; i < count; i++) {
+            pagd_solver* s = b->m[i];
+            const pagd_status si = pagd_run(s, nullptr, dt, nsteps, tol, iters_out ? iters_out + (size_t)i * nsteps : nullptr,
+                                            resid_out ? resid_out + (size_t)i * nsteps : nullptr);
+            if (si == PAGD_ECUDA || si == PAGD_ETIMEOUT) return bfail(b, si, s->err.c_str());
+            if (si != PAGD_OK) {
+                if (status_out) status_out[i] = si;
+                if (first == PAGD_OK) {
+                    first = si;
+                    b->err = s->err;
+                }
+            }
+        }
+        return first;
+    }
     int done = 0;
     while (done < nsteps) {
         const int c = (nsteps - done > kMaxChunk) ? kMaxChunk : nsteps - done;
@@ -1405,6 +1457,29 @@ pagd_status pagd_batch_step_with_guess(pagd_batch* b, const double* const* guess
         for (int i = 0; i < count; i++) status_out[i] = PAGD_OK;
     if (used_guess_out)
         for (int i = 0; i < count; i++) used_guess_out[i] = 0;
+    b->sequential = batch_members_fill_the_device(b) ? 1 : 0;
+    if (b->sequential) {
+        pagd_status first = PAGD_OK;
+        for (int i = 0; i < count; i++) {
+            pagd_solver* s = b->m[i];
+            pagd_status si;
+            if (guesses[i]) {
+                si = run_with_guess(s, guesses[i], dt, tol, iters_out ? iters_out + i : nullptr,
+                                    resid_out ? resid_out + i : nullptr, used_guess_out ? used_guess_out + i : nullptr);
+            } else {
+                si = pagd_run(s, nullptr, dt, 1, tol, iters_out ? iters_out + i : nullptr, resid_out ? resid_out + i : nullptr);
+            }
+            if (si == PAGD_ECUDA || si == PAGD_ETIMEOUT) return bfail(b, si, s->err.c_str());
+            if (si != PAGD_OK) {
+                if (status_out) status_out[i] = si;
+                if (first == PAGD_OK) {
+                    first = si;
+                    b->err = s->err;
+                }
+            }
+        }
+        return first;
+    }
     return batch_chunk(b, dt, 1, tol, live, 0, 1, iters_out, resid_out, status_out, guesses, used_guess_out);
 }
 

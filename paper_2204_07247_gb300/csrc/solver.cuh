@@ -2367,15 +2367,17 @@ constexpr int kIdleRank = 1 << 28;  // rank * 32 exceeds any point count (< 2^32
 // Tw of warp gw for instance i whose work is [g, g + cost) on the cost axis.
 __host__ __device__ inline void batch_split(Tw& t, long long gw, long long nw, long long total, long long g,
                                             long long cost, int units, int q) {
-    // Members with very many units per warp (3D grids): their units are dealt
-    // round robin over the warps whose slice starts inside the member ([ra, rb];
-    // every warp is in at most one such group), as in a single-instance launch,
-    // so that neighbouring units (which share 32-byte sectors of the half
-    // spectra) run at the same time instead of one after the other on one
-    // warp.  (Measured: better for two 256^3 members, worse for 2D members of
-    // up to 512^2, which keep contiguous ranges.)
+    // Members spread over many warps with very many units each (3D grids):
+    // their units are dealt round robin over the warps whose slice starts
+    // inside the member ([ra, rb]; every warp is in at most one such group), as
+    // in a single-instance launch, so that neighbouring units (which share
+    // 32-byte sectors of the half spectra) run at the same time instead of one
+    // after the other on one warp.  Members with a share of a few warps keep
+    // contiguous ranges (measured better for 2D members up to 512^2; a member
+    // smaller than one warp's share would otherwise land on one warp on top of
+    // that warp's own slice).
     const long long ra = (g * nw + total - 1) / total, rb = ((g + cost) * nw + total - 1) / total - 1;
-    if (rb >= ra && (long long)units >= 32 * (rb - ra + 1)) {
+    if (rb - ra + 1 >= 16 && (long long)units >= 32 * (rb - ra + 1)) {
         if (gw < ra || gw > rb) {
             t.wr = kIdleRank;
             t.wn = 1;

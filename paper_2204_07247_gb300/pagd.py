@@ -86,7 +86,7 @@ def _declare(lib):
         "pagd_batch_run": [P, d, i, d, IP, D, IP],
         "pagd_batch_set_shape": [P, i, i],
         "pagd_batch_step_with_guess": [P, ctypes.POINTER(P), d, d, IP, D, IP, IP],
-        "pagd_batch_launch_info": [P, IP, IP, ctypes.POINTER(ctypes.c_size_t)],
+        "pagd_batch_launch_info": [P, IP, IP, ctypes.POINTER(ctypes.c_size_t), IP],
         "pagd_batch_last_error": [P],
         "pagd_batch_destroy": [P],
     }
@@ -440,11 +440,11 @@ class Batch:
         return self.lib.pagd_batch_set_shape(self._h, int(warps_per_cta), int(ctas_per_sm)) == 0
 
     def launch_info(self):
-        g, w = ctypes.c_int(), ctypes.c_int()
+        g, w, q = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         sm = ctypes.c_size_t()
-        self._check(self.lib.pagd_batch_launch_info(self._h, ctypes.byref(g), ctypes.byref(w), ctypes.byref(sm)),
-                    "batch_launch_info")
-        return {"grid": g.value, "warps_per_cta": w.value, "smem": sm.value}
+        self._check(self.lib.pagd_batch_launch_info(self._h, ctypes.byref(g), ctypes.byref(w), ctypes.byref(sm),
+                                                    ctypes.byref(q)), "batch_launch_info")
+        return {"grid": g.value, "warps_per_cta": w.value, "smem": sm.value, "sequential": bool(q.value)}
 
     def close(self):
         if self._h:

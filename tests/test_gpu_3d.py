@@ -148,3 +148,26 @@ def test_pfc3d_256_full_run_properties(torch, batch3d):
         assert abs(u.sum() - u0.sum()) <= 1e-12 * abs(u0.sum())
     dn = _oracle_direction_norm(w, w.steps - 1, un, unm1, host(solvers[1].get_state()[0]))
     assert dn <= 2 * w.tol, dn
+
+
+def test_3d_batched_launch_matches_member_after_member(torch, lib, monkeypatch):
+    """Two 3D members fill the device on their own, so pagd_batch_run runs
+    them member after member through the single-instance kernel; forced into
+    one batched launch (PAGD_BATCH_SEQ=0) they take the same steps."""
+    import dataclasses
+    w = dataclasses.replace(I.PFC3D256, n=(64,) * 3, L=tuple(l / 4 for l in I.PFC3D256.L))
+    outs = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("PAGD_BATCH_SEQ", mode)
+        sols = []
+        for seed in w.seeds:
+            S = pagd.solver_for(w, lib=lib)
+            S.set_state(dev(torch, w.u0(seed)))
+            sols.append(S)
+        B = pagd.Batch(sols)
+        its, res, status = B.run(w.dt, 6, w.tol)
+        assert np.all(status == 0) and np.all(res <= w.tol)
+        assert B.launch_info()["sequential"] == (mode == "1")
+        outs[mode] = [host(S.get_state()[0]) for S in sols]
+    for a, b in zip(outs["0"], outs["1"]):
+        assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b)

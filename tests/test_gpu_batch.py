@@ -157,7 +157,8 @@ def test_launch_shapes_agree_and_autotuner_keeps_the_fastest(torch, lib):
     assert all(S.get_state()[2] == 0 for S in sols)  # states restored
     B.run(0.1, 3, 1e-8)
     ref = [host(S.get_state()[0]) for S in sols]
-    for w, c in ((2, 2), (1, 4)):
+    assert not B.set_shape(1, 8)  # eight 512^2 slices do not fit one SM
+    for w, c in ((2, 1), (1, 2)):
         assert B.set_shape(w, c)
         for S, u0 in zip(sols, u0s):
             S.set_state(u0)
