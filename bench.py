@@ -126,7 +126,7 @@ ITER_BYTES_2D_PFC = 48.3
 # kernel build on the same workload; the roofline's traffic is this times the
 # steps of one timed launch (the per-step traffic is flat once the working set
 # is resident).  Workloads without a capture report null.
-TRAFFIC_PER_STEP = {"fch2d_256_bdf2_fp32mixed": 2.808e6}
+TRAFFIC_PER_STEP = {"fch2d_256_bdf2_fp32mixed": 4.58e6}
 BATCH_TRAFFIC_PER_STEP = {"pfc2d_batch96_128_256_512_mp_fp32mixed": 10.40e9}
 ITER_BYTES_3D_PFC = 64.4
 
@@ -190,7 +190,8 @@ def bench_batch(torch, pagd, bw, steps, warm, plain_steps, bytes_per_eval, peak,
         "workload": bw.name, "members": m, "steps": steps, "ms": ms,
         "member_steps_per_s": m * steps / (ms / 1000.0), "batch_steps_per_s": steps / (ms / 1000.0),
         "iters_per_step": float(its.mean()), "max_iters": int(its.max()), "max_resid": float(res.max()),
-        "all_ok": bool(np.all(status == 0)), "gpu_launches": math.ceil(steps / 4096),
+        "all_ok": bool(np.all(status == 0)),
+        "gpu_launches": (len(members) if launch["sequential"] else 1) * math.ceil(steps / 4096),
         "scaling": "strong" if world > 1 else "weak",
         "schedule": schedule,
         "launch": {**launch, "strategy": "member after member through the single-instance kernel (every member "
@@ -200,9 +201,12 @@ def bench_batch(torch, pagd, bw, steps, warm, plain_steps, bytes_per_eval, peak,
         "plain_sample": f"each member alone, {plain_steps} steps after {warm} warm-up steps",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
+                     # DRAM bytes per launch: one member's steps when the members run one after
+                     # the other, else every member's
                      "traffic": (BATCH_TRAFFIC_PER_STEP[bw.name] * steps / math.ceil(steps / 4096)
+                                 / (len(bw.members) if launch["sequential"] else 1)
                                  if bw.name in BATCH_TRAFFIC_PER_STEP else None),
-                     "kernel": "pagd_batch_kernel<float>",
+                     "kernel": "pagd_kernel<float>" if launch["sequential"] else "pagd_batch_kernel<float>",
                      "bytes_model": f"{bytes_per_eval} B per point per residual evaluation of the "
                                     f"iteration passes x sum over members of points x evaluations "
                                     f"({nbytes / 1e9:.1f} GB); base evaluations not counted"},

@@ -235,10 +235,12 @@ pagd_status pagd_barrier_probe(pagd_solver* s, int count, double* us_per_phase);
  * device-wide; else the PAGD iterations of square 64^2, 128^2 and 256^2 grids
  * run inside one thread-block cluster of n/16 CTAs with their state in
  * distributed shared memory), whether the passes with FP64 lines run
- * CTA-cooperative units, and the dynamic shared memory per CTA.  Every output
- * nullable. */
+ * CTA-cooperative units, the dynamic shared memory per CTA, and whether the
+ * FP32 iteration passes stage their inputs through shared memory by
+ * asynchronous copies (PFC, FP32-mixed, square power-of-two grids; the same
+ * arithmetic either way).  Every output nullable. */
 pagd_status pagd_launch_info(const pagd_solver* s, int* grid, int* threads, int* cluster, int* coop,
-                             size_t* smem);
+                             size_t* smem, int* staged);
 
 const char* pagd_last_error(const pagd_solver* s);
 void pagd_destroy(pagd_solver* s);
@@ -292,11 +294,12 @@ pagd_status pagd_batch_run(pagd_batch* b, double dt, int nsteps, double tol, int
  * paper_2204_07247_gb300/autotune.py times candidate shapes and keeps the
  * fastest.  pagd_batch_launch_info: CTAs of the last launch (the planned grid
  * before the first), warps per CTA, dynamic shared memory per CTA, and
- * whether the last run went member after member (nullable outputs; see
- * pagd_batch_run). */
+ * whether the last run went member after member (see pagd_batch_run), and
+ * how many members' FP32 iteration passes stage their inputs through shared
+ * memory (see pagd_launch_info).  Nullable outputs. */
 pagd_status pagd_batch_set_shape(pagd_batch* b, int warps_per_cta, int ctas_per_sm);
 pagd_status pagd_batch_launch_info(const pagd_batch* b, int* grid, int* warps_per_cta, size_t* smem,
-                                   int* sequential);
+                                   int* sequential, int* staged);
 
 /* One step of every member in one launch, each from its own initial iterate
  * (the batched form of pagd_step_with_guess, with the same judging of each

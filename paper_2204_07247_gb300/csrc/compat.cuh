@@ -23,6 +23,7 @@ extern thread_local EmuDim3 threadIdx, blockIdx, blockDim, gridDim;
 
 struct alignas(8) float2 { float x, y; };
 struct alignas(16) double2 { double x, y; };
+struct alignas(16) float4 { float x, y, z, w; };
 
 inline void __syncthreads() {}
 inline void __threadfence() {}
@@ -41,6 +42,10 @@ inline double bits_dbl(unsigned long long u) { double d; std::memcpy(&d, &u, 8);
 #define PAGD_WARP 1
 template <class T> inline T warp_max(T v) { return v; }
 template <class T> inline T warp_sum(T v) { return v; }
+// asynchronous 16-byte global -> shared copies (the emulation copies at once)
+inline void cp_async16(void* dst, const void* src) { std::memcpy(dst, src, 16); }
+inline void cp_async_commit() {}
+template <int N> inline void cp_async_wait() {}
 
 #else  // CUDA
 #include <cuda_runtime.h>
@@ -62,5 +67,18 @@ template <class T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+// Asynchronous 16-byte copy global -> shared (cp.async, cached in L2 only):
+// both addresses 16-byte aligned.  Completion per thread in commit groups:
+// cp_async_wait<N>() returns once at most N of this thread's most recent
+// groups are still in flight; other threads' copies are visible after a
+// barrier that follows their waits.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 #endif

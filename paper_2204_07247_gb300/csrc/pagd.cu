@@ -55,7 +55,7 @@ struct pagd_solver {
     size_t ws_bytes;
     char* ws;
     // launch plan (grid_used: the grid of the last launch)
-    int grid, logtw, threads, coop, cl, grid_used;
+    int grid, logtw, threads, coop, cl, stage, grid_used;
     size_t smem, warp_bytes;
     // state
     int have_state, step, cur, trace, ref_valid;
@@ -152,6 +152,7 @@ static Params params_for(const pagd_solver* s, char* w) {
     P.inv_npts = 1.0 / (double)s->npts;
     P.warp_bytes = (long long)s->warp_bytes;
     P.coop = s->coop;
+    P.stage = s->stage;
     const double twopi = 6.283185307179586476925286766559;
     P.k0sq = (twopi / s->L[0]) * (twopi / s->L[0]);
     P.k1sq = (twopi / s->L[last]) * (twopi / s->L[last]);
@@ -327,6 +328,20 @@ static pagd_status run_program(pagd_solver* s, Params& P) {
     return st;
 }
 
+// The PFC FP32 iteration passes stage their inputs through shared memory
+// (row_pass_staged / col_pass_staged) when a warp slice of warp_bytes holds
+// the two staging slots; fixed line lengths only.  PAGD_STAGED=0 keeps the
+// register-staged passes (the same arithmetic, for comparison).
+static bool stage_fits(const pagd_solver* s, size_t warp_bytes) {
+    const int last = s->dim - 1;
+    const int nf = fixed_len(s->n[0], s->n[last]);
+    if (nf == 0 || s->tsize != 4 || s->model != M_PFC) return false;
+    if (const char* e = std::getenv("PAGD_STAGED"))
+        if (e[0] == '0' && e[1] == 0) return false;
+    const int k = k_iter(s->model);
+    return row_staged_smem(nf, k, 3) <= warp_bytes && col_staged_smem(nf, k, 3) <= warp_bytes;
+}
+
 // One warp per row unit / column / middle unit.  A CTA has as many warps (at
 // most 8) as their shared-memory slices allow (one in the emulation).  The
 // grid covers the largest unit count and is capped at the co-resident CTA
@@ -386,6 +401,7 @@ static void make_plan(pagd_solver* s) {
             if (nf == 256) s->coop = 0;
         }
     }
+    s->stage = stage_fits(s, s->warp_bytes) ? 1 : 0;
 }
 
 // ----------------------------------------------------------------- C ABI
@@ -1066,8 +1082,9 @@ pagd_status pagd_barrier_probe(pagd_solver* s, int count, double* us_per_phase) 
 // cluster-resident iterations (0: device-wide phases only), whether the
 // passes with FP64 lines run CTA-cooperative units, dynamic shared memory.
 pagd_status pagd_launch_info(const pagd_solver* s, int* grid, int* threads, int* cluster, int* coop,
-                             size_t* smem) {
+                             size_t* smem, int* staged) {
     if (!s) return PAGD_EINVAL;
+    if (staged) *staged = s->stage;
     if (grid) *grid = s->grid_used;
     if (threads) *threads = s->threads;
     if (cluster) *cluster = s->cl;
@@ -1284,8 +1301,12 @@ pagd_status pagd_batch_set_shape(pagd_batch* b, int warps_per_cta, int ctas_per_
 // before the first), warps per CTA, dynamic shared memory per CTA, and whether
 // the last run went member after member.
 pagd_status pagd_batch_launch_info(const pagd_batch* b, int* grid, int* warps_per_cta, size_t* smem,
-                                   int* sequential) {
+                                   int* sequential, int* staged) {
     if (!b) return PAGD_EINVAL;
+    if (staged) {
+        *staged = 0;
+        for (const pagd_solver* m : b->m) *staged += stage_fits(m, b->warp_bytes) ? 1 : 0;
+    }
     if (sequential) *sequential = b->sequential;
     if (grid) *grid = b->grid_used > 0 ? b->grid_used : b->grid;
     if (warps_per_cta) *warps_per_cta = b->wpb;
@@ -1320,6 +1341,7 @@ static pagd_status batch_chunk(pagd_batch* b, double dt, int nsteps, double tol,
         PI[i].warp_bytes = (long long)b->warp_bytes;
         PI[i].coop = 0;  // batch warps own their units: no CTA-wide barriers
         PI[i].cl = 0;    // and every phase of a batch is device-wide
+        PI[i].stage = stage_fits(s, b->warp_bytes) ? 1 : 0;
         PI[i].logtw = b->logtw;
         PI[i].guess = guesses ? guesses[i] : nullptr;  // the first step's initial iterate (nullable)
         st = dzero(s, PI[i].sc, sizeof(Scal));

@@ -96,7 +96,10 @@ struct Params {
     double cellvol;           // product of the spacings
     double eps, eta1, eta2, tau, M;
     double s;
-    int n_eta, accel, max_iter, max_recheck, theta_mode, pad0;
+    int n_eta, accel, max_iter, max_recheck, theta_mode;
+    // the PFC FP32 iteration passes stage their inputs by asynchronous copies
+    // (row_pass_staged / col_pass_staged; fixed line lengths)
+    int stage;
     double lam[16];      // (1 - eta_j sqrt s) / (1 + eta_j sqrt s)
     double tol, dt, dt_prev0;
     int step0, nsteps, cur0, nslots;  // nslots: norm / sum slots per step parity
@@ -747,6 +750,181 @@ __device__ void col_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
         }
         warp_sync();
     }
+}
+
+// ------------------------------------------- staged FP32 iteration passes
+//
+// The FP32 row and column passes of the PFC iterations with every input of a
+// unit staged in shared memory by asynchronous 16-byte copies (cp.async): a
+// warp issues all reads of its next unit (the half-spectrum pieces and the
+// pointwise state) before it transforms the current one, so that they are in
+// flight while it computes and hold no registers meanwhile.  Two staging slots
+// per warp alternate.  Selected on the host (Params::stage) where a warp's
+// slice of shared memory, sized for the FP64 phases, holds them; K fields per
+// line (PFC: 1), NS arrays of pointwise state.
+//
+// Row unit: rows r0, r0 + 1.  Slot = K x (N/2 + 1) 16-byte pieces (the two
+// rows' coefficients at k, adjacent in the [k][row] layout) + NS x 2 rows of
+// FP32 state.  Column unit: line k1.  Slot = K lines of the input spectrum +
+// NS lines of complex state, pitch N; the slot's spectrum lines are the first
+// transform buffer.
+
+__host__ __device__ constexpr size_t row_staged_smem(int n, int k, int ns) {
+    return 4 * (size_t)k * (size_t)(n + 2) * 8 + 2 * ((size_t)k * (size_t)(n / 2 + 1) * 16 + (size_t)ns * 2 * n * 4);
+}
+__host__ __device__ constexpr size_t col_staged_smem(int n, int k, int ns) {
+    return (size_t)k * n * 8 + 2 * (size_t)(k + ns) * n * 8;
+}
+
+template <int NF, int K, int NS, class Ap>
+__device__ void row_pass_staged(const Params& P, const Tw& tw, const float2* src, float2* dst,
+                                const float* const* sp, char* smem, Ap&& ap) {
+    constexpr int LOGN = ilog2c(NF), HALF = NF / 2, H1 = HALF + 1, PITCH = NF + 2, E = NF / kWarp;
+    constexpr int SLOT = K * H1 * 16 + NS * 2 * NF * 4;  // bytes
+    const int rows = P.rows;
+    const long long Hs = P.H;
+    const WarpCtx w = warp_ctx(P, smem);
+    float2* X0 = (float2*)w.mem;
+    float2* X1 = X0 + K * PITCH;
+    float2* Y0 = X1 + K * PITCH;
+    float2* Y1 = Y0 + K * PITCH;
+    char* slots = (char*)(Y1 + K * PITCH);
+    const float iscale = (float)P.inv_npts;
+    const URange ur = units_of(tw, rows / 2);
+    auto issue = [&](int u, int s) {
+        const int r0 = 2 * u;
+        float4* sq = (float4*)(slots + (size_t)s * SLOT);
+        float* st = (float*)(sq + K * H1);
+#pragma unroll
+        for (int f = 0; f < K; f++)
+            for (int k = w.lane; k < H1; k += kWarp)
+                cp_async16(sq + f * H1 + k, src + (size_t)f * Hs + (size_t)k * rows + r0);
+#pragma unroll
+        for (int a = 0; a < NS; a++)
+            for (int j = w.lane; j < NF / 2; j += kWarp)
+                cp_async16(st + a * 2 * NF + 4 * j, sp[a] + (size_t)r0 * NF + 4 * j);
+    };
+    if (ur.b < ur.e) issue(ur.b, 0);
+    cp_async_commit();
+    int s = 0;
+    for (int u = ur.b; u < ur.e; u += ur.s, s ^= 1) {
+        const int r0 = 2 * u;
+        if (u + ur.s < ur.e) issue(u + ur.s, s ^ 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        warp_sync();
+        const float4* sq = (const float4*)(slots + (size_t)s * SLOT);
+        const float* st = (const float*)(sq + K * H1);
+        // the two rows' half spectra -> one complex line (real part row r0)
+#pragma unroll
+        for (int f = 0; f < K; f++) {
+#pragma unroll
+            for (int i = 0; i < E; i++) {
+                const int x = w.lane + kWarp * i;
+                const int k = (x <= HALF) ? x : NF - x;
+                const float4 v = sq[f * H1 + k];
+                float2 A{v.x, v.y}, B{v.z, v.w};
+                if (x == 0 || x == HALF) { A.y = 0.f; B.y = 0.f; }
+                X0[f * PITCH + x] = (x <= HALF) ? float2{A.x - B.y, A.y + B.x} : float2{A.x + B.y, B.x - A.y};
+            }
+        }
+        const float2* Xr = fft_lines_fixed<+1, float, LOGN, K>(X0, X1, PITCH, K, tw.t32, tw.log, w.lane) ? X1 : X0;
+#pragma unroll
+        for (int i = 0; i < E; i++) {
+            const int x = w.lane + kWarp * i;
+#pragma unroll
+            for (int rr = 0; rr < 2; rr++) {
+                float sv[NS], in[K], out[K];
+#pragma unroll
+                for (int a = 0; a < NS; a++) sv[a] = st[a * 2 * NF + rr * NF + x];
+#pragma unroll
+                for (int f = 0; f < K; f++) {
+                    const float2 z = Xr[f * PITCH + x];
+                    in[f] = (rr ? z.y : z.x) * iscale;
+                }
+                ap((long long)(r0 + rr) * NF + x, r0 + rr, x, sv, in, out);
+#pragma unroll
+                for (int g = 0; g < K; g++) {
+                    if (rr) Y0[g * PITCH + x].y = out[g];
+                    else Y0[g * PITCH + x].x = out[g];
+                }
+            }
+        }
+        const float2* Yr = fft_lines_fixed<-1, float, LOGN, K>(Y0, Y1, PITCH, K, tw.t32, tw.log, w.lane) ? Y1 : Y0;
+#pragma unroll
+        for (int g = 0; g < K; g++) {
+            float4* d0 = (float4*)(dst + (size_t)g * Hs + r0);
+            const float2* zl = Yr + g * PITCH;
+            for (int k = w.lane; k <= HALF; k += kWarp) {
+                const float2 zk = zl[k], zn = zl[(NF - k) & (NF - 1)];
+                d0[(size_t)k * (rows / 2)] =
+                    float4{0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y), 0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x)};
+            }
+        }
+        warp_sync();
+    }
+    cp_async_wait<0>();
+    warp_sync();
+}
+
+template <int NF, int K, int NS, class Ap>
+__device__ void col_pass_staged(const Params& P, const Tw& tw, const float2* src, float2* dst,
+                                const float2* const* sc, char* smem, Ap&& ap) {
+    constexpr int LOGN = ilog2c(NF), E = NF / kWarp;
+    constexpr int SLOT = (K + NS) * NF * 8;  // bytes
+    const int ncols = P.ncols;
+    const long long Hs = P.H;
+    const WarpCtx w = warp_ctx(P, smem);
+    float2* B1 = (float2*)w.mem;
+    char* slots = (char*)(B1 + K * NF);
+    const URange ur = units_of(tw, ncols);
+    auto issue = [&](int k1, int s) {
+        float2* sl = (float2*)(slots + (size_t)s * SLOT);
+#pragma unroll
+        for (int f = 0; f < K; f++)
+            for (int j = w.lane; j < NF / 2; j += kWarp)
+                cp_async16(sl + f * NF + 2 * j, src + (size_t)f * Hs + (size_t)k1 * NF + 2 * j);
+#pragma unroll
+        for (int a = 0; a < NS; a++)
+            for (int j = w.lane; j < NF / 2; j += kWarp)
+                cp_async16(sl + (K + a) * NF + 2 * j, sc[a] + (size_t)k1 * NF + 2 * j);
+    };
+    if (ur.b < ur.e) issue(ur.b, 0);
+    cp_async_commit();
+    int s = 0;
+    for (int k1 = ur.b; k1 < ur.e; k1 += ur.s, s ^= 1) {
+        if (k1 + ur.s < ur.e) issue(k1 + ur.s, s ^ 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        warp_sync();
+        float2* b0 = (float2*)(slots + (size_t)s * SLOT);
+        const float2* st = b0 + K * NF;
+        const int r = fft_lines_fixed<-1, float, LOGN, K>(b0, B1, NF, K, tw.t32, tw.log, w.lane);
+        float2* Xr = r ? B1 : b0;
+        float2* Xi = r ? b0 : B1;
+#pragma unroll
+        for (int i = 0; i < E; i++) {
+            const int k0 = w.lane + kWarp * i;
+            float2 sv[NS], in[K], out[K];
+#pragma unroll
+            for (int a = 0; a < NS; a++) sv[a] = st[a * NF + k0];
+#pragma unroll
+            for (int f = 0; f < K; f++) in[f] = Xr[f * NF + k0];
+            ap(k1, k0, sv, in, out);
+#pragma unroll
+            for (int g = 0; g < K; g++) Xi[g * NF + k0] = out[g];
+        }
+        const float2* Yr = fft_lines_fixed<+1, float, LOGN, K>(Xi, Xr, NF, K, tw.t32, tw.log, w.lane) ? Xr : Xi;
+#pragma unroll
+        for (int g = 0; g < K; g++) {
+            float4* d = (float4*)(dst + (size_t)g * Hs + (size_t)k1 * NF);
+            const float4* y = (const float4*)(Yr + g * NF);
+            for (int j = w.lane; j < NF / 2; j += kWarp) d[j] = y[j];
+        }
+        warp_sync();
+    }
+    cp_async_wait<0>();
+    warp_sync();
 }
 
 // ------------------------------------------------ CTA-cooperative variants
@@ -1491,22 +1669,86 @@ __device__ PAGD_COLD void phase_EN(const Params& P, const Ctl& c, const Tw& tw, 
         });
 }
 
+// Constants of the iteration row pass at iteration it of the step.
+template <class T> struct RowK {
+    T lp, l, ts, tau, e2, eta1, eta2;
+};
+template <class T> __device__ __forceinline__ RowK<T> row_consts(const Params& P, const Ctl& c) {
+    const StepK& k = step_coeffs(P, c.step);
+    return RowK<T>{(T)lam_at(P, c.it - 1), (T)lam_at(P, c.it), (T)k.ts, (T)P.tau, (T)(P.eps * P.eps),
+                   (T)P.eta1,            (T)P.eta2};
+}
+
+// One point of the iteration row pass: delta_{i+1} from the direction
+// (Algorithm 2's update in the correction form) written over delta_{i-1}, the
+// max-norm and sum accumulators, the extrapolated iterate y and the nonlinear
+// term(s) at it (PFC: (b + y)^3 - b^3; FCH: the differences of F' and of the
+// second variation's nonlinear part).
+template <class T, class TI, bool PFC>
+__device__ __forceinline__ void row_point(const RowK<T>& q, T* dcur, long long p, T dp, T dpp, T b, T lb,
+                                          const TI* in, T* out, TI& amax, double& asum) {
+    const TI dd = in[0];
+    const T de = dp + q.lp * (dp - dpp) + q.ts * (T)dd;
+    dcur[p] = de;
+    const TI ad = fabs(dd);
+    amax = (ad > amax || ad != ad) ? ad : amax;
+    asum += (double)de;
+    const T y = de + q.l * (de - dp);
+    if (PFC) {
+        out[0] = y * ((T)3 * b * b + (T)3 * b * y + y * y);
+    } else {
+        const T tau = q.tau;
+        const T ly = (T)in[1];
+        const T f1b = dF1(b, tau), f2b = dF2(b, tau);
+        const T df1 = y * ((T)3 * b * b + (T)3 * b * y + y * y + tau * ((T)2 * b + y) - (T)1);
+        const T df2 = y * ((T)6 * b + (T)3 * y + (T)2 * tau);
+        const T f1n = f1b + df1, f2n = f2b + df2;
+        out[0] = df1;
+        out[1] = -q.e2 * (df2 * lb + (f2n - q.eta1) * ly) + df2 * f1n + (f2b - q.eta2) * df1;
+    }
+}
+
+// The PFC FP32 iteration row pass with staged inputs (row_pass_staged): its
+// own function, so that its registers are allocated apart from the general
+// pass's.
+template <int NF>
+__device__ __noinline__ void phase_R_staged(const Params& P, const Ctl& c, const Tw& tw, char* smem,
+                                            const float2* src) {
+    const RowK<float> q = row_consts<float>(P, c);
+    const int bank = c.step & 1;
+    float* dcur = (float*)P.DD[c.it & 1];
+    const float* sp[3] = {(const float*)P.DD[(c.it - 1) & 1], dcur, (const float*)P.VBt};
+    float amax = 0.f;
+    double asum = 0.0;
+    row_pass_staged<NF, 1, 3>(P, tw, src, (float2*)P.NB, sp, smem,
+                              [&](long long p, int, int, const float* sv, const float* in, float* out) {
+                                  row_point<float, float, true>(q, dcur, p, sv[0], sv[1], sv[2], 0.f, in, out,
+                                                                amax, asum);
+                              });
+    publish_max(&P.norms[(size_t)bank * P.nslots + c.ev], (double)amax);
+    publish_sum(&P.sums[(size_t)bank * P.nslots + c.ev], asum);
+}
+
 // Iteration row pass (R1 reads the FP64 base direction, RI the T one):
 // delta_it = ybar_{it-1} + theta_v s d_{it-1}; ||d_{it-1}||_inf; then the
 // nonlinear differences at ybar_it and their forward x-DFT.
 template <class TI, class T, int NF>
 __device__ PAGD_HOT void phase_R(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red,
                         const cx<TI>* src) {
-    const StepK& k = step_coeffs(P, c.step);
+    if constexpr (sizeof(TI) == 4 && sizeof(T) == 4 && (NF & (kNoCoop - 1)) != 0) {
+        if (P.stage && P.model == M_PFC) {
+            phase_R_staged<NF & (kNoCoop - 1)>(P, c, tw, smem, (const float2*)src);
+            return;
+        }
+    }
+    const RowK<T> q = row_consts<T>(P, c);
     const int it = c.it;
     const int bank = c.step & 1;
-    const T lp = (T)lam_at(P, it - 1), l = (T)lam_at(P, it), ts = (T)k.ts;
     T* dcur = (T*)P.DD[it & 1];
     const T* dprev = (const T*)P.DD[(it - 1) & 1];
     const T* vbt = (const T*)P.VBt;
     const T* lbt = (const T*)P.LBt;
     const int K = k_iter(P.model);
-    const T tau = (T)P.tau, e2 = (T)(P.eps * P.eps), eta1 = (T)P.eta1, eta2 = (T)P.eta2;
     TI amax = (TI)0;
     double asum = 0.0;
     const bool pfc = P.model == M_PFC;
@@ -1522,48 +1764,93 @@ __device__ PAGD_HOT void phase_R(const Params& P, const Ctl& c, const Tw& tw, ch
             return s;
         },
         [&](long long p, int, int, const St& s, const TI* in, T* out) {
-            const TI dd = in[0];
-            const T de = s.dp + lp * (s.dp - s.dpp) + ts * (T)dd;
-            dcur[p] = de;
-            const TI ad = fabs(dd);
-            amax = (ad > amax || ad != ad) ? ad : amax;
-            asum += (double)de;
-            const T y = de + l * (de - s.dp);
-            const T b = s.b;
-            if (pfc) {
-                out[0] = y * ((T)3 * b * b + (T)3 * b * y + y * y);
-            } else {
-                const T ly = (T)in[1];
-                const T f1b = dF1(b, tau), f2b = dF2(b, tau);
-                const T df1 = y * ((T)3 * b * b + (T)3 * b * y + y * y + tau * ((T)2 * b + y) - (T)1);
-                const T df2 = y * ((T)6 * b + (T)3 * y + (T)2 * tau);
-                const T f1n = f1b + df1, f2n = f2b + df2;
-                out[0] = df1;
-                out[1] = -e2 * (df2 * s.lb + (f2n - eta1) * ly) + df2 * f1n + (f2b - eta2) * df1;
-            }
+            if (pfc) row_point<T, TI, true>(q, dcur, p, s.dp, s.dpp, s.b, s.lb, in, out, amax, asum);
+            else row_point<T, TI, false>(q, dcur, p, s.dp, s.dpp, s.b, s.lb, in, out, amax, asum);
         });
     publish_max(&P.norms[(size_t)bank * P.nslots + c.ev], (double)amax);
     publish_sum(&P.sums[(size_t)bank * P.nslots + c.ev], asum);
 }
 
-// Iteration column pass: ybar_hat, spectral residual (Eq. obj:G' with the
-// zero mode removed), d_hat = r_hat / Lcal_hat (Algorithm 2), the spectral
-// state update, and the inverse y-DFT of d (and of Lap ybar_{it+1} for FCH).
+// Constants of the iteration column pass: the momentum factors, theta_v s, the
+// preconditioner's coefficients (averaged-Newton betas, Sec. 3.4.1) and the
+// linear part's in the iteration precision.
+template <class T> struct ColK {
+    T l, ln, ts, m2, b0, b2, b4, aim, c0, e2, e4;
+};
+template <class T> __device__ __forceinline__ ColK<T> col_consts(const Params& P, const Ctl& c) {
+    const StepK& k = step_coeffs(P, c.step);
+    const Beta B = betas(P, k, c.bsel);
+    const T e2 = (T)(P.eps * P.eps);
+    return ColK<T>{(T)lam_at(P, c.it), (T)lam_at(P, c.it + 1), (T)k.ts, (T)B.m2, (T)B.b0, (T)B.b2, (T)B.b4,
+                   (T)(k.Ai / P.M),   (T)(1.0 - P.eps),       e2,       e2 * e2};
+}
+
+// One wavenumber of the iteration column pass: ybar_hat, the spectral residual
+// (Eq. obj:G' with the zero mode removed), d_hat = r_hat / Lcal_hat (Algorithm
+// 2), the spectral state update written over the older state, and the outputs
+// to transform (d_hat; FCH also the Laplacian of ybar_{it+1}).
+template <class T, bool PFC>
+__device__ __forceinline__ void col_point(const Params& P, const ColK<T>& q, cx<T>* sprev, int k1, int k0, cx<T> sc,
+                                          cx<T> sp, cx<T> g0, const cx<T>* in, cx<T>* out) {
+    using C = cx<T>;
+    const long long idx = (long long)k1 * P.n0 + k0;
+    const T kap = kappa_t<T>(P, k1, k0);
+    const C yh = C{sc.x + q.l * (sc.x - sp.x), sc.y + q.l * (sc.y - sp.y)};
+    C d{(T)0, (T)0};
+    if (kap != (T)0) {
+        const T ik = (T)1 / kap;
+        const T il = (T)-1 / (q.m2 * ik + q.b0 + q.b2 * kap + q.b4 * kap * kap);
+        if (PFC) {
+            const T m = q.aim * ik + q.c0 - (T)2 * kap + kap * kap;
+            d.x = il * (g0.x + m * yh.x + in[0].x);
+            d.y = il * (g0.y + m * yh.y + in[0].y);
+        } else {
+            const T m = q.aim * ik + q.e4 * kap * kap;
+            const T e2k = q.e2 * kap;
+            d.x = il * (g0.x + m * yh.x + e2k * in[0].x + in[1].x);
+            d.y = il * (g0.y + m * yh.y + e2k * in[0].y + in[1].y);
+        }
+    }
+    const C sn = C{yh.x + q.ts * d.x, yh.y + q.ts * d.y};
+    sprev[idx] = sn;
+    out[0] = d;
+    if (!PFC) {
+        const T f = -kap;
+        out[1] = C{f * (sn.x + q.ln * (sn.x - sc.x)), f * (sn.y + q.ln * (sn.y - sc.y))};
+    }
+}
+
+// The PFC FP32 iteration column pass with staged inputs (col_pass_staged).
+template <int NF>
+__device__ __noinline__ void phase_CI_staged(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
+    const ColK<float> q = col_consts<float>(P, c);
+    float2* sprev = (float2*)P.SS[(c.it - 1) & 1];
+    const float2* sc3[3] = {(const float2*)P.SS[c.it & 1], sprev, (const float2*)P.C0};
+    col_pass_staged<NF, 1, 3>(P, tw, csrcT<float>(P), cdstT<float>(P), sc3, smem,
+                              [&](int k1, int k0, const float2* sv, const float2* in, float2* out) {
+                                  col_point<float, true>(P, q, sprev, k1, k0, sv[0], sv[1], sv[2], in, out);
+                              });
+}
+
+// Iteration column pass: ybar_hat, spectral residual, preconditioned
+// direction and spectral state update (col_point), and the inverse y-DFT of d
+// (and of Lap ybar_{it+1} for FCH).
 template <class T, int NF>
 __device__ PAGD_HOT void phase_CI(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     using C = cx<T>;
-    const StepK& k = step_coeffs(P, c.step);
-    const Beta B = betas(P, k, c.bsel);
+    if constexpr (sizeof(T) == 4 && (NF & (kNoCoop - 1)) != 0) {
+        if (P.stage && P.model == M_PFC) {
+            phase_CI_staged<NF & (kNoCoop - 1)>(P, c, tw, smem);
+            return;
+        }
+    }
+    const ColK<T> q = col_consts<T>(P, c);
     const int it = c.it;
-    const T l = (T)lam_at(P, it), ln = (T)lam_at(P, it + 1), ts = (T)k.ts;
     const C* scur = (const C*)P.SS[it & 1];
     C* sprev = (C*)P.SS[(it - 1) & 1];
     const C* C0 = (const C*)P.C0;
     const int K = k_iter(P.model);
     const bool pfc = P.model == M_PFC;
-    // spectral factors in the iteration precision
-    const T m2 = (T)B.m2, b0 = (T)B.b0, b2 = (T)B.b2, b4 = (T)B.b4;
-    const T aim = (T)(k.Ai / P.M), c0 = (T)(1.0 - P.eps), e2 = (T)(P.eps * P.eps), e4 = e2 * e2;
     struct St { C sc, sp, g0; };
     colp<T, NF>(
         P, tw, K, K, csrcT<T>(P), cdstT<T>(P), smem,
@@ -1572,33 +1859,8 @@ __device__ PAGD_HOT void phase_CI(const Params& P, const Ctl& c, const Tw& tw, c
             return St{scur[idx], sprev[idx], C0[idx]};
         },
         [&](int k1, int k0, const St& s, const C* in, C* out) {
-            const long long idx = (long long)k1 * P.n0 + k0;
-            const T kap = kappa_t<T>(P, k1, k0);
-            const C sc = s.sc, sp = s.sp;
-            const C yh = C{sc.x + l * (sc.x - sp.x), sc.y + l * (sc.y - sp.y)};
-            C d{(T)0, (T)0};
-            if (kap != (T)0) {
-                const C g0 = s.g0;
-                const T ik = (T)1 / kap;
-                const T il = (T)-1 / (m2 * ik + b0 + b2 * kap + b4 * kap * kap);
-                if (pfc) {
-                    const T m = aim * ik + c0 - (T)2 * kap + kap * kap;
-                    d.x = il * (g0.x + m * yh.x + in[0].x);
-                    d.y = il * (g0.y + m * yh.y + in[0].y);
-                } else {
-                    const T m = aim * ik + e4 * kap * kap;
-                    const T e2k = e2 * kap;
-                    d.x = il * (g0.x + m * yh.x + e2k * in[0].x + in[1].x);
-                    d.y = il * (g0.y + m * yh.y + e2k * in[0].y + in[1].y);
-                }
-            }
-            const C sn = C{yh.x + ts * d.x, yh.y + ts * d.y};
-            sprev[idx] = sn;
-            out[0] = d;
-            if (!pfc) {
-                const T f = -kap;
-                out[1] = C{f * (sn.x + ln * (sn.x - sc.x)), f * (sn.y + ln * (sn.y - sc.y))};
-            }
+            if (pfc) col_point<T, true>(P, q, sprev, k1, k0, s.sc, s.sp, s.g0, in, out);
+            else col_point<T, false>(P, q, sprev, k1, k0, s.sc, s.sp, s.g0, in, out);
         });
 }
 

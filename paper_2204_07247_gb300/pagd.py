@@ -75,7 +75,7 @@ def _declare(lib):
         "pagd_get_state": [P, P, P, IP],
         "pagd_step_static": [P, P, P, i, d, d, d, P, IP, D],
         "pagd_barrier_probe": [P, i, D],
-        "pagd_launch_info": [P, IP, IP, IP, IP, ctypes.POINTER(ctypes.c_size_t)],
+        "pagd_launch_info": [P, IP, IP, IP, IP, ctypes.POINTER(ctypes.c_size_t), IP],
         "pagd_set_trace": [P, i],
         "pagd_get_trace": [P, IP, D, i, IP],
         "pagd_last_error": [P],
@@ -86,7 +86,7 @@ def _declare(lib):
         "pagd_batch_run": [P, d, i, d, IP, D, IP],
         "pagd_batch_set_shape": [P, i, i],
         "pagd_batch_step_with_guess": [P, ctypes.POINTER(P), d, d, IP, D, IP, IP],
-        "pagd_batch_launch_info": [P, IP, IP, ctypes.POINTER(ctypes.c_size_t), IP],
+        "pagd_batch_launch_info": [P, IP, IP, ctypes.POINTER(ctypes.c_size_t), IP, IP],
         "pagd_batch_last_error": [P],
         "pagd_batch_destroy": [P],
     }
@@ -325,13 +325,14 @@ class Solver:
         return it.value, r.value
 
     def launch_info(self):
-        """{grid (of the last launch), threads, cluster, coop, smem} of the
-        solver's persistent kernel."""
-        g, t, c, co = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        """{grid (of the last launch), threads, cluster, coop, smem, staged} of
+        the solver's persistent kernel."""
+        g, t, c, co, sg = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         sm = ctypes.c_size_t()
         self._check(self.lib.pagd_launch_info(self._h, ctypes.byref(g), ctypes.byref(t), ctypes.byref(c),
-                                              ctypes.byref(co), ctypes.byref(sm)), "launch_info")
-        return {"grid": g.value, "threads": t.value, "cluster": c.value, "coop": co.value, "smem": sm.value}
+                                              ctypes.byref(co), ctypes.byref(sm), ctypes.byref(sg)), "launch_info")
+        return {"grid": g.value, "threads": t.value, "cluster": c.value, "coop": co.value, "smem": sm.value,
+                "staged": bool(sg.value)}
 
     def barrier_probe(self, count=2000):
         """Device time per empty phase of the persistent kernel (microseconds):
@@ -440,11 +441,12 @@ class Batch:
         return self.lib.pagd_batch_set_shape(self._h, int(warps_per_cta), int(ctas_per_sm)) == 0
 
     def launch_info(self):
-        g, w, q = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        g, w, q, sg = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         sm = ctypes.c_size_t()
         self._check(self.lib.pagd_batch_launch_info(self._h, ctypes.byref(g), ctypes.byref(w), ctypes.byref(sm),
-                                                    ctypes.byref(q)), "batch_launch_info")
-        return {"grid": g.value, "warps_per_cta": w.value, "smem": sm.value, "sequential": bool(q.value)}
+                                                    ctypes.byref(q), ctypes.byref(sg)), "batch_launch_info")
+        return {"grid": g.value, "warps_per_cta": w.value, "smem": sm.value, "sequential": bool(q.value),
+                "staged_members": sg.value}
 
     def close(self):
         if self._h:
