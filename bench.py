@@ -127,7 +127,11 @@ ITER_BYTES_2D_PFC = 48.3
 # steps of one timed launch (the per-step traffic is flat once the working set
 # is resident).  Workloads without a capture report null.
 TRAFFIC_PER_STEP = {"fch2d_256_bdf2_fp32mixed": 4.58e6}
-BATCH_TRAFFIC_PER_STEP = {"pfc2d_batch96_128_256_512_mp_fp32mixed": 10.40e9}
+# per batch step (all members).  The 3D figure is the capture of one 128^3
+# member (2 steps) scaled by points to 256^3, for two members: a lower bound,
+# as part of the 128^3 working set stays in L2
+BATCH_TRAFFIC_PER_STEP = {"pfc2d_batch96_128_256_512_mp_fp32mixed": 10.42e9,
+                          "pfc3d_256_bdf2_fp32mixed_x2": 2 * 8 * 0.9835e9}
 ITER_BYTES_3D_PFC = 64.4
 
 
@@ -570,13 +574,43 @@ def profile_form(torch, pagd, form, w, steps, warm, trace, grid=None):
     return 0
 
 
+# algorithmic HBM bytes per grid point of one FP32 iteration pass (PFC): the
+# row and column passes as in ITER_BYTES_2D_PFC, each middle pass reading and
+# writing one half spectrum
+PASS_BYTES_PFC = {"RI": 24.1, "CI": 24.2, "MF": 8.05, "MI": 8.05}
+
+
+def probe_pass(torch, pagd, w, which, count, warm, grid=None):
+    """One iteration pass of w repeated `count` times in one launch (after a
+    warm-up launch of `warm` steps): device time per pass with and without the
+    barrier, and the pass's algorithmic bytes over that time."""
+    if grid and len(w.n) == 3:
+        w = dataclasses.replace(w, n=(grid,) * 3, L=tuple(l * grid / n for l, n in zip(w.L, w.n)))
+    S = pagd.solver_for(w)
+    S.set_state(torch.from_numpy(w.u0(w.seeds[0])).cuda())
+    S.run(w.dt, warm, w.tol)
+    us = S.pass_probe(which, count)
+    bar = S.barrier_probe(count)
+    npts = int(np.prod(w.n))
+    out = {"workload": w.name, "grid": list(w.n), "pass": which, "count": count, "us_per_pass": us,
+           "barrier_us": bar, "launch": S.launch_info()}
+    if w.model == "pfc" and w.precision == "fp32_mixed":
+        nbytes = PASS_BYTES_PFC[which] * npts
+        out["bytes_per_pass"] = nbytes
+        out["GBps_with_barrier"] = nbytes / (us * 1e-6) / 1e9
+        out["GBps_without_barrier"] = nbytes / ((us - bar) * 1e-6) / 1e9
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=I.FCH256.name, choices=sorted(I.WORKLOADS))
+    ap.add_argument("--workload", default=I.FCH256.name,
+                    choices=sorted(I.WORKLOADS) + [m.name for m in I.PFC_BATCH96.members])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and 3D lines")
     ap.add_argument("--no-studies", action="store_true", help="skip the PGD and cost-to-accuracy studies")
@@ -584,9 +618,12 @@ def main():
                     "a form, then exit (the launch for ncu -s 1 -c 1)")
     ap.add_argument("--trace", choices=FORMS, help="print the phase trace of --steps steps of a form")
     ap.add_argument("--profile-grid", type=int, default=None,
-                    help="with --profile / --trace pfc3d: the 3D members at this grid^3, same spacing")
+                    help="with --profile / --trace pfc3d / --probe-pass: 3D members at this grid^3, same spacing")
+    ap.add_argument("--probe-pass", choices=("RI", "CI", "MF", "MI"),
+                    help="time one iteration pass of --workload run on its own (--steps repetitions in one "
+                         "launch, after --warmup steps; the launch for ncu -s 1 -c 1), then exit")
     args = ap.parse_args()
-    w = I.WORKLOADS[args.workload]
+    w = I.WORKLOADS.get(args.workload) or {m.name: m for m in I.PFC_BATCH96.members}[args.workload]
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -608,6 +645,8 @@ def main():
     K = max(1, args.steps)
     if args.profile or args.trace:
         return profile_form(torch, pagd, args.profile or args.trace, w, K, W, bool(args.trace), args.profile_grid)
+    if args.probe_pass:
+        return probe_pass(torch, pagd, w, args.probe_pass, K, W, args.profile_grid)
     S = pagd.solver_for(w)
     u0 = torch.from_numpy(w.u0(1 + rank)).cuda()
     S.set_state(u0)

@@ -229,6 +229,23 @@ pagd_status pagd_get_trace(pagd_solver* s, int* phase, double* t_us, int cap, in
  * workspace; leaves the solver state alone.  Synchronises the stream. */
 pagd_status pagd_barrier_probe(pagd_solver* s, int count, double* us_per_phase);
 
+/* Iteration pass probe (instrumentation, not in the paper): one launch of the
+ * solver's persistent kernel that repeats one pass of a PAGD iteration `count`
+ * (1..1000000) times, each ended by the device-wide barrier, so that a
+ * profiler capturing that launch sees the pass alone.  pass: 0 the row pass
+ * (RI: correction update, nonlinear term, forward transforms along the last
+ * axis), 1 the column pass (CI: spectral residual, preconditioner, state
+ * update, inverse transforms along the first axis), 2 / 3 the forward /
+ * inverse middle pass (MF / MI, 3D only).  The pass runs as iteration 1 of
+ * the last completed step, on the iteration buffers that step left (their
+ * contents are overwritten; u^n, u^{n-1} and the step count are kept, and
+ * the next pagd_run starts from them as usual).  *us_per_pass: the launch's
+ * device time / count, barrier included (pagd_barrier_probe gives the
+ * barrier alone).  PAGD_EINVAL for a bad argument or a middle pass in 2D,
+ * PAGD_ESTATE without a completed step of BDF2 or MP.  Synchronises the
+ * stream. */
+pagd_status pagd_pass_probe(pagd_solver* s, int pass, int count, double* us_per_pass);
+
 /* Launch plan of the solver's persistent kernel (instrumentation, not in the
  * paper): CTAs of the last launch (0 before the first), threads per CTA, the
  * cluster size of the cluster-resident iterations (0: every phase is

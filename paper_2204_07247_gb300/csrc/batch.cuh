@@ -9,9 +9,11 @@
 // work item per instance (its current phase), separated from the next by the
 // device-wide barrier.  The work of a global phase is laid out on a cost axis:
 // instance i covers [G_i, G_i + units_i * q_i), q_i the points a unit touches
-// (2 n1 for a row unit of two rows, n0 for a column), and warp w of the grid
-// takes the slice [C_w, C_{w+1}), C_w = floor(total * w / NW), so every warp
-// gets about the same number of points whatever the mix of sizes.  Each warp
+// (2 n1 for a row unit of two rows, n0 for a column) times the relative cost
+// per point of the instance's current phase (phase_weight: an FP64 base pass
+// costs several FP32 iteration passes), and warp w of the grid takes the
+// slice [C_w, C_{w+1}), C_w = floor(total * w / NW), so every warp gets about
+// the same time of work whatever the mix of sizes and phases.  Each warp
 // runs the members on its own slice; reductions are per warp (lane 0 publishes
 // with an atomic), so warps never wait for each other inside a global phase.
 #pragma once
@@ -72,7 +74,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pagd_batch_kernel(BatchParams 
                 const int i = i0 + (int)threadIdx.x;
                 long long v = 0;
                 if (i < B.count && ctl[i].ph != PH_DONE) {
-                    v = (long long)phase_units(B.PI[i], ctl[i].ph) * unit_cost(B.PI[i], ctl[i].ph);
+                    v = (long long)phase_units(B.PI[i], ctl[i].ph) * weighted_unit_cost(B.PI[i], ctl[i]);
                     mask |= 1u << ctl[i].ph;
                 }
 #pragma unroll
@@ -106,7 +108,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) pagd_batch_kernel(BatchParams 
             if (cost == 0) continue;
             const Params& P = B.PI[i];
             Tw t{t64, t32, B.logtw, 0, 0, 0, 0};
-            batch_split(t, gw, nw, total, G[i], cost, phase_units(P, ctl[i].ph), unit_cost(P, ctl[i].ph));
+            batch_split(t, gw, nw, total, G[i], cost, phase_units(P, ctl[i].ph), (int)weighted_unit_cost(P, ctl[i]));
             batch_exec<T>(P, ctl[i], t, wsm, red);
         }
         if (!grid_barrier(B.sc, gen)) break;

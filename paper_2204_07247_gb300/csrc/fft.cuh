@@ -150,9 +150,19 @@ namespace pagd {
 // Compile-time line length: the radix sequence, the per-lane butterfly loops and
 // the line loop unroll, so the loads of all lines a warp owns are in flight
 // together.  Lines l < nl (nl <= MAXL) sit at `pitch` apart in each buffer.
+//
+// Padded layout (PAD): point i of a line at i + i / 16, one slot of gap after
+// every 16 points.  The first stages of a Stockham transform store at a stride
+// of R (and then R^2) points; unpadded, the 32 lanes of a store then share
+// 2 (or 4) of the 16 eight-byte bank pairs, a 16-way (4-way) conflict.  With
+// the gap they spread over all 16 pairs.  A padded line of n points needs
+// n + n / 16 slots.
 
-template <int R, int S, class T, int LOGN, int LOGNS, int MAXL>
-__device__ __forceinline__ void stage_fixed(const cx<T>* src, cx<T>* dst, int pitch, int nl,
+template <bool P> __host__ __device__ __forceinline__ int pix(int i) { return P ? i + (i >> 4) : i; }
+__host__ __device__ constexpr int padded_len(int n) { return n + n / 16; }
+
+template <int R, int S, class T, int LOGN, int LOGNS, int MAXL, bool PS = false, bool PD = false>
+__device__ __forceinline__ void stage_fixed(const cx<T>* src, cx<T>* dst, int pitch_s, int pitch_d, int nl,
                                             const cx<T>* tw, int logTw, int lane) {
     using C = cx<T>;
     constexpr int LR = (R == 2) ? 1 : (R == 4) ? 2 : 3;
@@ -177,45 +187,68 @@ __device__ __forceinline__ void stage_fixed(const cx<T>* src, cx<T>* dst, int pi
 #pragma unroll
         for (int l = 0; l < MAXL; l++) {
             if (l < nl) {
-                const C* s = src + l * pitch;
-                C* d = dst + l * pitch;
+                const C* s = src + l * pitch_s;
+                C* d = dst + l * pitch_d;
                 C v[R];
 #pragma unroll
-                for (int r = 0; r < R; r++) v[r] = s[j + r * NB];
+                for (int r = 0; r < R; r++) v[r] = s[pix<PS>(j + r * NB)];
                 if (LOGNS > 0) {
 #pragma unroll
                     for (int r = 1; r < R; r++) v[r] = cmul(v[r], w[r]);
                 }
                 dftR<R, S>(v);
 #pragma unroll
-                for (int r = 0; r < R; r++) d[idxD + r * NS] = v[r];
+                for (int r = 0; r < R; r++) d[pix<PD>(idxD + r * NS)] = v[r];
             }
         }
     }
 }
 
-template <int S, class T, int LOGN, int LOGNS, int MAXL>
+// radix of the stage that starts at LOGNS: 8 while at least 3 levels remain
+// (4 when exactly 4 do), then 4, then 2
+__host__ __device__ constexpr int stage_radix(int logn, int logns) {
+    return (logn - logns >= 3 && logn - logns != 4) ? 8 : (logn - logns >= 2 ? 4 : 2);
+}
+__host__ __device__ constexpr int radix_log(int r) { return r == 2 ? 1 : (r == 4 ? 2 : 3); }
+
+template <int S, class T, int LOGN, int LOGNS, int MAXL, bool PAD = false>
 struct FixedStages {
     static __device__ __forceinline__ int run(cx<T>* b0, cx<T>* b1, int pitch, int nl, const cx<T>* tw,
                                               int logTw, int lane, int cur) {
         if constexpr (LOGNS >= LOGN) {
             return cur;
         } else {
-            constexpr int REM = LOGN - LOGNS;
-            constexpr int R = (REM >= 3 && REM != 4) ? 8 : (REM >= 2 ? 4 : 2);
-            constexpr int LR = (R == 2) ? 1 : (R == 4) ? 2 : 3;
+            constexpr int R = stage_radix(LOGN, LOGNS);
             warp_sync();
-            stage_fixed<R, S, T, LOGN, LOGNS, MAXL>(cur ? b1 : b0, cur ? b0 : b1, pitch, nl, tw, logTw, lane);
-            return FixedStages<S, T, LOGN, LOGNS + LR, MAXL>::run(b0, b1, pitch, nl, tw, logTw, lane, cur ^ 1);
+            stage_fixed<R, S, T, LOGN, LOGNS, MAXL, PAD, PAD>(cur ? b1 : b0, cur ? b0 : b1, pitch, pitch, nl, tw,
+                                                             logTw, lane);
+            return FixedStages<S, T, LOGN, LOGNS + radix_log(R), MAXL, PAD>::run(b0, b1, pitch, nl, tw, logTw, lane,
+                                                                                cur ^ 1);
         }
     }
 };
 
-// nl lines of length 1 << LOGN in b0 -> result in b0 (returns 0) or b1 (1)
-template <int S, class T, int LOGN, int MAXL>
+// nl lines of length 1 << LOGN in b0 -> result in b0 (returns 0) or b1 (1);
+// PAD: both buffers in the padded layout
+template <int S, class T, int LOGN, int MAXL, bool PAD = false>
 __device__ __forceinline__ int fft_lines_fixed(cx<T>* b0, cx<T>* b1, int pitch, int nl, const cx<T>* tw,
                                                int logTw, int lane) {
-    const int r = FixedStages<S, T, LOGN, 0, MAXL>::run(b0, b1, pitch, nl, tw, logTw, lane, 0);
+    const int r = FixedStages<S, T, LOGN, 0, MAXL, PAD>::run(b0, b1, pitch, nl, tw, logTw, lane, 0);
+    warp_sync();
+    return r;
+}
+
+// The same transform from an unpadded input `in` (lines pitch_in apart, left
+// unchanged) into the padded buffers b0 / b1 (lines pitch apart): the first
+// stage reads `in` and writes b0.  Returns 0 / 1, the buffer of the result.
+template <int S, class T, int LOGN, int MAXL>
+__device__ __forceinline__ int fft_lines_fixed_into_padded(const cx<T>* in, int pitch_in, cx<T>* b0, cx<T>* b1,
+                                                           int pitch, int nl, const cx<T>* tw, int logTw,
+                                                           int lane) {
+    constexpr int R = stage_radix(LOGN, 0);
+    warp_sync();
+    stage_fixed<R, S, T, LOGN, 0, MAXL, false, true>(in, b0, pitch_in, pitch, nl, tw, logTw, lane);
+    const int r = FixedStages<S, T, LOGN, radix_log(R), MAXL, true>::run(b0, b1, pitch, nl, tw, logTw, lane, 0);
     warp_sync();
     return r;
 }

@@ -55,7 +55,7 @@ struct pagd_solver {
     size_t ws_bytes;
     char* ws;
     // launch plan (grid_used: the grid of the last launch)
-    int grid, logtw, threads, coop, cl, stage, grid_used;
+    int grid, logtw, threads, coop, cl, stage, coop32, grid_used;
     size_t smem, warp_bytes;
     // state
     int have_state, step, cur, trace, ref_valid;
@@ -153,6 +153,7 @@ static Params params_for(const pagd_solver* s, char* w) {
     P.warp_bytes = (long long)s->warp_bytes;
     P.coop = s->coop;
     P.stage = s->stage;
+    P.coop32 = s->coop32;
     const double twopi = 6.283185307179586476925286766559;
     P.k0sq = (twopi / s->L[0]) * (twopi / s->L[0]);
     P.k1sq = (twopi / s->L[last]) * (twopi / s->L[last]);
@@ -339,6 +340,8 @@ static bool stage_fits(const pagd_solver* s, size_t warp_bytes) {
     if (const char* e = std::getenv("PAGD_STAGED"))
         if (e[0] == '0' && e[1] == 0) return false;
     const int k = k_iter(s->model);
+    // the middle passes of a cubic grid stage too (mid_pass_staged)
+    if (s->dim == 3 && s->n[1] == nf && mid_staged_smem(nf) > warp_bytes) return false;
     return row_staged_smem(nf, k, 3) <= warp_bytes && col_staged_smem(nf, k, 3) <= warp_bytes;
 }
 
@@ -402,6 +405,16 @@ static void make_plan(pagd_solver* s) {
         }
     }
     s->stage = stage_fits(s, s->warp_bytes) ? 1 : 0;
+    // FP32 iteration passes with CTA-cooperative units (unstaged FP32 passes
+    // of fixed line length): opt-in with PAGD_COOP32=1.  Measured slower on
+    // FCH 256^2 (128 row pairs on 152 SMs), where the FP64 passes gain from
+    // them: 382.7 against 359.3 us per step, the column pass 13.4 against
+    // 10.3 us.
+    s->coop32 = 0;
+    if (const char* e = std::getenv("PAGD_COOP32")) {
+        if (e[0] == '1' && e[1] == 0)
+            s->coop32 = (fixed_len(s->n[0], s->n[last]) != 0 && s->tsize == 4 && !s->stage && !s->cl) ? 1 : 0;
+    }
 }
 
 // ----------------------------------------------------------------- C ABI
@@ -1034,13 +1047,8 @@ pagd_status pagd_step_static(pagd_solver* s, const double* un_dev, const double*
 // solver's persistent kernel with its launch plan that runs `count` empty
 // phases, each ended by the device-wide barrier; *us_per_phase receives the
 // launch's device time / count (CUDA events on the solver's stream).
-pagd_status pagd_barrier_probe(pagd_solver* s, int count, double* us_per_phase) {
-    if (!s || count < 1 || count > 1000000 || !us_per_phase) return PAGD_EINVAL;
-    if (!s->ws) return fail(s, PAGD_ESTATE, "no workspace");
-    Params P = base_params(s);
-    P.prog = PROG_BARRIER;
-    P.nsteps = count;
-    P.trace = nullptr;
+// Device time per phase of one launch of a probe program (P.nsteps phases).
+static pagd_status timed_probe(pagd_solver* s, Params& P, double* us_per_phase) {
 #ifdef PAGD_EMU
     pagd_status st = run_program(s, P);
     *us_per_phase = 0.0;
@@ -1066,15 +1074,40 @@ pagd_status pagd_barrier_probe(pagd_solver* s, int count, double* us_per_phase) 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != PAGD_OK) return st;
-    if (e != cudaSuccess) return cuda_fail(s, e, "barrier probe timing");
+    if (e != cudaSuccess) return cuda_fail(s, e, "probe timing");
     Scal sc;
     st = dcopy(s, &sc, P.sc, sizeof(Scal));
     if (st == PAGD_OK) st = dsync(s);
     if (st != PAGD_OK) return st;
     if (sc.bar_error) return fail(s, PAGD_ETIMEOUT, "device barrier timed out");
-    *us_per_phase = 1000.0 * (double)ms / (double)count;
+    *us_per_phase = 1000.0 * (double)ms / (double)P.nsteps;
     return PAGD_OK;
 #endif
+}
+
+pagd_status pagd_barrier_probe(pagd_solver* s, int count, double* us_per_phase) {
+    if (!s || count < 1 || count > 1000000 || !us_per_phase) return PAGD_EINVAL;
+    if (!s->ws) return fail(s, PAGD_ESTATE, "no workspace");
+    Params P = base_params(s);
+    P.prog = PROG_BARRIER;
+    P.nsteps = count;
+    P.trace = nullptr;
+    return timed_probe(s, P, us_per_phase);
+}
+
+pagd_status pagd_pass_probe(pagd_solver* s, int pass, int count, double* us_per_pass) {
+    if (!s || pass < 0 || pass > 3 || count < 1 || count > 1000000 || !us_per_pass) return PAGD_EINVAL;
+    if (!s->ws) return fail(s, PAGD_ESTATE, "no workspace");
+    if (pass >= 2 && s->dim != 3) return fail(s, PAGD_EINVAL, "middle passes exist in 3D only");
+    if (s->step < 1 || s->scheme == PAGD_LBDF2 || s->scheme == PAGD_LMP)
+        return fail(s, PAGD_ESTATE, "the pass probe needs a completed step of an implicit scheme");
+    static const int kPass[4] = {PH_RI, PH_CI, PH_MF, PH_MI};
+    Params P = run_params(s, nullptr, s->dt_prev, count, 0.0);
+    P.prog = PROG_PASS;
+    P.pass = kPass[pass];
+    P.cl = 0;
+    P.trace = nullptr;
+    return timed_probe(s, P, us_per_pass);
 }
 
 // Launch plan of the solver's persistent kernel (instrumentation): CTAs of
@@ -1186,7 +1219,7 @@ template <class T> static pagd_status batch_launch(pagd_batch* b, const BatchPar
         for (int i = 0; i < B.count; i++)
             G[i + 1] = G[i] + (ctl[i].ph == PH_DONE ? 0
                                                     : (long long)phase_units(B.PI[i], ctl[i].ph) *
-                                                          unit_cost(B.PI[i], ctl[i].ph));
+                                                          weighted_unit_cost(B.PI[i], ctl[i]));
         const long long total = G[B.count];
         if (total == 0) break;
         for (int blk = 0; blk < b->grid; blk++) {
@@ -1200,7 +1233,7 @@ template <class T> static pagd_status batch_launch(pagd_batch* b, const BatchPar
                     const Params& P = B.PI[i];
                     Tw t{t64, t32, B.logtw, 0, 0, 0, 0};
                     batch_split(t, gw, nw, total, G[i], G[i + 1] - G[i], phase_units(P, ctl[i].ph),
-                                unit_cost(P, ctl[i].ph));
+                                (int)weighted_unit_cost(P, ctl[i]));
                     batch_exec_host<T>(P, ctl[i], t, wsm, red);
                 }
             }
@@ -1340,6 +1373,7 @@ static pagd_status batch_chunk(pagd_batch* b, double dt, int nsteps, double tol,
         PI[i].trace = nullptr;
         PI[i].warp_bytes = (long long)b->warp_bytes;
         PI[i].coop = 0;  // batch warps own their units: no CTA-wide barriers
+        PI[i].coop32 = 0;
         PI[i].cl = 0;    // and every phase of a batch is device-wide
         PI[i].stage = stage_fits(s, b->warp_bytes) ? 1 : 0;
         PI[i].logtw = b->logtw;

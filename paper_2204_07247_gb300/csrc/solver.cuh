@@ -37,7 +37,7 @@ enum { M_PFC = 0, M_FCH = 1 };
 enum { S_BDF2 = 0, S_MP = 1, S_LBDF2 = 2, S_LMP = 3 };
 enum { P_FP64 = 0, P_MIXED = 1 };
 enum { PROG_RUN = 0, PROG_FFT_FWD = 1, PROG_FFT_INV = 2, PROG_ENERGY = 3, PROG_MASS = 4,
-       PROG_IMEX = 5, PROG_RHS = 6, PROG_EST = 7, PROG_BARRIER = 8 };
+       PROG_IMEX = 5, PROG_RHS = 6, PROG_EST = 7, PROG_BARRIER = 8, PROG_PASS = 9 };
 enum { ST_OK = 0, ST_EINVAL = 1, ST_ENOMEM = 2, ST_ECUDA = 3, ST_ENOCONV = 4, ST_EPRECOND = 5,
        ST_ENAN = 6, ST_ESTATE = 7, ST_ETIMEOUT = 8 };
 enum { FLAG_PRECOND = 1 };
@@ -100,6 +100,11 @@ struct Params {
     // the PFC FP32 iteration passes stage their inputs by asynchronous copies
     // (row_pass_staged / col_pass_staged; fixed line lengths)
     int stage;
+    // PROG_PASS: the iteration pass it repeats (PH_RI, PH_CI, PH_MF, PH_MI)
+    int pass;
+    // the FP32 iteration passes run CTA-cooperative units (phase_R_coop /
+    // phase_CI_coop; opt-in, single-instance launches, unstaged passes)
+    int coop32;
     double lam[16];      // (1 - eta_j sqrt s) / (1 + eta_j sqrt s)
     double tol, dt, dt_prev0;
     int step0, nsteps, cur0, nslots;  // nslots: norm / sum slots per step parity
@@ -759,36 +764,37 @@ __device__ void col_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
 // warp issues all reads of its next unit (the half-spectrum pieces and the
 // pointwise state) before it transforms the current one, so that they are in
 // flight while it computes and hold no registers meanwhile.  Two staging slots
-// per warp alternate.  Selected on the host (Params::stage) where a warp's
-// slice of shared memory, sized for the FP64 phases, holds them; K fields per
-// line (PFC: 1), NS arrays of pointwise state.
+// per warp alternate.  The transforms run on two buffers in the padded layout
+// (fft.cuh: no bank conflicts in the strided stages).  Selected on the host
+// (Params::stage) where a warp's slice of shared memory, sized for the FP64
+// phases, holds them; K fields per line (PFC: 1), NS arrays of pointwise state.
 //
 // Row unit: rows r0, r0 + 1.  Slot = K x (N/2 + 1) 16-byte pieces (the two
 // rows' coefficients at k, adjacent in the [k][row] layout) + NS x 2 rows of
-// FP32 state.  Column unit: line k1.  Slot = K lines of the input spectrum +
-// NS lines of complex state, pitch N; the slot's spectrum lines are the first
-// transform buffer.
+// FP32 state.  The pointwise step writes its outputs over its inputs (each
+// point reads all of its fields before writing any).  Column unit: line k1.
+// Slot = K lines of the input spectrum + NS lines of complex state, pitch N;
+// the first stage of the forward transform reads the slot's lines.
 
 __host__ __device__ constexpr size_t row_staged_smem(int n, int k, int ns) {
-    return 4 * (size_t)k * (size_t)(n + 2) * 8 + 2 * ((size_t)k * (size_t)(n / 2 + 1) * 16 + (size_t)ns * 2 * n * 4);
+    return 2 * (size_t)k * (size_t)padded_len(n) * 8 +
+           2 * ((size_t)k * (size_t)(n / 2 + 1) * 16 + (size_t)ns * 2 * n * 4);
 }
 __host__ __device__ constexpr size_t col_staged_smem(int n, int k, int ns) {
-    return (size_t)k * n * 8 + 2 * (size_t)(k + ns) * n * 8;
+    return 2 * (size_t)k * (size_t)padded_len(n) * 8 + 2 * (size_t)(k + ns) * n * 8;
 }
 
 template <int NF, int K, int NS, class Ap>
 __device__ void row_pass_staged(const Params& P, const Tw& tw, const float2* src, float2* dst,
                                 const float* const* sp, char* smem, Ap&& ap) {
-    constexpr int LOGN = ilog2c(NF), HALF = NF / 2, H1 = HALF + 1, PITCH = NF + 2, E = NF / kWarp;
+    constexpr int LOGN = ilog2c(NF), HALF = NF / 2, H1 = HALF + 1, PP = padded_len(NF), E = NF / kWarp;
     constexpr int SLOT = K * H1 * 16 + NS * 2 * NF * 4;  // bytes
     const int rows = P.rows;
     const long long Hs = P.H;
     const WarpCtx w = warp_ctx(P, smem);
     float2* X0 = (float2*)w.mem;
-    float2* X1 = X0 + K * PITCH;
-    float2* Y0 = X1 + K * PITCH;
-    float2* Y1 = Y0 + K * PITCH;
-    char* slots = (char*)(Y1 + K * PITCH);
+    float2* X1 = X0 + K * PP;
+    char* slots = (char*)(X1 + K * PP);
     const float iscale = (float)P.inv_npts;
     const URange ur = units_of(tw, rows / 2);
     auto issue = [&](int u, int s) {
@@ -825,13 +831,17 @@ __device__ void row_pass_staged(const Params& P, const Tw& tw, const float2* src
                 const float4 v = sq[f * H1 + k];
                 float2 A{v.x, v.y}, B{v.z, v.w};
                 if (x == 0 || x == HALF) { A.y = 0.f; B.y = 0.f; }
-                X0[f * PITCH + x] = (x <= HALF) ? float2{A.x - B.y, A.y + B.x} : float2{A.x + B.y, B.x - A.y};
+                X0[f * PP + pix<true>(x)] =
+                    (x <= HALF) ? float2{A.x - B.y, A.y + B.x} : float2{A.x + B.y, B.x - A.y};
             }
         }
-        const float2* Xr = fft_lines_fixed<+1, float, LOGN, K>(X0, X1, PITCH, K, tw.t32, tw.log, w.lane) ? X1 : X0;
+        const int r = fft_lines_fixed<+1, float, LOGN, K, true>(X0, X1, PP, K, tw.t32, tw.log, w.lane);
+        float2* Xr = r ? X1 : X0;
+        float2* Xo = r ? X0 : X1;
 #pragma unroll
         for (int i = 0; i < E; i++) {
             const int x = w.lane + kWarp * i;
+            const int px = pix<true>(x);
 #pragma unroll
             for (int rr = 0; rr < 2; rr++) {
                 float sv[NS], in[K], out[K];
@@ -839,24 +849,25 @@ __device__ void row_pass_staged(const Params& P, const Tw& tw, const float2* src
                 for (int a = 0; a < NS; a++) sv[a] = st[a * 2 * NF + rr * NF + x];
 #pragma unroll
                 for (int f = 0; f < K; f++) {
-                    const float2 z = Xr[f * PITCH + x];
+                    const float2 z = Xr[f * PP + px];
                     in[f] = (rr ? z.y : z.x) * iscale;
                 }
                 ap((long long)(r0 + rr) * NF + x, r0 + rr, x, sv, in, out);
 #pragma unroll
                 for (int g = 0; g < K; g++) {
-                    if (rr) Y0[g * PITCH + x].y = out[g];
-                    else Y0[g * PITCH + x].x = out[g];
+                    if (rr) Xr[g * PP + px].y = out[g];
+                    else Xr[g * PP + px].x = out[g];
                 }
             }
         }
-        const float2* Yr = fft_lines_fixed<-1, float, LOGN, K>(Y0, Y1, PITCH, K, tw.t32, tw.log, w.lane) ? Y1 : Y0;
+        const int r2 = fft_lines_fixed<-1, float, LOGN, K, true>(Xr, Xo, PP, K, tw.t32, tw.log, w.lane);
+        const float2* Yr = r2 ? Xo : Xr;
 #pragma unroll
         for (int g = 0; g < K; g++) {
             float4* d0 = (float4*)(dst + (size_t)g * Hs + r0);
-            const float2* zl = Yr + g * PITCH;
+            const float2* zl = Yr + g * PP;
             for (int k = w.lane; k <= HALF; k += kWarp) {
-                const float2 zk = zl[k], zn = zl[(NF - k) & (NF - 1)];
+                const float2 zk = zl[pix<true>(k)], zn = zl[pix<true>((NF - k) & (NF - 1))];
                 d0[(size_t)k * (rows / 2)] =
                     float4{0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y), 0.5f * (zk.y + zn.y), 0.5f * (zn.x - zk.x)};
             }
@@ -870,13 +881,14 @@ __device__ void row_pass_staged(const Params& P, const Tw& tw, const float2* src
 template <int NF, int K, int NS, class Ap>
 __device__ void col_pass_staged(const Params& P, const Tw& tw, const float2* src, float2* dst,
                                 const float2* const* sc, char* smem, Ap&& ap) {
-    constexpr int LOGN = ilog2c(NF), E = NF / kWarp;
+    constexpr int LOGN = ilog2c(NF), PP = padded_len(NF), E = NF / kWarp;
     constexpr int SLOT = (K + NS) * NF * 8;  // bytes
     const int ncols = P.ncols;
     const long long Hs = P.H;
     const WarpCtx w = warp_ctx(P, smem);
-    float2* B1 = (float2*)w.mem;
-    char* slots = (char*)(B1 + K * NF);
+    float2* B0 = (float2*)w.mem;
+    float2* B1 = B0 + K * PP;
+    char* slots = (char*)(B1 + K * PP);
     const URange ur = units_of(tw, ncols);
     auto issue = [&](int k1, int s) {
         float2* sl = (float2*)(slots + (size_t)s * SLOT);
@@ -897,29 +909,33 @@ __device__ void col_pass_staged(const Params& P, const Tw& tw, const float2* src
         cp_async_commit();
         cp_async_wait<1>();
         warp_sync();
-        float2* b0 = (float2*)(slots + (size_t)s * SLOT);
-        const float2* st = b0 + K * NF;
-        const int r = fft_lines_fixed<-1, float, LOGN, K>(b0, B1, NF, K, tw.t32, tw.log, w.lane);
-        float2* Xr = r ? B1 : b0;
-        float2* Xi = r ? b0 : B1;
+        const float2* sl = (const float2*)(slots + (size_t)s * SLOT);
+        const float2* st = sl + K * NF;
+        const int r = fft_lines_fixed_into_padded<-1, float, LOGN, K>(sl, NF, B0, B1, PP, K, tw.t32, tw.log, w.lane);
+        float2* Xr = r ? B1 : B0;
+        float2* Xi = r ? B0 : B1;
 #pragma unroll
         for (int i = 0; i < E; i++) {
             const int k0 = w.lane + kWarp * i;
+            const int pk = pix<true>(k0);
             float2 sv[NS], in[K], out[K];
 #pragma unroll
             for (int a = 0; a < NS; a++) sv[a] = st[a * NF + k0];
 #pragma unroll
-            for (int f = 0; f < K; f++) in[f] = Xr[f * NF + k0];
+            for (int f = 0; f < K; f++) in[f] = Xr[f * PP + pk];
             ap(k1, k0, sv, in, out);
 #pragma unroll
-            for (int g = 0; g < K; g++) Xi[g * NF + k0] = out[g];
+            for (int g = 0; g < K; g++) Xi[g * PP + pk] = out[g];
         }
-        const float2* Yr = fft_lines_fixed<+1, float, LOGN, K>(Xi, Xr, NF, K, tw.t32, tw.log, w.lane) ? Xr : Xi;
+        const float2* Yr = fft_lines_fixed<+1, float, LOGN, K, true>(Xi, Xr, PP, K, tw.t32, tw.log, w.lane) ? Xr : Xi;
 #pragma unroll
         for (int g = 0; g < K; g++) {
             float4* d = (float4*)(dst + (size_t)g * Hs + (size_t)k1 * NF);
-            const float4* y = (const float4*)(Yr + g * NF);
-            for (int j = w.lane; j < NF / 2; j += kWarp) d[j] = y[j];
+            const float2* y = Yr + g * PP;
+            for (int j = w.lane; j < NF / 2; j += kWarp) {
+                const int q = pix<true>(2 * j);  // 2j and 2j + 1 share a 16-point group
+                d[j] = float4{y[q].x, y[q].y, y[q + 1].x, y[q + 1].y};
+            }
         }
         warp_sync();
     }
@@ -1100,6 +1116,7 @@ constexpr int kNoCoop = 1 << 20;
 // every km holds kMidG neighbouring values.
 constexpr int kMidG = 2;
 
+// sz: bytes of a real scalar (8 for FP64 lines)
 __host__ __device__ __forceinline__ size_t mid_warp_smem(int nm, int sz) {
     return (size_t)2 * kMidG * pitch_of(nm) * 2 * sz;
 }
@@ -1176,6 +1193,85 @@ __device__ void mid_pass(const Params& P, const Tw& tw, int k, const cx<T>* src,
             warp_sync();
         }
     }
+}
+
+// The FP32 middle passes of cubic grids with their inputs staged as in the
+// iteration passes: a unit (kMidG lines of one field) is 16-byte pieces, each
+// two neighbouring lines' values at one position (row side: i1 pairs of one
+// line; transposed side: the kMidG values at one km), copied by cp.async into
+// one of two slots while the warp transforms the previous unit; transforms in
+// the padded layout.
+__host__ __device__ constexpr size_t mid_staged_smem(int n) {
+    return 2 * (size_t)kMidG * (size_t)padded_len(n) * 8 + 2 * (size_t)n * 16;
+}
+
+template <int NF, int S>
+__device__ void mid_pass_staged(const Params& P, const Tw& tw, int k, const float2* src, float2* dst, char* smem) {
+    constexpr int LOGN = ilog2c(NF), PP = padded_len(NF);
+    static_assert(kMidG == 2, "a 16-byte piece holds kMidG FP32 complex values");
+    const int n0 = P.n0, rows = P.rows, gpp = P.n0 / kMidG;
+    const long long H = P.H;
+    const WarpCtx w = warp_ctx(P, smem);
+    float2* B0 = (float2*)w.mem;
+    float2* B1 = B0 + kMidG * PP;
+    float4* slots = (float4*)(B1 + kMidG * PP);  // 2 x NF pieces
+    const URange ur = units_of(tw, P.h1 * gpp);
+    auto issue = [&](int u, int f, int s) {
+        const int k1 = u / gpp, i0 = (u - k1 * gpp) * kMidG;
+        const float2* sf = src + (size_t)f * H;
+        float4* sl = slots + s * NF;
+        if (S < 0) {
+            const float2* rb = sf + (size_t)k1 * rows + (size_t)i0 * NF;  // [k1][i0][i1]
+            for (int j = w.lane; j < NF; j += kWarp) cp_async16(sl + j, rb + 2 * j);
+        } else {
+            const float2* cb = sf + (size_t)k1 * NF * n0 + i0;  // [k1][km][i0]
+            for (int km = w.lane; km < NF; km += kWarp) cp_async16(sl + km, cb + (size_t)km * n0);
+        }
+    };
+    int u = ur.b, f = 0, s = 0;
+    if (u < ur.e && k > 0) issue(u, 0, 0);
+    cp_async_commit();
+    while (u < ur.e && k > 0) {
+        int un = u, fn = f + 1;
+        if (fn == k) {
+            fn = 0;
+            un = u + ur.s;
+        }
+        if (un < ur.e) issue(un, fn, s ^ 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        warp_sync();
+        const float2* sl = (const float2*)(slots + s * NF);
+#pragma unroll 4
+        for (int j = w.lane; j < kMidG * NF; j += kWarp) {
+            if (S < 0) B0[(j / NF) * PP + pix<true>(j % NF)] = sl[j];         // line g = j / NF
+            else B0[(j % kMidG) * PP + pix<true>(j / kMidG)] = sl[j];         // km = j / kMidG
+        }
+        const int r = fft_lines_fixed<S, float, LOGN, kMidG, true>(B0, B1, PP, kMidG, tw.t32, tw.log, w.lane);
+        const float2* Br = r ? B1 : B0;
+        const int k1 = u / gpp, i0 = (u - k1 * gpp) * kMidG;
+        float2* df = dst + (size_t)f * H;
+        if (S < 0) {
+            float4* cb = (float4*)(df + (size_t)k1 * NF * n0 + i0);
+            for (int km = w.lane; km < NF; km += kWarp) {
+                const float2 a = Br[pix<true>(km)], b = Br[PP + pix<true>(km)];
+                cb[(size_t)km * (n0 / 2)] = float4{a.x, a.y, b.x, b.y};
+            }
+        } else {
+            float4* rb = (float4*)(df + (size_t)k1 * rows + (size_t)i0 * NF);
+            for (int j = w.lane; j < NF; j += kWarp) {
+                const int g = (2 * j) / NF, q = pix<true>((2 * j) % NF);  // i1 and i1 + 1 share a group
+                const float2 a = Br[g * PP + q], b = Br[g * PP + q + 1];
+                rb[j] = float4{a.x, a.y, b.x, b.y};
+            }
+        }
+        warp_sync();
+        u = un;
+        f = fn;
+        s ^= 1;
+    }
+    cp_async_wait<0>();
+    warp_sync();
 }
 
 // Column passes read the last row pass's output and write the next row pass's
@@ -1729,6 +1825,34 @@ __device__ __noinline__ void phase_R_staged(const Params& P, const Ctl& c, const
     publish_sum(&P.sums[(size_t)bank * P.nslots + c.ev], asum);
 }
 
+// The FP32 iteration row pass with CTA-cooperative units (row_pass_coop), an
+// opt-in alternative (Params::coop32) for grids with fewer row units than
+// SMs, where one warp per unit leaves most of an SM idle.
+template <int NF>
+__device__ __noinline__ void phase_R_coop(const Params& P, const Ctl& c, const Tw& tw, char* smem, const float2* src) {
+    const RowK<float> q = row_consts<float>(P, c);
+    const int bank = c.step & 1;
+    float* dcur = (float*)P.DD[c.it & 1];
+    const float* dprev = (const float*)P.DD[(c.it - 1) & 1];
+    const float* vbt = (const float*)P.VBt;
+    const float* lbt = (const float*)P.LBt;
+    const int K = k_iter(P.model);
+    const bool pfc = P.model == M_PFC;
+    float amax = 0.f;
+    double asum = 0.0;
+    struct St { float dp, dpp, b, lb; };
+    row_pass_coop<float, float, NF>(
+        P, tw, K, K, src, (float2*)P.NB, smem,
+        [&](long long p, int, int) { return St{dprev[p], dcur[p], vbt[p], pfc ? 0.f : lbt[p]}; },
+        [&](long long p, int, int, const St& s, const float* in, float* out) {
+            if (pfc) row_point<float, float, true>(q, dcur, p, s.dp, s.dpp, s.b, s.lb, in, out, amax, asum);
+            else row_point<float, float, false>(q, dcur, p, s.dp, s.dpp, s.b, s.lb, in, out, amax, asum);
+        });
+    // every warp publishes its threads' norm and sum
+    publish_max(&P.norms[(size_t)bank * P.nslots + c.ev], (double)amax);
+    publish_sum(&P.sums[(size_t)bank * P.nslots + c.ev], asum);
+}
+
 // Iteration row pass (R1 reads the FP64 base direction, RI the T one):
 // delta_it = ybar_{it-1} + theta_v s d_{it-1}; ||d_{it-1}||_inf; then the
 // nonlinear differences at ybar_it and their forward x-DFT.
@@ -1739,6 +1863,12 @@ __device__ PAGD_HOT void phase_R(const Params& P, const Ctl& c, const Tw& tw, ch
         if (P.stage && P.model == M_PFC) {
             phase_R_staged<NF & (kNoCoop - 1)>(P, c, tw, smem, (const float2*)src);
             return;
+        }
+        if constexpr (!(NF & kNoCoop)) {
+            if (P.coop32) {
+                phase_R_coop<NF>(P, c, tw, smem, (const float2*)src);
+                return;
+            }
         }
     }
     const RowK<T> q = row_consts<T>(P, c);
@@ -1832,6 +1962,28 @@ __device__ __noinline__ void phase_CI_staged(const Params& P, const Ctl& c, cons
                               });
 }
 
+// The FP32 iteration column pass with CTA-cooperative units (col_pass_coop).
+template <int NF>
+__device__ __noinline__ void phase_CI_coop(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
+    const ColK<float> q = col_consts<float>(P, c);
+    const float2* scur = (const float2*)P.SS[c.it & 1];
+    float2* sprev = (float2*)P.SS[(c.it - 1) & 1];
+    const float2* C0 = (const float2*)P.C0;
+    const int K = k_iter(P.model);
+    const bool pfc = P.model == M_PFC;
+    struct St { float2 sc, sp, g0; };
+    col_pass_coop<float, float, NF>(
+        P, tw, K, K, csrcT<float>(P), cdstT<float>(P), smem,
+        [&](int k1, int k0) {
+            const long long idx = (long long)k1 * P.n0 + k0;
+            return St{scur[idx], sprev[idx], C0[idx]};
+        },
+        [&](int k1, int k0, const St& s, const float2* in, float2* out) {
+            if (pfc) col_point<float, true>(P, q, sprev, k1, k0, s.sc, s.sp, s.g0, in, out);
+            else col_point<float, false>(P, q, sprev, k1, k0, s.sc, s.sp, s.g0, in, out);
+        });
+}
+
 // Iteration column pass: ybar_hat, spectral residual, preconditioned
 // direction and spectral state update (col_point), and the inverse y-DFT of d
 // (and of Lap ybar_{it+1} for FCH).
@@ -1842,6 +1994,12 @@ __device__ PAGD_HOT void phase_CI(const Params& P, const Ctl& c, const Tw& tw, c
         if (P.stage && P.model == M_PFC) {
             phase_CI_staged<NF & (kNoCoop - 1)>(P, c, tw, smem);
             return;
+        }
+        if constexpr (!(NF & kNoCoop)) {
+            if (P.coop32) {
+                phase_CI_coop<NF>(P, c, tw, smem);
+                return;
+            }
         }
     }
     const ColK<T> q = col_consts<T>(P, c);
@@ -2245,6 +2403,16 @@ __host__ __device__ inline Ctl ctl_init(const Params& P) {
         case PROG_RHS: c.ph = PH_RH_R0; break;
         case PROG_EST: c.ph = PH_EST; break;
         case PROG_BARRIER: c.ph = (P.nsteps > 0) ? PH_NOP : PH_DONE; break;
+        case PROG_PASS:
+            // one iteration pass repeated on the buffers of the last step, as
+            // iteration 1 of the step (a middle pass in the iterations' form:
+            // the iteration fields, in T)
+            c.ph = (P.nsteps > 0) ? P.pass : PH_DONE;
+            c.it = 1;
+            c.ev = 1;
+            c.m64 = 0;
+            c.mk = k_iter(P.model);
+            break;
         default: c.ph = PH_MASS; break;
     }
     return c;
@@ -2398,6 +2566,11 @@ __device__ void ctl_step(const Params& P, Ctl& c);
 // are read.
 template <class T>
 __device__ void ctl_advance(const Params& P, Ctl& c) {
+    if (P.prog == PROG_PASS) {
+        c.step++;
+        if (c.step >= P.nsteps) c.ph = PH_DONE;
+        return;
+    }
     if (phase_is_mid(c.ph)) {
         c.ph = c.after;
         return;
@@ -2519,6 +2692,13 @@ __device__ PAGD_DISPATCH void exec_cold(const Params& P, const Ctl& c, const Tw&
     }
 }
 
+// the FP32 middle passes of a cubic grid run staged (mid_pass_staged) when
+// the launch stages its iteration passes
+template <class T, int NF> __device__ __forceinline__ bool mid_staged(const Params& P) {
+    if constexpr (sizeof(T) == 4 && (NF & (kNoCoop - 1)) != 0) return P.stage && P.nm == (NF & (kNoCoop - 1));
+    return false;
+}
+
 template <class T, int NF>
 __device__ __forceinline__ void exec_phase(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red) {
     switch (c.ph) {
@@ -2527,10 +2707,12 @@ __device__ __forceinline__ void exec_phase(const Params& P, const Ctl& c, const 
         case PH_CI: phase_CI<T, NF>(P, c, tw, smem); break;
         case PH_MF:
             if (c.m64) mid_pass<double, -1, NF>(P, tw, c.mk, P.NB64, P.X64, smem);
+            else if (mid_staged<T, NF>(P)) mid_pass_staged<NF & (kNoCoop - 1), -1>(P, tw, c.mk, (const float2*)P.NB, (float2*)P.X, smem);
             else mid_pass<T, -1, NF>(P, tw, c.mk, (const cx<T>*)P.NB, (cx<T>*)P.X, smem);
             break;
         case PH_MI:
             if (c.m64) mid_pass<double, +1, NF>(P, tw, c.mk, P.NB64, P.DB64, smem);
+            else if (mid_staged<T, NF>(P)) mid_pass_staged<NF & (kNoCoop - 1), +1>(P, tw, c.mk, (const float2*)P.NB, (float2*)P.DB, smem);
             else mid_pass<T, +1, NF>(P, tw, c.mk, (const cx<T>*)P.NB, (cx<T>*)P.DB, smem);
             break;
         default: exec_cold<T, NF>(P, c, tw, smem, red); break;
@@ -2542,7 +2724,7 @@ __device__ __forceinline__ void exec_phase(const Params& P, const Ctl& c, const 
 inline size_t warp_smem_bytes(int n0, int n1, int model, int tsize, int nf, int nm = 1) {
     size_t m = 0;
     auto upd = [&](size_t v) { if (v > m) m = v; };
-    if (nm > 1) upd(mid_warp_smem(nm, 16));  // middle passes (3D), FP64 worst case
+    if (nm > 1) upd(mid_warp_smem(nm, 8));  // middle passes (3D), FP64 worst case
     const int ki = k_iter(model);
     if (nf == 0) {
         upd(row_warp_smem(n1, 0, 8, 3, 8));            // B (PFC: 3 fields) / IMEX R0
@@ -2608,6 +2790,32 @@ __host__ __device__ inline int phase_units(const Params& P, int ph) {
 }
 __host__ __device__ inline int unit_cost(const Params& P, int ph) {
     return phase_is_col(ph) ? P.n0 : phase_is_mid(ph) ? kMidG * P.nm : 2 * P.n1;
+}
+// Device time per point of a member's current phase, in units of an FP32
+// iteration pass (measured on GB300 with pure phases of a 96-member batch:
+// exact base row / column passes 8.8x / 7.8x, incremental ones ~2/3 of that,
+// the last step's accept 5x).  The batched launch lays members out on a cost
+// axis of points x this weight, so that a global phase mixing members in FP64
+// base evaluations with members in FP32 iterations gives every warp about the
+// same time of work.  Only the dealing of units to warps depends on it.
+__host__ __device__ inline int phase_weight(const Params& P, const Ctl& c) {
+    const bool t64 = P.precision != P_MIXED;
+    switch (c.ph) {
+        case PH_B: return c.inc ? 6 : 9;
+        case PH_C:
+        case PH_D:
+        case PH_E: return c.inc ? 5 : 8;
+        case PH_R1:
+        case PH_RI:
+        case PH_CI: return t64 ? 3 : 1;
+        case PH_MF:
+        case PH_MI: return (c.m64 || t64) ? 3 * (c.mk > 0 ? c.mk : 1) : 1;
+        case PH_ACCEPT: return 5;
+        default: return t64 ? 4 : 2;
+    }
+}
+__host__ __device__ inline long long weighted_unit_cost(const Params& P, const Ctl& c) {
+    return (long long)unit_cost(P, c.ph) * phase_weight(P, c);
 }
 
 // the fixed line lengths compiled into the batched kernel (others: runtime length)

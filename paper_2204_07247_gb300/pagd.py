@@ -27,7 +27,7 @@ SCHEMES = {"bdf2": BDF2, "mp": MP, "lbdf2": LBDF2, "lmp": LMP}
 PRECISIONS = {"fp64": FP64, "fp32_mixed": FP32_MIXED}
 EXPORTS = ("pagd_default_opts", "pfc_init", "fch_init", "pagd_workspace_size", "pagd_set_workspace",
            "pagd_set_state", "pagd_step", "pagd_step_with_guess", "pagd_run", "pagd_run_host", "pagd_energy", "pagd_mass",
-           "pagd_rhs", "pagd_run_adaptive", "pagd_fft_r2c", "pagd_fft_c2r", "pagd_get_state", "pagd_step_static", "pagd_barrier_probe", "pagd_launch_info", "pagd_set_trace",
+           "pagd_rhs", "pagd_run_adaptive", "pagd_fft_r2c", "pagd_fft_c2r", "pagd_get_state", "pagd_step_static", "pagd_barrier_probe", "pagd_pass_probe", "pagd_launch_info", "pagd_set_trace",
            "pagd_get_trace", "pagd_last_error", "pagd_destroy", "pagd_batch_create",
            "pagd_batch_workspace_size", "pagd_batch_set_workspace", "pagd_batch_run", "pagd_batch_set_shape",
            "pagd_batch_step_with_guess",
@@ -75,6 +75,7 @@ def _declare(lib):
         "pagd_get_state": [P, P, P, IP],
         "pagd_step_static": [P, P, P, i, d, d, d, P, IP, D],
         "pagd_barrier_probe": [P, i, D],
+        "pagd_pass_probe": [P, i, i, D],
         "pagd_launch_info": [P, IP, IP, IP, IP, ctypes.POINTER(ctypes.c_size_t), IP],
         "pagd_set_trace": [P, i],
         "pagd_get_trace": [P, IP, D, i, IP],
@@ -339,6 +340,18 @@ class Solver:
         the cost of one device-wide barrier with this solver's launch plan."""
         us = ctypes.c_double()
         self._check(self.lib.pagd_barrier_probe(self._h, int(count), ctypes.byref(us)), "barrier_probe")
+        return us.value
+
+    PASSES = ("RI", "CI", "MF", "MI")
+
+    def pass_probe(self, which, count=100):
+        """Device time per repetition of one iteration pass ("RI", "CI", and
+        in 3D "MF", "MI") run on its own in one launch, barrier included
+        (microseconds).  Needs a completed step; overwrites the iteration
+        buffers, keeps the state."""
+        us = ctypes.c_double()
+        self._check(self.lib.pagd_pass_probe(self._h, self.PASSES.index(which), int(count), ctypes.byref(us)),
+                    "pass_probe")
         return us.value
 
     def set_trace(self, enable=True):

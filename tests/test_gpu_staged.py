@@ -106,3 +106,30 @@ def test_staged_3d_matches_register_staged(torch, lib, monkeypatch):
     assert _counts_agree(runs["1"][0], runs["0"][0])
     a, b = runs["1"][1], runs["0"][1]
     assert np.linalg.norm(a - b) <= REL * np.linalg.norm(b)
+
+
+def test_cooperative_fp32_passes_match_warp_owned(torch, lib, monkeypatch):
+    """FCH 256^2 with the opt-in CTA-cooperative FP32 iteration passes
+    (PAGD_COOP32=1) against the warp-owned passes (0) on the same input, and
+    both against the oracle's reference trajectory at step 25."""
+    import json
+    import os
+    w = I.FCH256
+    runs = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("PAGD_COOP32", mode)
+        S = pagd.solver_for(w, lib=lib)
+        S.set_state(dev(torch, w.u0(1)))
+        out = torch.empty(w.n, dtype=torch.float64, device="cuda")
+        its, res = S.run(w.dt, 25, w.tol, out)
+        assert np.all(res <= w.tol)
+        runs[mode] = (list(its), host(out))
+    assert _counts_agree(runs["1"][0], runs["0"][0])
+    a, b = runs["1"][1], runs["0"][1]
+    assert np.linalg.norm(a - b) <= REL * np.linalg.norm(b)
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_fch2d_256_bdf2_fp32mixed.json")))
+    st = ref["states"]["25"]
+    for u in (a, b):
+        est = I.sketch_rel_l2(I.sketch(u, ref["sketch"]["count"], ref["sketch"]["seed"]), st["sketch"], st["sumsq"])
+        # within the oracle's own tolerance floor at this step (twice, for the sketch's spread)
+        assert est <= 2 * ref["tol_floor"]["rel_l2"]["25"], est
