@@ -329,20 +329,22 @@ static pagd_status run_program(pagd_solver* s, Params& P) {
     return st;
 }
 
-// The PFC FP32 iteration passes stage their inputs through shared memory
+// The FP32 iteration passes stage their inputs through shared memory
 // (row_pass_staged / col_pass_staged) when a warp slice of warp_bytes holds
-// the two staging slots; fixed line lengths only.  PAGD_STAGED=0 keeps the
+// the staging slots (PFC two, FCH one); fixed line lengths only.  PAGD_STAGED=0 keeps the
 // register-staged passes (the same arithmetic, for comparison).
 static bool stage_fits(const pagd_solver* s, size_t warp_bytes) {
     const int last = s->dim - 1;
     const int nf = fixed_len(s->n[0], s->n[last]);
-    if (nf == 0 || s->tsize != 4 || s->model != M_PFC) return false;
+    if (nf == 0 || s->tsize != 4) return false;
     if (const char* e = std::getenv("PAGD_STAGED"))
         if (e[0] == '0' && e[1] == 0) return false;
     const int k = k_iter(s->model);
     // the middle passes of a cubic grid stage too (mid_pass_staged)
     if (s->dim == 3 && s->n[1] == nf && mid_staged_smem(nf) > warp_bytes) return false;
-    return row_staged_smem(nf, k, 3) <= warp_bytes && col_staged_smem(nf, k, 3) <= warp_bytes;
+    const int sl = staged_slots(s->model);
+    return row_staged_smem(nf, k, staged_row_state(s->model), sl) <= warp_bytes &&
+           col_staged_smem(nf, k, 3, sl) <= warp_bytes;
 }
 
 // One warp per row unit / column / middle unit.  A CTA has as many warps (at
@@ -404,7 +406,7 @@ static void make_plan(pagd_solver* s) {
             if (nf == 256) s->coop = 0;
         }
     }
-    s->stage = stage_fits(s, s->warp_bytes) ? 1 : 0;
+    s->stage = (!s->cl && stage_fits(s, s->warp_bytes)) ? 1 : 0;
     // FP32 iteration passes with CTA-cooperative units (unstaged FP32 passes
     // of fixed line length): opt-in with PAGD_COOP32=1.  Measured slower on
     // FCH 256^2 (128 row pairs on 152 SMs), where the FP64 passes gain from

@@ -776,15 +776,20 @@ __device__ void col_pass_fixed(const Params& P, const Tw& tw, int kin, int kout,
 // Slot = K lines of the input spectrum + NS lines of complex state, pitch N;
 // the first stage of the forward transform reads the slot's lines.
 
-__host__ __device__ constexpr size_t row_staged_smem(int n, int k, int ns) {
+__host__ __device__ constexpr size_t row_staged_smem(int n, int k, int ns, int slots) {
     return 2 * (size_t)k * (size_t)padded_len(n) * 8 +
-           2 * ((size_t)k * (size_t)(n / 2 + 1) * 16 + (size_t)ns * 2 * n * 4);
+           (size_t)slots * ((size_t)k * (size_t)(n / 2 + 1) * 16 + (size_t)ns * 2 * n * 4);
 }
-__host__ __device__ constexpr size_t col_staged_smem(int n, int k, int ns) {
-    return 2 * (size_t)k * (size_t)padded_len(n) * 8 + 2 * (size_t)(k + ns) * n * 8;
+__host__ __device__ constexpr size_t col_staged_smem(int n, int k, int ns, int slots) {
+    return 2 * (size_t)k * (size_t)padded_len(n) * 8 + (size_t)slots * (size_t)(k + ns) * n * 8;
 }
+// staging slots per model: PFC (one field) prefetches the next unit into a
+// second slot; FCH (two fields, four state arrays) has room for one slot,
+// which still puts all of a unit's reads in flight at once
+__host__ __device__ constexpr int staged_slots(int model) { return model == 0 ? 2 : 1; }
+__host__ __device__ constexpr int staged_row_state(int model) { return model == 0 ? 3 : 4; }
 
-template <int NF, int K, int NS, class Ap>
+template <int NF, int K, int NS, int SLOTS, class Ap>
 __device__ void row_pass_staged(const Params& P, const Tw& tw, const float2* src, float2* dst,
                                 const float* const* sp, char* smem, Ap&& ap) {
     constexpr int LOGN = ilog2c(NF), HALF = NF / 2, H1 = HALF + 1, PP = padded_len(NF), E = NF / kWarp;
@@ -810,14 +815,21 @@ __device__ void row_pass_staged(const Params& P, const Tw& tw, const float2* src
             for (int j = w.lane; j < NF / 2; j += kWarp)
                 cp_async16(st + a * 2 * NF + 4 * j, sp[a] + (size_t)r0 * NF + 4 * j);
     };
-    if (ur.b < ur.e) issue(ur.b, 0);
-    cp_async_commit();
+    if (SLOTS == 2 && ur.b < ur.e) issue(ur.b, 0);
+    if (SLOTS == 2) cp_async_commit();
     int s = 0;
-    for (int u = ur.b; u < ur.e; u += ur.s, s ^= 1) {
+    for (int u = ur.b; u < ur.e; u += ur.s, s ^= (SLOTS - 1)) {
         const int r0 = 2 * u;
-        if (u + ur.s < ur.e) issue(u + ur.s, s ^ 1);
-        cp_async_commit();
-        cp_async_wait<1>();
+        if constexpr (SLOTS == 2) {
+            // this unit's copies were issued with the previous unit
+            if (u + ur.s < ur.e) issue(u + ur.s, s ^ 1);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            issue(u, 0);
+            cp_async_commit();
+            cp_async_wait<0>();
+        }
         warp_sync();
         const float4* sq = (const float4*)(slots + (size_t)s * SLOT);
         const float* st = (const float*)(sq + K * H1);
@@ -878,7 +890,7 @@ __device__ void row_pass_staged(const Params& P, const Tw& tw, const float2* src
     warp_sync();
 }
 
-template <int NF, int K, int NS, class Ap>
+template <int NF, int K, int NS, int SLOTS, class Ap>
 __device__ void col_pass_staged(const Params& P, const Tw& tw, const float2* src, float2* dst,
                                 const float2* const* sc, char* smem, Ap&& ap) {
     constexpr int LOGN = ilog2c(NF), PP = padded_len(NF), E = NF / kWarp;
@@ -901,13 +913,19 @@ __device__ void col_pass_staged(const Params& P, const Tw& tw, const float2* src
             for (int j = w.lane; j < NF / 2; j += kWarp)
                 cp_async16(sl + (K + a) * NF + 2 * j, sc[a] + (size_t)k1 * NF + 2 * j);
     };
-    if (ur.b < ur.e) issue(ur.b, 0);
-    cp_async_commit();
+    if (SLOTS == 2 && ur.b < ur.e) issue(ur.b, 0);
+    if (SLOTS == 2) cp_async_commit();
     int s = 0;
-    for (int k1 = ur.b; k1 < ur.e; k1 += ur.s, s ^= 1) {
-        if (k1 + ur.s < ur.e) issue(k1 + ur.s, s ^ 1);
-        cp_async_commit();
-        cp_async_wait<1>();
+    for (int k1 = ur.b; k1 < ur.e; k1 += ur.s, s ^= (SLOTS - 1)) {
+        if constexpr (SLOTS == 2) {
+            if (k1 + ur.s < ur.e) issue(k1 + ur.s, s ^ 1);
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            issue(k1, 0);
+            cp_async_commit();
+            cp_async_wait<0>();
+        }
         warp_sync();
         const float2* sl = (const float2*)(slots + (size_t)s * SLOT);
         const float2* st = sl + K * NF;
@@ -1804,23 +1822,26 @@ __device__ __forceinline__ void row_point(const RowK<T>& q, T* dcur, long long p
     }
 }
 
-// The PFC FP32 iteration row pass with staged inputs (row_pass_staged): its
-// own function, so that its registers are allocated apart from the general
-// pass's.
-template <int NF>
+// The FP32 iteration row pass with staged inputs (row_pass_staged): its own
+// function, so that its registers are allocated apart from the general
+// pass's.  PFC: one field, state delta_i, delta_{i-1}, base; FCH: two fields
+// (the direction and its Laplacian), and the base's Laplacian as fourth state.
+template <int NF, bool PFC>
 __device__ __noinline__ void phase_R_staged(const Params& P, const Ctl& c, const Tw& tw, char* smem,
                                             const float2* src) {
+    constexpr int K = PFC ? 1 : 2, NS = staged_row_state(PFC ? 0 : 1), SL = staged_slots(PFC ? 0 : 1);
     const RowK<float> q = row_consts<float>(P, c);
     const int bank = c.step & 1;
     float* dcur = (float*)P.DD[c.it & 1];
-    const float* sp[3] = {(const float*)P.DD[(c.it - 1) & 1], dcur, (const float*)P.VBt};
+    const float* sp[4] = {(const float*)P.DD[(c.it - 1) & 1], dcur, (const float*)P.VBt, (const float*)P.LBt};
     float amax = 0.f;
     double asum = 0.0;
-    row_pass_staged<NF, 1, 3>(P, tw, src, (float2*)P.NB, sp, smem,
-                              [&](long long p, int, int, const float* sv, const float* in, float* out) {
-                                  row_point<float, float, true>(q, dcur, p, sv[0], sv[1], sv[2], 0.f, in, out,
-                                                                amax, asum);
-                              });
+    row_pass_staged<NF, K, NS, SL>(P, tw, src, (float2*)P.NB, sp, smem,
+                                   [&](long long p, int, int, const float* sv, const float* in, float* out) {
+                                       row_point<float, float, PFC>(q, dcur, p, sv[0], sv[1], sv[2],
+                                                                    NS > 3 ? sv[NS > 3 ? 3 : 0] : 0.f, in, out,
+                                                                    amax, asum);
+                                   });
     publish_max(&P.norms[(size_t)bank * P.nslots + c.ev], (double)amax);
     publish_sum(&P.sums[(size_t)bank * P.nslots + c.ev], asum);
 }
@@ -1860,8 +1881,9 @@ template <class TI, class T, int NF>
 __device__ PAGD_HOT void phase_R(const Params& P, const Ctl& c, const Tw& tw, char* smem, double* red,
                         const cx<TI>* src) {
     if constexpr (sizeof(TI) == 4 && sizeof(T) == 4 && (NF & (kNoCoop - 1)) != 0) {
-        if (P.stage && P.model == M_PFC) {
-            phase_R_staged<NF & (kNoCoop - 1)>(P, c, tw, smem, (const float2*)src);
+        if (P.stage) {
+            if (P.model == M_PFC) phase_R_staged<NF & (kNoCoop - 1), true>(P, c, tw, smem, (const float2*)src);
+            else phase_R_staged<NF & (kNoCoop - 1), false>(P, c, tw, smem, (const float2*)src);
             return;
         }
         if constexpr (!(NF & kNoCoop)) {
@@ -1950,16 +1972,18 @@ __device__ __forceinline__ void col_point(const Params& P, const ColK<T>& q, cx<
     }
 }
 
-// The PFC FP32 iteration column pass with staged inputs (col_pass_staged).
-template <int NF>
+// The FP32 iteration column pass with staged inputs (col_pass_staged): K
+// fields out (PFC: the direction; FCH: also the Laplacian of ybar_{it+1}).
+template <int NF, bool PFC>
 __device__ __noinline__ void phase_CI_staged(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
+    constexpr int K = PFC ? 1 : 2, SL = staged_slots(PFC ? 0 : 1);
     const ColK<float> q = col_consts<float>(P, c);
     float2* sprev = (float2*)P.SS[(c.it - 1) & 1];
     const float2* sc3[3] = {(const float2*)P.SS[c.it & 1], sprev, (const float2*)P.C0};
-    col_pass_staged<NF, 1, 3>(P, tw, csrcT<float>(P), cdstT<float>(P), sc3, smem,
-                              [&](int k1, int k0, const float2* sv, const float2* in, float2* out) {
-                                  col_point<float, true>(P, q, sprev, k1, k0, sv[0], sv[1], sv[2], in, out);
-                              });
+    col_pass_staged<NF, K, 3, SL>(P, tw, csrcT<float>(P), cdstT<float>(P), sc3, smem,
+                                  [&](int k1, int k0, const float2* sv, const float2* in, float2* out) {
+                                      col_point<float, PFC>(P, q, sprev, k1, k0, sv[0], sv[1], sv[2], in, out);
+                                  });
 }
 
 // The FP32 iteration column pass with CTA-cooperative units (col_pass_coop).
@@ -1991,8 +2015,9 @@ template <class T, int NF>
 __device__ PAGD_HOT void phase_CI(const Params& P, const Ctl& c, const Tw& tw, char* smem) {
     using C = cx<T>;
     if constexpr (sizeof(T) == 4 && (NF & (kNoCoop - 1)) != 0) {
-        if (P.stage && P.model == M_PFC) {
-            phase_CI_staged<NF & (kNoCoop - 1)>(P, c, tw, smem);
+        if (P.stage) {
+            if (P.model == M_PFC) phase_CI_staged<NF & (kNoCoop - 1), true>(P, c, tw, smem);
+            else phase_CI_staged<NF & (kNoCoop - 1), false>(P, c, tw, smem);
             return;
         }
         if constexpr (!(NF & kNoCoop)) {

@@ -116,6 +116,7 @@ def test_cooperative_fp32_passes_match_warp_owned(torch, lib, monkeypatch):
     import os
     w = I.FCH256
     runs = {}
+    monkeypatch.setenv("PAGD_STAGED", "0")  # the cooperative passes replace the register-staged ones
     for mode in ("1", "0"):
         monkeypatch.setenv("PAGD_COOP32", mode)
         S = pagd.solver_for(w, lib=lib)
@@ -133,3 +134,23 @@ def test_cooperative_fp32_passes_match_warp_owned(torch, lib, monkeypatch):
         est = I.sketch_rel_l2(I.sketch(u, ref["sketch"]["count"], ref["sketch"]["seed"]), st["sketch"], st["sumsq"])
         # within the oracle's own tolerance floor at this step (twice, for the sketch's spread)
         assert est <= 2 * ref["tol_floor"]["rel_l2"]["25"], est
+
+
+@pytest.mark.parametrize("name", ["fch2d_256_bdf2_fp32mixed", "fch2d_512_bdf2_fp32mixed"])
+def test_staged_fch_matches_register_staged(torch, lib, monkeypatch, name):
+    """FCH's staged passes (two fields, one staging slot) against its
+    register-staged passes on the same input, 20 steps."""
+    w = I.WORKLOADS[name]
+    runs = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("PAGD_STAGED", mode)
+        S = pagd.solver_for(w, lib=lib)
+        assert S.launch_info()["staged"] == (mode == "1")
+        S.set_state(dev(torch, w.u0(1)))
+        out = torch.empty(w.n, dtype=torch.float64, device="cuda")
+        its, res = S.run(w.dt, 20, w.tol, out)
+        assert np.all(res <= w.tol)
+        runs[mode] = (list(its), host(out))
+    assert _counts_agree(runs["1"][0], runs["0"][0])
+    a, b = runs["1"][1], runs["0"][1]
+    assert np.linalg.norm(a - b) <= REL * np.linalg.norm(b)

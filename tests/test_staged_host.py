@@ -43,9 +43,12 @@ def test_staging_selection(emu, monkeypatch):
     # PFC FP32-mixed on a square power-of-two grid: staged
     S = pagd.Solver("pfc", (64, 64), (16 * math.pi,) * 2, 0.25, precision="fp32_mixed", lib=emu)
     assert S.launch_info()["staged"]
-    # FP64 iterations, FCH, and runtime line lengths keep the register-staged passes
+    # FCH FP32-mixed too (one staging slot)
+    S = pagd.Solver("fch", (64, 64), (16 * math.pi,) * 2, 0.1, 0.1, 0.1, 0.0, precision="fp32_mixed", lib=emu)
+    assert S.launch_info()["staged"]
+    # FP64 iterations and runtime line lengths keep the register-staged passes
     for kw in (dict(model="pfc", n=(64, 64), precision="fp64"),
-               dict(model="fch", n=(64, 64), precision="fp32_mixed"),
+               dict(model="fch", n=(64, 64), precision="fp64"),
                dict(model="pfc", n=(16, 32), precision="fp32_mixed")):
         args = (0.25,) if kw["model"] == "pfc" else (0.1, 0.1, 0.1, 0.0)
         S = pagd.Solver(kw["model"], kw["n"], (16 * math.pi,) * 2, *args, precision=kw["precision"], lib=emu)
@@ -155,3 +158,23 @@ def test_cooperative_fp32_passes_match_warp_owned_bitwise(emu, monkeypatch, mode
         outs[mode] = (list(its), out)
     assert outs["1"][0] == outs["0"][0]
     assert np.array_equal(outs["1"][1], outs["0"][1])
+
+
+@pytest.mark.parametrize("n,scheme", [((64, 64), "bdf2"), ((128, 128), "mp"), ((64, 64, 64), "bdf2")])
+def test_staged_fch_matches_register_staged_bitwise(emu, monkeypatch, n, scheme):
+    """FCH stages its two-field passes with one slot (and, on a cubic 3D grid,
+    its middle passes): the same states bit for bit as the register-staged
+    passes."""
+    L = (4 * math.pi,) * len(n)
+    outs = {}
+    for staged in (True, False):
+        monkeypatch.setenv("PAGD_STAGED", "1" if staged else "0")
+        S = pagd.Solver("fch", n, L, 0.1, 0.05, 0.07, 0.1, scheme=scheme, precision="fp32_mixed", lib=emu)
+        assert S.launch_info()["staged"] == staged
+        S.set_state(I.noisy_field(n, -0.3, 0.05, 61))
+        out = S.empty_field()
+        its, res = S.run(0.001, 3, 1e-8, out)
+        assert all(res <= 1e-8)
+        outs[staged] = (list(its), out)
+    assert outs[True][0] == outs[False][0]
+    assert np.array_equal(outs[True][1], outs[False][1])
