@@ -126,7 +126,7 @@ ITER_BYTES_2D_PFC = 48.3
 # kernel build on the same workload; the roofline's traffic is this times the
 # steps of one timed launch (the per-step traffic is flat once the working set
 # is resident).  Workloads without a capture report null.
-TRAFFIC_PER_STEP = {"fch2d_256_bdf2_fp32mixed": 5.68e6}
+TRAFFIC_PER_STEP = {"fch2d_256_bdf2_fp32mixed": 5.07e6}
 # per batch step (all members).  The 3D figure is the capture of one 128^3
 # member (2 steps) scaled by points to 256^3, for two members: a lower bound,
 # as part of the 128^3 working set stays in L2
