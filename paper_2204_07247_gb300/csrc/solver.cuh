@@ -2816,15 +2816,34 @@ __host__ __device__ inline int phase_units(const Params& P, int ph) {
 __host__ __device__ inline int unit_cost(const Params& P, int ph) {
     return phase_is_col(ph) ? P.n0 : phase_is_mid(ph) ? kMidG * P.nm : 2 * P.n1;
 }
-// Device time per point of a member's current phase, in units of an FP32
-// iteration pass (measured on GB300 with pure phases of a 96-member batch:
-// exact base row / column passes 8.8x / 7.8x, incremental ones ~2/3 of that,
-// the last step's accept 5x).  The batched launch lays members out on a cost
-// axis of points x this weight, so that a global phase mixing members in FP64
-// base evaluations with members in FP32 iterations gives every warp about the
-// same time of work.  Only the dealing of units to warps depends on it.
+// Device time per point of a member's current phase, in units of a PFC FP32
+// iteration pass, measured on GB300 with pure phases of batched launches.
+// PFC (96 members): exact base row / column passes 8.8x / 7.8x, incremental
+// ones ~2/3 of that, the last step's accept 5x.  FCH (8 members of 512^2): its
+// iteration passes carry two fields, about 2x a PFC pass per point; relative
+// to them, exact base passes 4.5-5x, incremental B / C / D / E
+// 4.0 / 2.3 / 1.7 / 3.2x, accept 1.5x.  The batched
+// launch lays members out on a cost axis of points x this weight, so that a
+// global phase mixing members in FP64 base evaluations with members in FP32
+// iterations gives every warp about the same time of work.  Only the dealing
+// of units to warps depends on it.
 __host__ __device__ inline int phase_weight(const Params& P, const Ctl& c) {
     const bool t64 = P.precision != P_MIXED;
+    if (P.model == M_FCH && !t64) {
+        switch (c.ph) {
+            case PH_B: return c.inc ? 8 : 10;
+            case PH_C: return c.inc ? 5 : 10;
+            case PH_D: return c.inc ? 3 : 10;
+            case PH_E: return c.inc ? 6 : 10;
+            case PH_R1:
+            case PH_RI:
+            case PH_CI: return 2;
+            case PH_MF:
+            case PH_MI: return c.m64 ? 3 * (c.mk > 0 ? c.mk : 1) : 2;
+            case PH_ACCEPT: return 3;
+            default: return 4;
+        }
+    }
     switch (c.ph) {
         case PH_B: return c.inc ? 6 : 9;
         case PH_C:
