@@ -2718,9 +2718,17 @@ __device__ PAGD_DISPATCH void exec_cold(const Params& P, const Ctl& c, const Tw&
 }
 
 // the FP32 middle passes of a cubic grid run staged (mid_pass_staged) when
-// the launch stages its iteration passes
-template <class T, int NF> __device__ __forceinline__ bool mid_staged(const Params& P) {
-    if constexpr (sizeof(T) == 4 && (NF & (kNoCoop - 1)) != 0) return P.stage && P.nm == (NF & (kNoCoop - 1));
+// the launch stages its iteration passes; returns whether it ran them (only
+// fixed line lengths instantiate the staged pass)
+template <class T, int NF, int S>
+__device__ __forceinline__ bool mid_pass_staged_if(const Params& P, const Tw& tw, int k, const void* src, void* dst,
+                                                   char* smem) {
+    if constexpr (sizeof(T) == 4 && (NF & (kNoCoop - 1)) != 0) {
+        if (P.stage && P.nm == (NF & (kNoCoop - 1))) {
+            mid_pass_staged<NF & (kNoCoop - 1), S>(P, tw, k, (const float2*)src, (float2*)dst, smem);
+            return true;
+        }
+    }
     return false;
 }
 
@@ -2732,13 +2740,13 @@ __device__ __forceinline__ void exec_phase(const Params& P, const Ctl& c, const 
         case PH_CI: phase_CI<T, NF>(P, c, tw, smem); break;
         case PH_MF:
             if (c.m64) mid_pass<double, -1, NF>(P, tw, c.mk, P.NB64, P.X64, smem);
-            else if (mid_staged<T, NF>(P)) mid_pass_staged<NF & (kNoCoop - 1), -1>(P, tw, c.mk, (const float2*)P.NB, (float2*)P.X, smem);
-            else mid_pass<T, -1, NF>(P, tw, c.mk, (const cx<T>*)P.NB, (cx<T>*)P.X, smem);
+            else if (!mid_pass_staged_if<T, NF, -1>(P, tw, c.mk, P.NB, P.X, smem))
+                mid_pass<T, -1, NF>(P, tw, c.mk, (const cx<T>*)P.NB, (cx<T>*)P.X, smem);
             break;
         case PH_MI:
             if (c.m64) mid_pass<double, +1, NF>(P, tw, c.mk, P.NB64, P.DB64, smem);
-            else if (mid_staged<T, NF>(P)) mid_pass_staged<NF & (kNoCoop - 1), +1>(P, tw, c.mk, (const float2*)P.NB, (float2*)P.DB, smem);
-            else mid_pass<T, +1, NF>(P, tw, c.mk, (const cx<T>*)P.NB, (cx<T>*)P.DB, smem);
+            else if (!mid_pass_staged_if<T, NF, +1>(P, tw, c.mk, P.NB, P.DB, smem))
+                mid_pass<T, +1, NF>(P, tw, c.mk, (const cx<T>*)P.NB, (cx<T>*)P.DB, smem);
             break;
         default: exec_cold<T, NF>(P, c, tw, smem, red); break;
     }
