@@ -580,6 +580,26 @@ def profile_form(torch, pagd, form, w, steps, warm, trace, grid=None):
 PASS_BYTES_PFC = {"RI": 24.1, "CI": 24.2, "MF": 8.05, "MI": 8.05}
 
 
+def pass_rooflines(torch, pagd, w, peak, count=20, warm=3, lib=None):
+    """Each FP32 iteration pass of the PFC FP32-mixed workload w on its own
+    (pagd_pass_probe: `count` repetitions in one launch after `warm` steps,
+    barrier included, CUDA events): device time, algorithmic bytes
+    (PASS_BYTES_PFC x points) over that time, and the fraction of the
+    measured HBM peak."""
+    S = pagd.solver_for(w, lib=lib)
+    S.set_state(torch.from_numpy(w.u0(w.seeds[0])).cuda())
+    S.run(w.dt, warm, w.tol)
+    npts = int(np.prod(w.n))
+    out = {"workload": w.name, "count": count, "barrier_us": S.barrier_probe(count),
+           "bytes_per_point": dict(PASS_BYTES_PFC), "unit": "GB/s", "peak": peak,
+           "source": "pagd_pass_probe, one launch per pass, CUDA events"}
+    for p in (("RI", "CI", "MF", "MI") if len(w.n) == 3 else ("RI", "CI")):
+        us = S.pass_probe(p, count)
+        achieved = PASS_BYTES_PFC[p] * npts / (us * 1e-6) / 1e9 if us > 0 else None
+        out[p] = {"us": us, "achieved": achieved, "frac": achieved / peak if achieved else None}
+    return out
+
+
 def probe_pass(torch, pagd, w, which, count, warm, grid=None):
     """One iteration pass of w repeated `count` times in one launch (after a
     warm-up launch of `warm` steps): device time per pass with and without the
@@ -755,6 +775,11 @@ def main():
                 extra["pfc3d"]["vs_reference_trajectory"] = {
                     "at_64^3_same_spacing": batch_vs_reference(torch, pagd, ["pfc3d_64_bdf2_fp32mixed"]),
                     "at_256^3": batch_vs_reference(torch, pagd, [w3.name])}
+                # each iteration pass alone, after the timed region: reported, never fatal to the line
+                try:
+                    extra["pfc3d"]["roofline"]["passes"] = pass_rooflines(torch, pagd, w3, peak)
+                except Exception as e:  # pragma: no cover - reported in the JSON line
+                    extra["pfc3d"]["roofline"]["passes"] = {"error": f"{type(e).__name__}: {e}"}
         if rank == 0 and not args.no_cpu_baseline:
             # secondary baselines: a failure here is reported, never fatal to the line
             for key, fn in (("batched", lambda: oracle_batch_baseline(I.PFC_BATCH96, 2, host_cores())),
